@@ -1,0 +1,120 @@
+"""Right-preconditioned restarted GMRES and the fractional iteration count
+(Sec. 5.1).
+
+The paper preconditions GMRES with one multigrid V-cycle and stops at a
+relative residual reduction of 1e-8; it does not state the restart length,
+the orthogonalization or the side of the preconditioner.  Readings used on
+both sides of every parity test:
+
+* right preconditioning, x0 = 0, restart m (default 50);
+* modified Gram-Schmidt, Givens rotations;
+* the search directions z_j = M^{-1} v_j are kept (the flexible form), so the
+  update is x = x0 + Z y; for a fixed linear preconditioner this is the same
+  iterate as standard right-preconditioned GMRES;
+* stop when the Givens residual estimate |g_{j+1}| <= rtol * ||r_0||_2
+  (||r_0|| = ||b|| for x0 = 0); the reported residual is the true
+  ||b - A x||_2 / ||b||_2 after the update.
+
+The paper's printed counts are reproduced (within the soft tolerance of the
+tests) by left preconditioning with the preconditioned residual, deal.II's
+default; ``side="left"`` implements that protocol for the table comparison.
+Right preconditioning is the default because it measures the true residual
+and admits the single-precision (flexible) preconditioner of Sec. 5.2.
+
+nu_frac: the paper prints "nu = -8 log10 r_bar" with r_bar the geometric mean
+reduction per step; only nu = -8 / log10(r_bar) gives nu = n for a
+reduction of exactly 1e-8 in n steps (and 8 for r_bar = 0.1), so that is the
+reading used.  Absolute counts against the paper's tables remain a soft
+comparison (parity unpinned for absolute counts): the paper leaves gamma,
+the node placement and the GMRES details open.
+
+TEST INFRASTRUCTURE ONLY -- see the package docstring.
+"""
+
+import math
+
+import numpy as np
+
+
+def gmres(A, b, M=None, rtol=1e-8, restart=50, maxit=1000, side="right"):
+    """Returns (x, iterations, history of residual estimates, true relres).
+
+    side="right" (default) minimizes the true residual b - A x;
+    side="left" minimizes the preconditioned residual M^{-1}(b - A x) and
+    stops on its reduction, the convention of deal.II's GMRES, which the
+    paper's tables follow."""
+    if M is None:
+        M = lambda v: v
+    n = b.shape[0]
+    x = np.zeros(n)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, [0.0], 0.0
+    r = b - A @ x
+    if side == "left":
+        r = M(r)
+    ref = np.linalg.norm(r)
+    hist = [ref]
+    it = 0
+    while True:
+        beta = np.linalg.norm(r)
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        j_done = 0
+        converged = False
+        for j in range(restart):
+            if side == "left":
+                z = V[j]
+                w = M(A @ z)
+            else:
+                z = M(V[j])
+                w = A @ z
+            Z.append(z)
+            for i in range(j + 1):
+                H[i, j] = np.dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            rho = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / rho, H[j + 1, j] / rho
+            H[j, j] = rho
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            j_done = j + 1
+            hist.append(abs(g[j + 1]))
+            if abs(g[j + 1]) <= rtol * ref or it >= maxit:
+                converged = True
+                break
+            wn = np.linalg.norm(w)
+            if wn == 0.0:
+                converged = True
+                break
+            V.append(w / wn)
+        y = np.zeros(j_done)
+        for i in range(j_done - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:j_done] @ y[i + 1:j_done]) / H[i, i]
+        for i in range(j_done):
+            x = x + y[i] * Z[i]
+        r = b - A @ x
+        if converged:
+            break
+        if side == "left":
+            r = M(r)
+    return x, it, hist, np.linalg.norm(b - A @ x) / bnorm
+
+
+def nu_frac(res0, resn, n):
+    """Fractional iteration count: n steps scaled to a 1e-8 reduction."""
+    if n == 0:
+        return 0.0
+    rbar = (resn / res0) ** (1.0 / n)
+    return -8.0 / math.log10(rbar)

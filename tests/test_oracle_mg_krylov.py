@@ -1,0 +1,125 @@
+"""Pins for transfers, the V-cycle (Algorithm 1) and GMRES (Sec. 5.1)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spl
+
+from oracle import assemble, krylov, mg
+from oracle.basis import basis_table, gll_points
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables_nu_frac.json")
+
+
+def _nodes(k, N):
+    z = gll_points(k)
+    return np.concatenate([(c + z[:-1]) / N for c in range(N)] + [[1.0]])
+
+
+@pytest.mark.parametrize("k", [2, 3, 5, 7])
+def test_prolongation_1d_is_the_embedding(k):
+    # a coarse Q_k function is reproduced exactly at every fine support point
+    Nc = 3
+    P = mg.prolongation_1d(k, Nc, full=True)
+    xc, xf = _nodes(k, Nc), _nodes(k, 2 * Nc)
+    rng = np.random.default_rng(k)
+    coarse = rng.standard_normal(len(xc))
+    # evaluate the coarse FE function at the fine points cell by cell
+    ref = np.zeros(len(xf))
+    for i, x in enumerate(xf):
+        C = min(int(x * Nc), Nc - 1)
+        ref[i] = basis_table(k, [x * Nc - C], 0)[:, 0] @ coarse[k * C:k * C + k + 1]
+    assert np.allclose(P @ coarse, ref, atol=1e-13)
+    # and a global polynomial of degree k is prolongated to itself
+    p = lambda x: (x - 0.3) ** k - 2 * x
+    assert np.allclose(P @ p(xc), p(xf), atol=1e-12)
+
+
+def test_prolongation_2d_reproduces_tensor_polynomials():
+    k, Nc = 3, 2
+    P = mg.prolongation(2, k, Nc)
+    f = lambda x, y: x * (1 - x) * (x + 0.5) * y * (1 - y) * (2 - y)
+    xc, xf = _nodes(k, Nc)[1:-1], _nodes(k, 2 * Nc)[1:-1]
+    C = f(*np.meshgrid(xc, xc, indexing="xy")).ravel()
+    F = f(*np.meshgrid(xf, xf, indexing="xy")).ravel()
+    assert np.allclose(P @ C, F, atol=1e-13)
+
+
+def test_gmres_identity_preconditioner_solves_small_system():
+    A = assemble.c0ip_matrix(2, 2, 3)
+    b = np.random.default_rng(0).standard_normal(A.shape[0])
+    x, it, hist, rr = krylov.gmres(A, b, rtol=1e-10, restart=100)
+    assert rr < 1e-9
+    assert it <= A.shape[0]
+    assert np.allclose(x, spl.spsolve(A.tocsc(), b), rtol=1e-8)
+    assert all(h1 <= h0 * (1 + 1e-12) for h0, h1 in zip(hist, hist[1:]))
+
+
+def test_gmres_restart_still_converges():
+    A = assemble.c0ip_matrix(2, 2, 3)
+    b = np.random.default_rng(1).standard_normal(A.shape[0])
+    x, it, hist, rr = krylov.gmres(A, b, rtol=1e-9, restart=5, maxit=5000)
+    assert rr < 2e-9
+
+
+def test_nu_frac_closed_forms():
+    assert abs(krylov.nu_frac(1.0, 1e-8, 7) - 7.0) < 1e-12
+    assert abs(krylov.nu_frac(1.0, 0.1 ** 5, 5) - 8.0) < 1e-12
+    assert abs(krylov.nu_frac(3.0, 3e-12, 3) - 2.0) < 1e-12
+
+
+@pytest.mark.parametrize("smoother,ls", [("mvs", "inexact"), ("avs", "inexact"), ("mvs", "exact")])
+def test_mg_gmres_solves_to_tolerance(smoother, ls):
+    d, k, L = 2, 3, 3
+    steps = 2 if smoother == "avs" else 1
+    H = mg.Hierarchy(d, k, L, smoother=smoother, local_solver=ls, pre=steps, post=steps)
+    b = assemble.load_vector(d, k, 2 ** L, assemble.manufactured_f)
+    x, it, hist, rr = krylov.gmres(H.A[L], b, H.preconditioner, 1e-8)
+    assert rr <= 1.01e-8
+    u = spl.spsolve(H.A[L].tocsc(), b)
+    assert np.linalg.norm(x - u) <= 1e-6 * np.linalg.norm(u)
+    assert it <= 20
+
+
+def test_vcycle_is_a_convergent_iteration():
+    d, k, L = 2, 2, 4
+    H = mg.Hierarchy(d, k, L, smoother="mvs", local_solver="inexact")
+    A = H.A[L]
+    b = np.random.default_rng(2).standard_normal(A.shape[0])
+    u = spl.spsolve(A.tocsc(), b)
+    x = np.zeros_like(b)
+    errs = []
+    for _ in range(4):
+        x = H.vcycle(L, x, b)
+        errs.append(np.linalg.norm(x - u))
+    rates = np.array(errs[1:]) / np.array(errs[:-1])
+    assert rates.max() < 0.5
+
+
+def test_level_independent_iterations():
+    d, k = 2, 3
+    counts = []
+    for L in (3, 4, 5):
+        H = mg.Hierarchy(d, k, L, smoother="mvs", local_solver="inexact")
+        b = assemble.load_vector(d, k, 2 ** L, assemble.paper_sine_f)
+        _, it, _, _ = krylov.gmres(H.A[L], b, H.preconditioner, 1e-8, side="left")
+        counts.append(it)
+    assert max(counts) - min(counts) <= 1, counts
+
+
+@pytest.mark.parametrize("k,L,table", [(2, 5, "tab2_mvs_inexact_2d"), (3, 4, "tab2_mvs_inexact_2d"),
+                                       (4, 4, "tab2_mvs_inexact_2d"), (3, 4, "tab1_mvs_exact_2d")])
+def test_soft_comparison_with_paper_tables(k, L, table):
+    """Soft pin (parity of absolute counts unpinned): with deal.II's left
+    preconditioning the oracle's nu_frac at a small level lies within 25 % of
+    the paper's level-independent value (its first printed level)."""
+    golden = json.load(open(GOLDEN))
+    col = golden["degrees"].index(k)
+    printed = [row[col] for row in golden[table] if row[col] is not None][0]
+    ls = "exact" if table.startswith("tab1") else "inexact"
+    H = mg.Hierarchy(2, k, L, smoother="mvs", local_solver=ls)
+    b = assemble.load_vector(2, k, 2 ** L, assemble.paper_sine_f)
+    _, it, hist, _ = krylov.gmres(H.A[L], b, H.preconditioner, 1e-8, side="left")
+    nu = krylov.nu_frac(hist[0], hist[-1], it)
+    assert abs(nu - printed) <= 0.25 * printed, (nu, printed)
