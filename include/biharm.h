@@ -1,0 +1,178 @@
+/*
+ * biharm.h -- C ABI of the GB300 multigrid library for the C0 interior-penalty
+ * (C0IP) discretization of the clamped biharmonic problem on (0,1)^d
+ * (Sec. 2 of "Tensor-product vertex patch smoothers for biharmonic problems",
+ * arXiv 2412.05082), with Q_k elements on uniform Cartesian meshes.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A context owns one multigrid hierarchy: levels l = 1..L, level l has
+ *    N = 2^l cells per direction (the coarsest mesh of 2^d cells is one vertex
+ *    patch, Sec. 5.1).  Its unknowns are the interior support points,
+ *    n = (k N - 1)^d values, stored lexicographically with x fastest.  The
+ *    Q_k support points are the Gauss-Lobatto-Legendre points.
+ *  - Pointers named *_dev are device pointers owned by the caller: FP64,
+ *    contiguous, with the size of the level they refer to.  The library never
+ *    frees or keeps them.  Pointers named *_host are host pointers.
+ *  - Work is enqueued on the CUDA stream given to bh_create and is
+ *    asynchronous unless stated otherwise.  Calls on one context must not
+ *    overlap (a context is not thread-safe); distinct contexts are
+ *    independent.
+ *  - Every call returns a bh_status.  On failure a message is available from
+ *    bh_last_error() (thread-local).  The library never aborts, never prints,
+ *    never traps on the device, and has no CPU fallback: without a usable
+ *    CUDA device bh_create fails with BH_ECUDA.
+ */
+#ifndef BIHARM_H
+#define BIHARM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bh_ctx bh_ctx;
+
+typedef enum {
+  BH_OK = 0,
+  BH_EINVAL = -1,    /* bad argument (size, level, null pointer, option) */
+  BH_ENOMEM = -2,    /* device or host allocation failed */
+  BH_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  BH_ENOCONV = -4,   /* the Krylov solver did not reach the tolerance */
+  BH_ETIMEOUT = -5,  /* a bounded device-side wait ran out */
+  BH_EBUSY = -6      /* resource in use (server queue full) */
+} bh_status;
+
+/* smoother (Sec. 3): additive vertex-patch smoother with atomic or colored
+ * writes (Sec. 5), or the colored multiplicative one. */
+enum { BH_AVS_ATOMIC = 0, BH_AVS_COLORED = 1, BH_MVS_COLORED = 2 };
+/* local solver: fast diagonalization of the separable A~_v
+ * (Eq. (localsolverbila), Sec. 4.1) or the exact inverse of A_v (Sec. 3). */
+enum { BH_FDM = 0, BH_EXACT = 1 };
+/* precision of the V-cycle: FP64, or FP32 inside FP64 GMRES (Sec. 5.2). */
+enum { BH_FP64 = 0, BH_MIXED_FP32 = 1 };
+/* GMRES preconditioning side (Sec. 5.1 leaves it open).  BH_LEFT stops on the
+ * reduction of the preconditioned residual M^-1 (b - A x), the convention whose
+ * iteration counts match the paper's tables; BH_RIGHT stops on the true
+ * residual b - A x, whose FP64 rounding floor eps ||A|| ||x|| / ||b|| exceeds
+ * 1e-8 on the paper's finest meshes. */
+enum { BH_RIGHT = 0, BH_LEFT = 1 };
+/* coarse solver on level 1 (Sec. 5.1: "one smoothing step"). */
+enum { BH_COARSE_EXACT = 0, BH_COARSE_SMOOTH = 1 };
+/* right-hand sides for bh_rhs. */
+enum { BH_RHS_MANUFACTURED = 0, BH_RHS_PAPER_SINE = 1 };
+
+typedef struct {
+  int dim;           /* d = 2 or 3 */
+  int degree;        /* k = 2..7 */
+  int level;         /* finest level L >= 1 (N = 2^L) */
+  double gamma;      /* penalty constant of Eq. (bfc0ip), used as gamma/h; <= 0: k(k+1) */
+  int smoother;      /* BH_AVS_ATOMIC | BH_AVS_COLORED | BH_MVS_COLORED */
+  int local_solver;  /* BH_FDM | BH_EXACT */
+  int pre_steps;     /* smoothing steps before / after the coarse correction */
+  int post_steps;
+  double omega;      /* damping; <= 0: Sec. 5.1 defaults (AVS 1/4 in 2D, 0.1 in 3D
+                        (1/8 exact); MVS 1 in 2D, 0.7 in 3D) */
+  int precision;     /* BH_FP64 | BH_MIXED_FP32 */
+  int gmres_restart; /* restart length m (default 50) */
+  int gmres_side;    /* BH_LEFT (default) | BH_RIGHT */
+  int coarse;        /* BH_COARSE_EXACT (default) | BH_COARSE_SMOOTH */
+} bh_params;
+
+/* Fill *out with the defaults above for (dim, degree, level): MVS, FDM,
+ * one pre- and one post-smoothing step, FP64, GMRES(50), left side.
+ * Host only.  BH_EINVAL for d not in {2,3}, k not in 2..7 or level < 1. */
+bh_status bh_default_params(int dim, int degree, int level, bh_params* out);
+
+/* Create a context: host setup of the 1D data in FP64 (Eq. (matrix1d),
+ * Sec. 4.1: 1D mass/stiffness/bulk-and-face matrices, the generalized
+ * eigenpairs B s = lambda M s, the dense coarse inverse), allocation of every
+ * level's device buffers and the GMRES workspace.  stream: a cudaStream_t
+ * (NULL = legacy default stream).  The context is returned in *out and must be
+ * released with bh_destroy.  Synchronous. */
+bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out);
+
+/* Release every device and host resource of ctx (synchronizes its stream). */
+bh_status bh_destroy(bh_ctx* ctx);
+
+/* Number of unknowns (k 2^level - 1)^d of a level. Host only. */
+bh_status bh_num_unknowns(const bh_ctx* ctx, int level, int64_t* n);
+
+/* y = A_l x: the C0IP operator of Eq. (bfc0ip) on level l, applied
+ * matrix-free by sum factorization of its Kronecker form Eq. (c0iptensorvp)
+ * (2D) / Eq. (c0iptensorvp3D) (3D).  x_dev and y_dev: n(l) values, must not
+ * alias. */
+bh_status bh_apply_A(bh_ctx* ctx, int level, const double* x_dev, double* y_dev);
+
+/* r = b - A_l x (Algorithm 1, restriction step).  r_dev must not alias x_dev. */
+bh_status bh_residual(bh_ctx* ctx, int level, const double* x_dev, const double* b_dev,
+                      double* r_dev);
+
+/* steps smoothing steps x <- S_l(x, b) of the context's smoother (AVS or
+ * colored MVS, Sec. 3) with its local solver and damping, in place on x_dev. */
+bh_status bh_smooth(bh_ctx* ctx, int level, double* x_dev, const double* b_dev, int steps);
+
+/* xf += I_{l-1}^up xc: the embedding V_{l-1} -> V_l (Sec. 3).  level is the
+ * fine level (>= 2); xc_dev has n(level-1) values, xf_dev n(level). */
+bh_status bh_prolongate_add(bh_ctx* ctx, int level, const double* xc_dev, double* xf_dev);
+
+/* bc = (I_{l-1}^up)^T rf: restriction, the transpose of the embedding
+ * (Sec. 3).  level is the fine level (>= 2). */
+bh_status bh_restrict(bh_ctx* ctx, int level, const double* rf_dev, double* bc_dev);
+
+/* x <- MG_l(x, b): one V-cycle of Algorithm 1 from level l down to the coarse
+ * level 1, in the context's precision (FP32 inside, FP64 in and out, for
+ * BH_MIXED_FP32).  In place on x_dev. */
+bh_status bh_vcycle(bh_ctx* ctx, int level, double* x_dev, const double* b_dev);
+
+/* Solve A_L x = b on the finest level with GMRES preconditioned by one V-cycle
+ * (Sec. 5.1), x0 = 0, until the Givens estimate of the minimized residual
+ * (preconditioned for BH_LEFT, true for BH_RIGHT) has dropped by rtol relative
+ * to its initial value, or maxit iterations.  Right preconditioning keeps the
+ * preconditioned directions (flexible form), as the FP32 V-cycle requires.  On
+ * return (synchronous) *iters holds the iteration count and *relres the true
+ * ||b - A x|| / ||b|| in FP64.  BH_ENOCONV if rtol was not reached (x holds the
+ * last iterate). */
+bh_status bh_solve(bh_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit,
+                   int* iters, double* relres);
+
+/* bh_solve with host buffers: copies b_host to the device, solves, copies x
+ * back (b_host, x_host: n(L) doubles, pinned or pageable).  Synchronous. */
+bh_status bh_solve_host(bh_ctx* ctx, const double* b_host, double* x_host, double rtol,
+                        int maxit, int* iters, double* relres);
+
+/* b_i = int f phi_i for f = Delta^2 u of the manufactured u = prod sin^2(pi x_a)
+ * (BH_RHS_MANUFACTURED) or of the paper's u = prod sin(pi x_a)
+ * (BH_RHS_PAPER_SINE, Sec. 5.1), on level l. */
+bh_status bh_rhs(bh_ctx* ctx, int level, int kind, double* b_dev);
+
+/* Counters and CUDA-event timings of the context as a JSON object written to
+ * buf (NUL-terminated, truncated to len).  Host only. */
+bh_status bh_stats(const bh_ctx* ctx, char* buf, size_t len);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* bh_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts).  Host only; never fails. */
+long long bh_kernel_launches(void);
+
+/* Host-only 1D setup in FP64 on a line of `cells` cells of size 1 (the level
+ * scaling is applied by the caller): which = 0, 1, 2 returns the mass M,
+ * stiffness L and bulk-plus-face matrix B of Eq. (matrix1d) / Eq. (ev) on the
+ * nodes 0..k*cells, row-major into out (ld = k*cells + 1). */
+bh_status bh_setup_1d(int degree, double gamma, int cells, int which, double* out);
+
+/* Host-only: the fast-diagonalization data of Sec. 4.1 for the 1D patch
+ * matrices (B_v, M_v) of patch type `type` (0 interior, 1 touching x = 0,
+ * 2 touching x = 1, 3 both: the single patch of N = 2) on cells of size 1:
+ * S (m x m, row-major, columns the M-orthonormal eigenvectors) and lambda (m),
+ * m = 2k - 1, with S^T M_v S = I and S^T B_v S = diag(lambda). */
+bh_status bh_setup_fdm(int degree, double gamma, int type, double* S, double* lambda);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIHARM_H */

@@ -1,0 +1,234 @@
+"""Python binding of libbiharm.so, the GB300 multigrid library for the C0IP
+biharmonic problem (arXiv 2412.05082).
+
+Argument marshalling only: every computation runs in the CUDA library behind
+the C ABI declared in ``include/biharm.h``; PyTorch supplies device memory and
+streams.  There is no CPU fallback -- without the built library (or without a
+CUDA device) the calls raise.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbiharm.so")
+
+# enums of biharm.h
+BH_OK, BH_EINVAL, BH_ENOMEM, BH_ECUDA, BH_ENOCONV, BH_ETIMEOUT, BH_EBUSY = 0, -1, -2, -3, -4, -5, -6
+AVS_ATOMIC, AVS_COLORED, MVS_COLORED = 0, 1, 2
+FDM, EXACT = 0, 1
+FP64, MIXED_FP32 = 0, 1
+RIGHT, LEFT = 0, 1
+COARSE_EXACT, COARSE_SMOOTH = 0, 1
+RHS_MANUFACTURED, RHS_PAPER_SINE = 0, 1
+
+STATUS_NAMES = {0: "BH_OK", -1: "BH_EINVAL", -2: "BH_ENOMEM", -3: "BH_ECUDA",
+                -4: "BH_ENOCONV", -5: "BH_ETIMEOUT", -6: "BH_EBUSY"}
+
+
+class BiharmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("level", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("smoother", ctypes.c_int),
+                ("local_solver", ctypes.c_int), ("pre_steps", ctypes.c_int),
+                ("post_steps", ctypes.c_int), ("omega", ctypes.c_double),
+                ("precision", ctypes.c_int), ("gmres_restart", ctypes.c_int),
+                ("gmres_side", ctypes.c_int), ("coarse", ctypes.c_int)]
+
+
+# every entry point of biharm.h with its ctypes signature
+_c = ctypes
+_P, _D, _I, _I64 = _c.c_void_p, _c.c_double, _c.c_int, _c.c_int64
+SIGNATURES = {
+    "bh_default_params": (_I, [_I, _I, _I, _c.POINTER(Params)]),
+    "bh_create": (_I, [_c.POINTER(Params), _P, _c.POINTER(_P)]),
+    "bh_destroy": (_I, [_P]),
+    "bh_num_unknowns": (_I, [_P, _I, _c.POINTER(_I64)]),
+    "bh_apply_A": (_I, [_P, _I, _P, _P]),
+    "bh_residual": (_I, [_P, _I, _P, _P, _P]),
+    "bh_smooth": (_I, [_P, _I, _P, _P, _I]),
+    "bh_prolongate_add": (_I, [_P, _I, _P, _P]),
+    "bh_restrict": (_I, [_P, _I, _P, _P]),
+    "bh_vcycle": (_I, [_P, _I, _P, _P]),
+    "bh_solve": (_I, [_P, _P, _P, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
+    "bh_solve_host": (_I, [_P, _P, _P, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
+    "bh_rhs": (_I, [_P, _I, _I, _P]),
+    "bh_stats": (_I, [_P, _c.c_char_p, _c.c_size_t]),
+    "bh_last_error": (_c.c_char_p, []),
+    "bh_kernel_launches": (_c.c_longlong, []),
+    "bh_setup_1d": (_I, [_I, _D, _I, _I, _P]),
+    "bh_setup_fdm": (_I, [_I, _D, _I, _P, _P]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libbiharm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise BiharmError(BH_ECUDA, "libbiharm.so is not built (run build.build())")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != BH_OK:
+        raise BiharmError(status, load().bh_last_error().decode())
+    return status
+
+
+def default_params(dim, degree, level, **overrides):
+    p = Params()
+    _check(load().bh_default_params(dim, degree, level, ctypes.byref(p)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def kernel_launches():
+    return int(load().bh_kernel_launches())
+
+
+def last_error():
+    return load().bh_last_error().decode()
+
+
+def setup_1d(degree, gamma, cells, which):
+    """Host FP64 1D matrix (0 = M, 1 = L, 2 = B) on `cells` cells of size 1."""
+    import numpy as np
+    n = degree * cells + 1
+    out = np.zeros((n, n))
+    _check(load().bh_setup_1d(degree, gamma, cells, which, out.ctypes.data))
+    return out
+
+
+def setup_fdm(degree, gamma, ptype):
+    """Host FP64 fast-diagonalization data (S, lambda) of a patch type."""
+    import numpy as np
+    m = 2 * degree - 1
+    S = np.zeros((m, m))
+    lam = np.zeros(m)
+    _check(load().bh_setup_fdm(degree, gamma, ptype, S.ctypes.data, lam.ctypes.data))
+    return S, lam
+
+
+def _dev(t, n, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be a contiguous float64 tensor with %d values" % (name, n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One multigrid hierarchy (levels 1..L) on the current CUDA device."""
+
+    def __init__(self, params, stream=None):
+        import torch
+        self.params = params
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(load().bh_create(ctypes.byref(params), ctypes.c_void_p(stream.cuda_stream),
+                                ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise BiharmError(BH_EINVAL, "context closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(load().bh_destroy(self._h))
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def num_unknowns(self, level=None):
+        level = self.params.level if level is None else level
+        n = ctypes.c_int64()
+        _check(load().bh_num_unknowns(self.handle, level, ctypes.byref(n)))
+        return n.value
+
+    def apply_A(self, level, x, y):
+        n = self.num_unknowns(level)
+        _check(load().bh_apply_A(self.handle, level, _dev(x, n, "x"), _dev(y, n, "y")))
+
+    def residual(self, level, x, b, r):
+        n = self.num_unknowns(level)
+        _check(load().bh_residual(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b"),
+                                  _dev(r, n, "r")))
+
+    def smooth(self, level, x, b, steps=1):
+        n = self.num_unknowns(level)
+        _check(load().bh_smooth(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b"), steps))
+
+    def prolongate_add(self, level, xc, xf):
+        _check(load().bh_prolongate_add(self.handle, level,
+                                        _dev(xc, self.num_unknowns(level - 1), "xc"),
+                                        _dev(xf, self.num_unknowns(level), "xf")))
+
+    def restrict(self, level, rf, bc):
+        _check(load().bh_restrict(self.handle, level, _dev(rf, self.num_unknowns(level), "rf"),
+                                  _dev(bc, self.num_unknowns(level - 1), "bc")))
+
+    def vcycle(self, level, x, b):
+        n = self.num_unknowns(level)
+        _check(load().bh_vcycle(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b")))
+
+    def solve(self, b, x, rtol=1e-8, maxit=200, raise_on_noconv=True):
+        n = self.num_unknowns()
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        st = load().bh_solve(self.handle, _dev(b, n, "b"), _dev(x, n, "x"), rtol, maxit,
+                             ctypes.byref(it), ctypes.byref(rr))
+        if st != BH_ENOCONV or raise_on_noconv:
+            _check(st)
+        return it.value, rr.value
+
+    def solve_host(self, b, x, rtol=1e-8, maxit=200):
+        """b, x: host float64 arrays (numpy or CPU tensors, contiguous)."""
+        import numpy as np
+        n = self.num_unknowns()
+        for a in (b, x):
+            arr = a.numpy() if hasattr(a, "numpy") else a
+            if arr.dtype != np.float64 or arr.size != n or not arr.flags.c_contiguous:
+                raise ValueError("host buffers must be contiguous float64 with %d values" % n)
+        pb = (b.numpy() if hasattr(b, "numpy") else b).ctypes.data
+        px = (x.numpy() if hasattr(x, "numpy") else x).ctypes.data
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        _check(load().bh_solve_host(self.handle, pb, px, rtol, maxit, ctypes.byref(it),
+                                    ctypes.byref(rr)))
+        return it.value, rr.value
+
+    def rhs(self, level, kind, b):
+        _check(load().bh_rhs(self.handle, level, kind, _dev(b, self.num_unknowns(level), "b")))
+
+    def stats(self):
+        import json
+        buf = ctypes.create_string_buffer(4096)
+        _check(load().bh_stats(self.handle, buf, len(buf)))
+        return json.loads(buf.value.decode())

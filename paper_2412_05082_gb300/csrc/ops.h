@@ -1,0 +1,88 @@
+// Host-visible interface of the CUDA kernels (no device code here).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "setup.h"
+
+namespace bh {
+
+// Kernels launched by this process (all contexts).
+extern std::atomic<long long> g_kernel_launches;
+
+struct LevelGeom {
+  int d;       // dimension
+  int k;       // degree
+  int N;       // cells per direction
+  int n;       // interior nodes per direction, k N - 1
+  int64_t nd;  // n^d
+};
+
+// Number of scratch arrays (each nd values) that apply() needs.
+inline int apply_scratch_arrays(int d) { return d == 2 ? 3 : 6; }
+
+enum ApplyMode { kStore = 0, kResidual = 1 };
+
+template <typename T>
+struct Ops {
+  // Kernel-parameter tables (1D class tables, FDM eigendata, prolongation)
+  // converted to T; opaque, freed with free_tables.
+  static void* make_tables(const Setup1D& s, int d);
+  static void free_tables(void* tab, int k);
+
+  // mode kStore: y = scale * A_ref x; mode kResidual: y = b - scale * A_ref x.
+  static cudaError_t apply(const void* tab, const LevelGeom& g, const T* x, const T* b, T* y,
+                           double scale, int mode, T* scratch, cudaStream_t st);
+
+  // x += scale * sum_{v in verts} R_v^T A~_v,ref^-1 R_v r  (fast diagonalization).
+  static cudaError_t patch_fdm(const void* tab, const LevelGeom& g, const T* r, T* x,
+                               const int* verts, int count, double scale, bool atomic,
+                               cudaStream_t st);
+
+  // x += scale * sum_{v in verts} R_v^T Ainv[combo(v)] R_v r  (dense exact inverse;
+  // Ainv holds 4^d slots of m^d x m^d matrices, slot = sum_a type_a 4^a).
+  static cudaError_t patch_exact(const LevelGeom& g, const T* Ainv, const T* r, T* x,
+                                 const int* verts, int count, double scale, bool atomic,
+                                 cudaStream_t st);
+
+  // xf += P xc (embedding), fine geometry given; s0, s1 scratch of fine nd each.
+  static cudaError_t prolongate_add(const void* tab, const LevelGeom& fine, const T* xc, T* xf,
+                                    T* s0, T* s1, cudaStream_t st);
+
+  // bc = P^T rf.
+  static cudaError_t restrict_(const void* tab, const LevelGeom& fine, const T* rf, T* bc, T* s0,
+                               T* s1, cudaStream_t st);
+
+  // y += x
+  static cudaError_t add(T* y, const T* x, int64_t n, cudaStream_t st);
+
+  // out = scale * A (n x n dense symmetric, FP64) * in.
+  static cudaError_t dense_symv(int n, const double* A, const T* in, T* out, double scale,
+                                cudaStream_t st);
+};
+
+// ---- vector kernels (FP64 unless noted) -------------------------------------
+// Deterministic dot product: partial sums per block, then one block in fixed order.
+constexpr int kDotBlocks = 608;  // 4 x 152 SMs
+cudaError_t vec_dot(const double* x, const double* y, int64_t n, double* partials, double* out,
+                    cudaStream_t st);
+// y += a x (host scalar)
+cudaError_t vec_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t st);
+// y += sign * (*a) x (device scalar)
+cudaError_t vec_axpy_dev(double* y, const double* a, double sign, const double* x, int64_t n,
+                         cudaStream_t st);
+// y = a x
+cudaError_t vec_scale(double* y, double a, const double* x, int64_t n, cudaStream_t st);
+// r = b - y
+cudaError_t vec_sub(double* r, const double* b, const double* y, int64_t n, cudaStream_t st);
+// conversions
+cudaError_t vec_d2f(float* y, const double* x, int64_t n, cudaStream_t st);
+cudaError_t vec_f2d(double* y, const float* x, int64_t n, cudaStream_t st);
+// b = sum_terms c_t (F_t0 (x) F_t1 [(x) F_t2]) on the interior nodes of a level:
+// separable right-hand sides; F holds nterms * d rows of n values.
+cudaError_t rhs_separable(int d, int n, int nterms, const double* coef, const double* F,
+                          double* b, cudaStream_t st);
+
+}  // namespace bh

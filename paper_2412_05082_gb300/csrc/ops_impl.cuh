@@ -1,0 +1,357 @@
+// Host launchers of the kernels in kernels.cuh: degree dispatch, grid sizing
+// and the per-context tables.  Included once per value type (inst_f64.cu,
+// inst_f32.cu).
+#pragma once
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace bh {
+
+template <typename T, int K>
+struct HostTables {
+  Tables<T, K> t;
+  T* dinv = nullptr;  // device, 4^d slots x m^d reciprocals of the eigenvalue sums
+  int d = 0;
+};
+
+template <typename T, int K>
+static void* make_tables_k(const Setup1D& s, int d) {
+  auto* h = new (std::nothrow) HostTables<T, K>();
+  if (!h) return nullptr;
+  const int nc = 3 * K + 1, bw = 4 * K + 1, m = 2 * K - 1;
+  for (int c = 0; c < nc; ++c)
+    for (int t = 0; t < bw; ++t) {
+      h->t.op.M[c][t] = (T)s.tabM[c * bw + t];
+      h->t.op.L[c][t] = (T)s.tabL[c * bw + t];
+      h->t.op.B[c][t] = (T)s.tabB[c * bw + t];
+    }
+  for (int ty = 0; ty < 4; ++ty) {
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j < m; ++j) h->t.fdm.S[ty][i][j] = (T)s.fdmS[ty][i * m + j];
+      h->t.fdm.lam[ty][i] = (T)s.fdmLam[ty][i];
+    }
+  }
+  for (int r = 0; r < 2 * K; ++r)
+    for (int q = 0; q <= K; ++q) h->t.xfer.P[r][q] = (T)s.prolong[r * (K + 1) + q];
+  // reciprocal eigenvalue sums per type combination (FP64, then converted)
+  int md = 1, slots = 1;
+  for (int a = 0; a < d; ++a) {
+    md *= m;
+    slots *= 4;
+  }
+  std::vector<T> dinv((size_t)slots * md);
+  for (int slot = 0; slot < slots; ++slot)
+    for (int l = 0; l < md; ++l) {
+      double sum = 0.0;
+      int ll = l, ss = slot;
+      for (int a = 0; a < d; ++a) {
+        sum += s.fdmLam[ss % 4][ll % m];
+        ll /= m;
+        ss /= 4;
+      }
+      dinv[(size_t)slot * md + l] = (T)(1.0 / sum);
+    }
+  h->d = d;
+  if (cudaMalloc(&h->dinv, dinv.size() * sizeof(T)) != cudaSuccess ||
+      cudaMemcpy(h->dinv, dinv.data(), dinv.size() * sizeof(T), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaFree(h->dinv);
+    delete h;
+    return nullptr;
+  }
+  return h;
+}
+
+#define BH_K_DISPATCH(k, CALL) \
+  switch (k) {                 \
+    case 2: CALL(2); break;    \
+    case 3: CALL(3); break;    \
+    case 4: CALL(4); break;    \
+    case 5: CALL(5); break;    \
+    case 6: CALL(6); break;    \
+    case 7: CALL(7); break;    \
+    default: return cudaErrorInvalidValue; \
+  }
+
+inline unsigned grid_for(int64_t threads, int block) {
+  return (unsigned)((threads + block - 1) / block);
+}
+
+template <typename T>
+void* Ops<T>::make_tables(const Setup1D& s, int d) {
+  switch (s.k) {
+    case 2: return make_tables_k<T, 2>(s, d);
+    case 3: return make_tables_k<T, 3>(s, d);
+    case 4: return make_tables_k<T, 4>(s, d);
+    case 5: return make_tables_k<T, 5>(s, d);
+    case 6: return make_tables_k<T, 6>(s, d);
+    case 7: return make_tables_k<T, 7>(s, d);
+  }
+  return nullptr;
+}
+
+template <typename T, int K>
+static void free_tables_k(void* p) {
+  auto* h = static_cast<HostTables<T, K>*>(p);
+  cudaFree(h->dinv);
+  delete h;
+}
+
+template <typename T>
+void Ops<T>::free_tables(void* p, int k) {
+  if (!p) return;
+  switch (k) {
+    case 2: free_tables_k<T, 2>(p); break;
+    case 3: free_tables_k<T, 3>(p); break;
+    case 4: free_tables_k<T, 4>(p); break;
+    case 5: free_tables_k<T, 5>(p); break;
+    case 6: free_tables_k<T, 6>(p); break;
+    case 7: free_tables_k<T, 7>(p); break;
+  }
+}
+
+template <typename T, int K, int KIND>
+static cudaError_t launch_sweep(const OpTab<T, K>& tab, const SweepArgs<T>& a, cudaStream_t st) {
+  const int block = 128;
+  sweep_kernel<T, K, KIND><<<grid_for(a.lines * a.N, block), block, 0, st>>>(tab, a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <typename T, int K>
+static cudaError_t apply_k(const void* tabp, const LevelGeom& g, const T* x, const T* b, T* y,
+                           double scale, int mode, T* scratch, cudaStream_t st) {
+  const auto& tab = static_cast<const HostTables<T, K>*>(tabp)->t.op;
+  SweepArgs<T> a{};
+  a.d = g.d;
+  a.N = g.N;
+  a.n = g.n;
+  a.lines = g.nd / g.n;
+  a.scale = scale;
+  a.mode = mode;
+  a.b = b;
+  T* s[6];
+  for (int i = 0; i < 6; ++i) s[i] = scratch + (int64_t)i * g.nd;
+  // pass x: split into M x, L x, B x
+  a.axis = 0;
+  a.stride = 1;
+  a.in[0] = x;
+  a.out[0] = s[0];
+  a.out[1] = s[1];
+  a.out[2] = s[2];
+  cudaError_t e = launch_sweep<T, K, 0>(tab, a, st);
+  if (e != cudaSuccess) return e;
+  if (g.d == 2) {
+    a.axis = 1;
+    a.stride = g.n;
+    a.in[0] = s[0];
+    a.in[1] = s[1];
+    a.in[2] = s[2];
+    a.out[0] = y;
+    return launch_sweep<T, K, 2>(tab, a, st);
+  }
+  a.axis = 1;
+  a.stride = g.n;
+  a.in[0] = s[0];
+  a.in[1] = s[1];
+  a.in[2] = s[2];
+  a.out[0] = s[3];
+  a.out[1] = s[4];
+  a.out[2] = s[5];
+  e = launch_sweep<T, K, 1>(tab, a, st);
+  if (e != cudaSuccess) return e;
+  a.axis = 2;
+  a.stride = (int64_t)g.n * g.n;
+  a.in[0] = s[3];
+  a.in[1] = s[4];
+  a.in[2] = s[5];
+  a.out[0] = y;
+  return launch_sweep<T, K, 3>(tab, a, st);
+}
+
+template <typename T>
+cudaError_t Ops<T>::apply(const void* tab, const LevelGeom& g, const T* x, const T* b, T* y,
+                          double scale, int mode, T* scratch, cudaStream_t st) {
+#define BH_CALL(KK) return apply_k<T, KK>(tab, g, x, b, y, scale, mode, scratch, st)
+  BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int D, int K>
+static cudaError_t patch_fdm_k(const void* tabp, const LevelGeom& g, const T* r, T* x,
+                               const int* verts, int count, double scale, bool atomic,
+                               cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const auto* h = static_cast<const HostTables<T, K>*>(tabp);
+  PatchArgs<T> a{};
+  a.r = r;
+  a.x = x;
+  a.verts = verts;
+  a.count = count;
+  a.N = g.N;
+  a.n = g.n;
+  a.scale = scale;
+  a.dinv = h->dinv;
+  constexpr int PB = PatchCfg<T, D, K>::PB;
+  const unsigned grid = (unsigned)((count + PB - 1) / PB);
+  if (atomic)
+    patch_fdm_kernel<T, D, K, true><<<grid, 256, 0, st>>>(h->t.fdm, a);
+  else
+    patch_fdm_kernel<T, D, K, false><<<grid, 256, 0, st>>>(h->t.fdm, a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::patch_fdm(const void* tab, const LevelGeom& g, const T* r, T* x,
+                              const int* verts, int count, double scale, bool atomic,
+                              cudaStream_t st) {
+  if (g.d == 2) {
+#define BH_CALL(KK) return patch_fdm_k<T, 2, KK>(tab, g, r, x, verts, count, scale, atomic, st)
+    BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  } else {
+#define BH_CALL(KK) return patch_fdm_k<T, 3, KK>(tab, g, r, x, verts, count, scale, atomic, st)
+    BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int D, int K>
+static cudaError_t patch_exact_k(const LevelGeom& g, const T* ainv, const T* r, T* x,
+                                 const int* verts, int count, double scale, bool atomic,
+                                 cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  PatchArgs<T> a{};
+  a.r = r;
+  a.x = x;
+  a.verts = verts;
+  a.count = count;
+  a.N = g.N;
+  a.n = g.n;
+  a.scale = scale;
+  a.ainv = ainv;
+  constexpr int PB = PatchCfg<T, D, K>::PB;
+  const unsigned grid = (unsigned)((count + PB - 1) / PB);
+  if (atomic)
+    patch_exact_kernel<T, D, K, true><<<grid, 256, 0, st>>>(a);
+  else
+    patch_exact_kernel<T, D, K, false><<<grid, 256, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::patch_exact(const LevelGeom& g, const T* Ainv, const T* r, T* x,
+                                const int* verts, int count, double scale, bool atomic,
+                                cudaStream_t st) {
+  if (g.d == 2) {
+#define BH_CALL(KK) return patch_exact_k<T, 2, KK>(g, Ainv, r, x, verts, count, scale, atomic, st)
+    BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  } else {
+#define BH_CALL(KK) return patch_exact_k<T, 3, KK>(g, Ainv, r, x, verts, count, scale, atomic, st)
+    BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  }
+  return cudaErrorInvalidValue;
+}
+
+// one transfer pass along `axis`; shapes per axis given for input and output
+template <typename T, int K, bool PROLONG>
+static cudaError_t xfer_pass(const XferTab<T, K>& tab, int d, int axis, const int* din,
+                             const int* dout, int Nc, int nc, int nf, const T* in, T* out,
+                             bool add, cudaStream_t st) {
+  XferArgs<T> a{};
+  a.in = in;
+  a.out = out;
+  a.d = d;
+  a.axis = axis;
+  a.Nc = Nc;
+  a.nc = nc;
+  a.nf = nf;
+  a.add = add;
+  int64_t si = 1, so = 1, lines = 1;
+  for (int i = 0; i < 3; ++i) {
+    a.dims_in[i] = i < d ? din[i] : 1;
+    a.dims_out[i] = i < d ? dout[i] : 1;
+    a.str_in[i] = si;
+    a.str_out[i] = so;
+    si *= a.dims_in[i];
+    so *= a.dims_out[i];
+    if (i < d && i != axis) lines *= din[i];
+  }
+  a.lines = lines;
+  const int block = 128;
+  if (PROLONG)
+    prolong_kernel<T, K><<<grid_for(lines * Nc, block), block, 0, st>>>(tab, a);
+  else
+    restrict_kernel<T, K><<<grid_for(lines * Nc, block), block, 0, st>>>(tab, a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <typename T, int K, bool PROLONG>
+static cudaError_t transfer_k(const void* tabp, const LevelGeom& fine, const T* in, T* out,
+                              T* s0, T* s1, cudaStream_t st) {
+  const auto& tab = static_cast<const HostTables<T, K>*>(tabp)->t.xfer;
+  const int d = fine.d, Nc = fine.N / 2, nc = K * Nc - 1, nf = fine.n;
+  int dims[3];
+  for (int i = 0; i < 3; ++i) dims[i] = PROLONG ? nc : nf;
+  const T* src = in;
+  T* bufs[2] = {s0, s1};
+  for (int axis = 0; axis < d; ++axis) {
+    int dn[3] = {dims[0], dims[1], dims[2]};
+    dn[axis] = PROLONG ? nf : nc;
+    const bool last = axis == d - 1;
+    T* dst = last ? out : bufs[axis % 2];
+    cudaError_t e =
+        xfer_pass<T, K, PROLONG>(tab, d, axis, dims, dn, Nc, nc, nf, src, dst, PROLONG && last, st);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < 3; ++i) dims[i] = dn[i];
+    src = dst;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Ops<T>::prolongate_add(const void* tab, const LevelGeom& fine, const T* xc, T* xf,
+                                   T* s0, T* s1, cudaStream_t st) {
+#define BH_CALL(KK) return transfer_k<T, KK, true>(tab, fine, xc, xf, s0, s1, st)
+  BH_K_DISPATCH(fine.k, BH_CALL)
+#undef BH_CALL
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Ops<T>::restrict_(const void* tab, const LevelGeom& fine, const T* rf, T* bc, T* s0,
+                              T* s1, cudaStream_t st) {
+#define BH_CALL(KK) return transfer_k<T, KK, false>(tab, fine, rf, bc, s0, s1, st)
+  BH_K_DISPATCH(fine.k, BH_CALL)
+#undef BH_CALL
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Ops<T>::add(T* y, const T* x, int64_t n, cudaStream_t st) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  add_kernel<T><<<(unsigned)(g < 1 ? 1 : g), 256, 0, st>>>(y, x, n);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::dense_symv(int n, const double* A, const T* in, T* out, double scale,
+                               cudaStream_t st) {
+  dense_symv_kernel<T><<<grid_for(n, 128), 128, 0, st>>>(n, A, in, out, scale);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+}  // namespace bh

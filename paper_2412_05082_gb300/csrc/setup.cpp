@@ -1,0 +1,443 @@
+// Host-side FP64 setup: Q_k basis on Gauss-Lobatto-Legendre points, the 1D
+// matrices of Eq. (matrix1d) with the face terms of Eq. (ev)/(eh), their row
+// classes, the vertex-patch submatrices, the generalized eigenpairs of the
+// fast diagonalization method (Sec. 4.1) and dense SPD inverses for the exact
+// local and coarse solvers.
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <stdexcept>
+
+namespace bh {
+
+namespace {
+
+// Legendre P_n(x) and P_{n-1}(x) by the three-term recurrence.
+void legendre(int n, double x, double& pn, double& pnm1) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { pn = 1.0; pnm1 = 0.0; return; }
+  for (int m = 1; m < n; ++m) {
+    double p2 = ((2.0 * m + 1.0) * x * p1 - m * p0) / (m + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  pn = p1;
+  pnm1 = p0;
+}
+
+}  // namespace
+
+std::vector<double> gll_points(int k) {
+  // end points and the roots of P_k', found by Newton's method from the
+  // Chebyshev-Gauss-Lobatto points; P_k' and P_k'' from the Legendre ODE.
+  std::vector<double> x(k + 1);
+  x[0] = -1.0;
+  x[k] = 1.0;
+  for (int j = 1; j < k; ++j) {
+    double t = -std::cos(M_PI * j / k);
+    for (int it = 0; it < 100; ++it) {
+      double pn, pm;
+      legendre(k, t, pn, pm);
+      double d1 = k * (t * pn - pm) / (t * t - 1.0);
+      double d2 = (2.0 * t * d1 - k * (k + 1.0) * pn) / (1.0 - t * t);
+      double dt = d1 / d2;
+      t -= dt;
+      if (std::fabs(dt) < 1e-17) break;
+    }
+    x[j] = t;
+  }
+  std::sort(x.begin(), x.end());
+  for (double& v : x) v = 0.5 * (v + 1.0);
+  x[0] = 0.0;
+  x[k] = 1.0;
+  return x;
+}
+
+void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(q, 0.0);
+  w.assign(q, 0.0);
+  for (int j = 0; j < q; ++j) {
+    double t = std::cos(M_PI * (j + 0.75) / (q + 0.5));
+    double d1 = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double pn, pm;
+      legendre(q, t, pn, pm);
+      d1 = q * (t * pn - pm) / (t * t - 1.0);
+      double dt = pn / d1;
+      t -= dt;
+      if (std::fabs(dt) < 1e-17) break;
+    }
+    double pn, pm;
+    legendre(q, t, pn, pm);
+    d1 = q * (t * pn - pm) / (t * t - 1.0);
+    x[j] = 0.5 * (t + 1.0);
+    w[j] = 1.0 / ((1.0 - t * t) * d1 * d1);  // 2/((1-t^2)P'^2), halved for [0,1]
+  }
+}
+
+double lagrange(const std::vector<double>& z, int i, double x, int deriv) {
+  // l_i = prod_{j != i} (x - z_j)/(z_i - z_j); derivatives by the product rule.
+  const int n = (int)z.size();
+  auto fac = [&](int j) { return (x - z[j]) / (z[i] - z[j]); };
+  if (deriv == 0) {
+    double p = 1.0;
+    for (int j = 0; j < n; ++j)
+      if (j != i) p *= fac(j);
+    return p;
+  }
+  if (deriv == 1) {
+    double s = 0.0;
+    for (int m = 0; m < n; ++m) {
+      if (m == i) continue;
+      double p = 1.0 / (z[i] - z[m]);
+      for (int j = 0; j < n; ++j)
+        if (j != i && j != m) p *= fac(j);
+      s += p;
+    }
+    return s;
+  }
+  double s = 0.0;
+  for (int m = 0; m < n; ++m) {
+    if (m == i) continue;
+    for (int l = 0; l < n; ++l) {
+      if (l == i || l == m) continue;
+      double p = 1.0 / ((z[i] - z[m]) * (z[i] - z[l]));
+      for (int j = 0; j < n; ++j)
+        if (j != i && j != m && j != l) p *= fac(j);
+      s += p;
+    }
+  }
+  return s;
+}
+
+static void cell_matrices(int k, const std::vector<double>& z, std::vector<double>& M,
+                          std::vector<double>& L, std::vector<double>& B) {
+  std::vector<double> x, w;
+  gauss_rule(k + 2, x, w);
+  const int n = k + 1;
+  M.assign(n * n, 0.0);
+  L.assign(n * n, 0.0);
+  B.assign(n * n, 0.0);
+  for (size_t q = 0; q < x.size(); ++q) {
+    double v0[kMaxK + 1], v1[kMaxK + 1], v2[kMaxK + 1];
+    for (int i = 0; i < n; ++i) {
+      v0[i] = lagrange(z, i, x[q], 0);
+      v1[i] = lagrange(z, i, x[q], 1);
+      v2[i] = lagrange(z, i, x[q], 2);
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        M[i * n + j] += w[q] * v0[i] * v0[j];
+        L[i * n + j] += w[q] * v1[i] * v1[j];
+        B[i * n + j] += w[q] * v2[i] * v2[j];
+      }
+  }
+}
+
+void global_1d(int k, double gamma, int cells, std::vector<double>& M, std::vector<double>& L,
+               std::vector<double>& B) {
+  const std::vector<double> z = gll_points(k);
+  std::vector<double> cM, cL, cB;
+  cell_matrices(k, z, cM, cL, cB);
+  const int n = k * cells + 1, c1 = k + 1;
+  M.assign((size_t)n * n, 0.0);
+  L.assign((size_t)n * n, 0.0);
+  B.assign((size_t)n * n, 0.0);
+  for (int c = 0; c < cells; ++c)
+    for (int i = 0; i < c1; ++i)
+      for (int j = 0; j < c1; ++j) {
+        size_t o = (size_t)(k * c + i) * n + (k * c + j);
+        M[o] += cM[i * c1 + j];
+        L[o] += cL[i * c1 + j];
+        B[o] += cB[i * c1 + j];
+      }
+  // derivative traces at the cell end points (cell size 1)
+  std::vector<double> d1l(c1), d1r(c1), d2l(c1), d2r(c1);
+  for (int i = 0; i < c1; ++i) {
+    d1l[i] = lagrange(z, i, 0.0, 1);
+    d1r[i] = lagrange(z, i, 1.0, 1);
+    d2l[i] = lagrange(z, i, 0.0, 2);
+    d2r[i] = lagrange(z, i, 1.0, 2);
+  }
+  // face points f = 0..cells: jump = sum of outward derivatives, mean = half sum
+  // (one-sided on the boundary); gamma/h [[.]][[.]] - {.}[[.]] - [[.]]{.}, h = 1
+  for (int f = 0; f <= cells; ++f) {
+    std::vector<int> ids;
+    std::vector<double> J, Mu;
+    const bool interior = (f > 0 && f < cells);
+    if (f > 0) {  // cell f-1 on the left, outward normal +x
+      for (int i = 0; i < c1; ++i) {
+        ids.push_back(k * (f - 1) + i);
+        J.push_back(d1r[i]);
+        Mu.push_back(d2r[i] * (interior ? 0.5 : 1.0));
+      }
+    }
+    if (f < cells) {  // cell f on the right, outward normal -x
+      for (int i = 0; i < c1; ++i) {
+        ids.push_back(k * f + i);
+        J.push_back(-d1l[i]);
+        Mu.push_back(d2l[i] * (interior ? 0.5 : 1.0));
+      }
+    }
+    for (size_t a = 0; a < ids.size(); ++a)
+      for (size_t b = 0; b < ids.size(); ++b)
+        B[(size_t)ids[a] * n + ids[b]] += gamma * J[a] * J[b] - J[a] * Mu[b] - Mu[a] * J[b];
+  }
+}
+
+static void fill_class(const std::vector<double>& full, int n, int k, int cells, int g, double* row) {
+  const int last = k * cells - 1;  // last interior node
+  for (int t = -2 * k; t <= 2 * k; ++t) {
+    int col = g + t;
+    row[t + 2 * k] = (col >= 1 && col <= last) ? full[(size_t)g * n + col] : 0.0;
+  }
+}
+
+static void cholesky_lower(int n, double* A) {
+  // A = L L^T, L overwrites the lower triangle (row-major); upper part zeroed.
+  for (int j = 0; j < n; ++j) {
+    double* rj = A + (size_t)j * n;
+    double s = rj[j];
+    for (int p = 0; p < j; ++p) s -= rj[p] * rj[p];
+    if (!(s > 0.0)) throw std::runtime_error("matrix not positive definite");
+    const double ljj = std::sqrt(s);
+    rj[j] = ljj;
+#pragma omp parallel for schedule(static) if (n > 256)
+    for (int i = j + 1; i < n; ++i) {
+      double* ri = A + (size_t)i * n;
+      double t = ri[j];
+      for (int p = 0; p < j; ++p) t -= ri[p] * rj[p];
+      ri[j] = t / ljj;
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) A[(size_t)i * n + j] = 0.0;
+}
+
+bool spd_inverse(int n, double* A) {
+  try {
+    cholesky_lower(n, A);
+  } catch (...) {
+    return false;
+  }
+  // U = (L^-1)^T, row-major upper triangular: U[i][p] = Linv[p][i]
+  std::vector<double> U((size_t)n * n, 0.0);
+#pragma omp parallel for schedule(dynamic, 8) if (n > 256)
+  for (int j = 0; j < n; ++j) {  // column j of L^-1: forward substitution
+    std::vector<double> x(n, 0.0);
+    for (int i = j; i < n; ++i) {
+      const double* ri = A + (size_t)i * n;
+      double t = (i == j) ? 1.0 : 0.0;
+      for (int p = j; p < i; ++p) t -= ri[p] * x[p];
+      x[i] = t / ri[i];
+    }
+    for (int i = j; i < n; ++i) U[(size_t)j * n + i] = x[i];
+  }
+  // A^-1 = L^-T L^-1: (A^-1)_ij = sum_{p >= max(i,j)} U[i][p] U[j][p]
+#pragma omp parallel for schedule(dynamic, 8) if (n > 256)
+  for (int i = 0; i < n; ++i) {
+    const double* ui = U.data() + (size_t)i * n;
+    for (int j = i; j < n; ++j) {
+      const double* uj = U.data() + (size_t)j * n;
+      double s = 0.0;
+      for (int p = j; p < n; ++p) s += ui[p] * uj[p];
+      A[(size_t)i * n + j] = s;
+      A[(size_t)j * n + i] = s;
+    }
+  }
+  return true;
+}
+
+bool gen_eig(int n, const double* B, const double* M, double* S, double* lambda) {
+  // M = L L^T; C = L^-1 B L^-T; C = Q diag(lambda) Q^T by cyclic Jacobi
+  // rotations; S = L^-T Q.
+  std::vector<double> Lm(M, M + (size_t)n * n);
+  try {
+    cholesky_lower(n, Lm.data());
+  } catch (...) {
+    return false;
+  }
+  auto Lat = [&](int i, int j) { return Lm[(size_t)i * n + j]; };
+  std::vector<double> Y((size_t)n * n), C((size_t)n * n);
+  for (int c = 0; c < n; ++c)  // Y = L^-1 B, column by column
+    for (int i = 0; i < n; ++i) {
+      double t = B[(size_t)i * n + c];
+      for (int p = 0; p < i; ++p) t -= Lat(i, p) * Y[(size_t)p * n + c];
+      Y[(size_t)i * n + c] = t / Lat(i, i);
+    }
+  for (int c = 0; c < n; ++c)  // C = L^-1 Y^T
+    for (int i = 0; i < n; ++i) {
+      double t = Y[(size_t)c * n + i];
+      for (int p = 0; p < i; ++p) t -= Lat(i, p) * C[(size_t)p * n + c];
+      C[(size_t)i * n + c] = t / Lat(i, i);
+    }
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      double s = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
+      C[(size_t)i * n + j] = C[(size_t)j * n + i] = s;
+    }
+  std::vector<double> Q((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double v = C[(size_t)i * n + j] * C[(size_t)i * n + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-32 * tot) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = C[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        double app = C[(size_t)p * n + p], aqq = C[(size_t)q * n + q];
+        double theta = (aqq - app) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int r = 0; r < n; ++r) {  // columns p, q
+          double crp = C[(size_t)r * n + p], crq = C[(size_t)r * n + q];
+          C[(size_t)r * n + p] = c * crp - s * crq;
+          C[(size_t)r * n + q] = s * crp + c * crq;
+        }
+        for (int r = 0; r < n; ++r) {  // rows p, q
+          double cpr = C[(size_t)p * n + r], cqr = C[(size_t)q * n + r];
+          C[(size_t)p * n + r] = c * cpr - s * cqr;
+          C[(size_t)q * n + r] = s * cpr + c * cqr;
+        }
+        for (int r = 0; r < n; ++r) {
+          double qrp = Q[(size_t)r * n + p], qrq = Q[(size_t)r * n + q];
+          Q[(size_t)r * n + p] = c * qrp - s * qrq;
+          Q[(size_t)r * n + q] = s * qrp + c * qrq;
+        }
+      }
+  }
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(),
+            [&](int a, int b) { return C[(size_t)a * n + a] < C[(size_t)b * n + b]; });
+  // S = L^-T Q (back substitution with L^T), columns reordered by eigenvalue
+  for (int jj = 0; jj < n; ++jj) {
+    const int j = order[jj];
+    lambda[jj] = C[(size_t)j * n + j];
+    std::vector<double> x(n);
+    for (int i = n - 1; i >= 0; --i) {
+      double t = Q[(size_t)i * n + j];
+      for (int p = i + 1; p < n; ++p) t -= Lat(p, i) * x[p];
+      x[i] = t / Lat(i, i);
+    }
+    for (int i = 0; i < n; ++i) S[(size_t)i * n + jj] = x[i];
+  }
+  return true;
+}
+
+void build_setup(int k, double gamma, Setup1D& s) {
+  if (k < 2 || k > kMaxK) throw std::runtime_error("degree out of range");
+  s.k = k;
+  s.gamma = gamma;
+  s.z = gll_points(k);
+  cell_matrices(k, s.z, s.cellM, s.cellL, s.cellB);
+  const int nc = n_classes(k), bw = band(k), m = 2 * k - 1;
+  s.tabM.assign(nc * bw, 0.0);
+  s.tabL.assign(nc * bw, 0.0);
+  s.tabB.assign(nc * bw, 0.0);
+  // Reference lines of 7 cells (every canonical row's full band lies inside)
+  // and of 2 cells (the single patch touching both faces).
+  std::vector<double> M7, L7, B7, M2, L2, B2;
+  global_1d(k, gamma, 7, M7, L7, B7);
+  global_1d(k, gamma, 2, M2, L2, B2);
+  const int n7 = 7 * k + 1, n2 = 2 * k + 1;
+  for (int q = 0; q < k; ++q) {  // canonical rows: band -2k..2k away from both faces
+    const int g = 3 * k + q;
+    fill_class(M7, n7, k, 7, g, &s.tabM[q * bw]);
+    fill_class(L7, n7, k, 7, g, &s.tabL[q * bw]);
+    fill_class(B7, n7, k, 7, g, &s.tabB[q * bw]);
+  }
+  for (int g = 1; g <= k; ++g) {  // rows touching x = 0
+    const int c = k + g - 1;
+    fill_class(M7, n7, k, 7, g, &s.tabM[c * bw]);
+    fill_class(L7, n7, k, 7, g, &s.tabL[c * bw]);
+    fill_class(B7, n7, k, 7, g, &s.tabB[c * bw]);
+  }
+  for (int g = 6 * k; g <= 7 * k - 1; ++g) {  // rows touching x = 1
+    const int c = 2 * k + (g - 6 * k);
+    fill_class(M7, n7, k, 7, g, &s.tabM[c * bw]);
+    fill_class(L7, n7, k, 7, g, &s.tabL[c * bw]);
+    fill_class(B7, n7, k, 7, g, &s.tabB[c * bw]);
+  }
+  {  // N = 2, middle vertex g = k touches both faces
+    const int c = 3 * k;
+    fill_class(M2, n2, k, 2, k, &s.tabM[c * bw]);
+    fill_class(L2, n2, k, 2, k, &s.tabL[c * bw]);
+    fill_class(B2, n2, k, 2, k, &s.tabB[c * bw]);
+  }
+  // patch submatrices: nodes (first .. first + m - 1) of the reference line;
+  // patch vertices v = 3 (interior), 1 (left), 6 (right) of 7 cells, 1 of 2 cells
+  struct Src { const std::vector<double>* M; const std::vector<double>* L; const std::vector<double>* B; int n; int first; };
+  const Src src[4] = {{&M7, &L7, &B7, n7, 2 * k + 1}, {&M7, &L7, &B7, n7, 1},
+                      {&M7, &L7, &B7, n7, 5 * k + 1}, {&M2, &L2, &B2, n2, 1}};
+  for (int t = 0; t < 4; ++t) {
+    s.patchM[t].assign(m * m, 0.0);
+    s.patchL[t].assign(m * m, 0.0);
+    s.patchB[t].assign(m * m, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        size_t o = (size_t)(src[t].first + i) * src[t].n + (src[t].first + j);
+        s.patchM[t][i * m + j] = (*src[t].M)[o];
+        s.patchL[t][i * m + j] = (*src[t].L)[o];
+        s.patchB[t][i * m + j] = (*src[t].B)[o];
+      }
+    s.fdmS[t].assign(m * m, 0.0);
+    s.fdmLam[t].assign(m, 0.0);
+    if (!gen_eig(m, s.patchB[t].data(), s.patchM[t].data(), s.fdmS[t].data(), s.fdmLam[t].data()))
+      throw std::runtime_error("generalized eigenproblem failed (B_v not definite: gamma too small?)");
+  }
+  // prolongation: fine nodes of the two fine cells inside a coarse cell
+  s.prolong.assign(2 * k * (k + 1), 0.0);
+  for (int r = 0; r < 2 * k; ++r) {
+    const double xi = (r < k) ? 0.5 * s.z[r] : 0.5 * (1.0 + s.z[r - k]);
+    for (int q = 0; q <= k; ++q) s.prolong[r * (k + 1) + q] = lagrange(s.z, q, xi, 0);
+  }
+}
+
+void patch_matrix(const Setup1D& s, int d, const int* types, bool mixed, std::vector<double>& A) {
+  const int m = 2 * s.k - 1;
+  int sz = 1;
+  for (int a = 0; a < d; ++a) sz *= m;
+  A.assign((size_t)sz * sz, 0.0);
+  // terms: (coefficient, operator per axis: 0 = M, 1 = L, 2 = B)
+  std::vector<std::pair<double, std::vector<int>>> terms;
+  if (d == 2) {
+    terms = {{1.0, {2, 0}}, {1.0, {0, 2}}};
+    if (mixed) terms.push_back({2.0, {1, 1}});
+  } else {
+    terms = {{1.0, {2, 0, 0}}, {1.0, {0, 2, 0}}, {1.0, {0, 0, 2}}};
+    if (mixed) {
+      terms.push_back({2.0, {1, 1, 0}});
+      terms.push_back({2.0, {0, 1, 1}});
+      terms.push_back({2.0, {1, 0, 1}});
+    }
+  }
+  for (int I = 0; I < sz; ++I) {
+    int ii[3] = {I % m, (I / m) % m, I / (m * m)};
+    for (int J = 0; J < sz; ++J) {
+      int jj[3] = {J % m, (J / m) % m, J / (m * m)};
+      double v = 0.0;
+      for (auto& t : terms) {
+        double p = t.first;
+        for (int a = 0; a < d; ++a) {
+          const std::vector<double>* P = t.second[a] == 0 ? &s.patchM[types[a]]
+                                        : t.second[a] == 1 ? &s.patchL[types[a]]
+                                                           : &s.patchB[types[a]];
+          p *= (*P)[ii[a] * m + jj[a]];
+        }
+        v += p;
+      }
+      A[(size_t)I * sz + J] = v;
+    }
+  }
+}
+
+}  // namespace bh

@@ -1,0 +1,308 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
+the same seeded inputs.  Tolerances (relative, infinity norm, from the
+arithmetic: FP64 sums of O(100) terms each carry ~1e-15 relative rounding):
+apply_A and transfers 1e-12, one smoothing step and one V-cycle 1e-10, solves
+reach the same 1e-8 relative residual with iteration counts within +-1."""
+import functools
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import workload  # noqa: E402
+from oracle import assemble, kron, krylov, mg, smoothers  # noqa: E402
+from oracle.patches import LocalSolvers  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def bh():
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device: the -m gpu tests need a GB300")
+    import paper_2412_05082_gb300 as m
+    m.load()
+    return m
+
+
+def cuda(v):
+    return torch.tensor(np.asarray(v), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_A(d, k, N, mixed=True):
+    return assemble.c0ip_matrix(d, k, N, mixed=mixed)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_local(d, k, N, ls):
+    src = oracle_A(d, k, N) if ls == "exact" else oracle_A(d, k, N, False)
+    return LocalSolvers(src, d, k, N)
+
+
+def make_ctx(bh, d, k, L, **kw):
+    return bh.Context(bh.default_params(d, k, L, **kw))
+
+
+APPLY_CASES = [(2, k, N) for k in range(2, 8) for N in (2, 4, 8)] + \
+    [(2, 3, 32), (2, 2, 64), (3, 2, 2), (3, 2, 4), (3, 2, 8), (3, 3, 4), (3, 4, 4), (3, 5, 2),
+     (3, 7, 2)]
+
+
+@pytest.mark.parametrize("d,k,N", APPLY_CASES)
+def test_apply_A(bh, d, k, N):
+    L = workload.level_of(N)
+    with make_ctx(bh, d, k, L) as ctx:
+        n = ctx.num_unknowns(L)
+        x = workload.vector_uniform(n, seed=10 + k)
+        X, Y = cuda(x), torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.apply_A(L, X, Y)
+        ref = oracle_A(d, k, N) @ x
+        assert relerr(host(Y), ref) <= 1e-12
+        # residual mode
+        b = workload.rhs_uniform(n, seed=3)
+        R = torch.empty_like(X)
+        ctx.residual(L, X, cuda(b), R)
+        assert relerr(host(R), b - ref) <= 1e-12
+
+
+def test_apply_A_every_level_of_a_hierarchy(bh):
+    d, k, L = 2, 3, 5
+    with make_ctx(bh, d, k, L) as ctx:
+        for l in range(1, L + 1):
+            n = ctx.num_unknowns(l)
+            x = workload.vector_uniform(n, seed=l)
+            Y = torch.empty(n, dtype=torch.float64, device="cuda")
+            ctx.apply_A(l, cuda(x), Y)
+            assert relerr(host(Y), oracle_A(d, k, 2 ** l) @ x) <= 1e-12
+
+
+@pytest.mark.parametrize("d,k,N", [(2, 2, 8), (2, 3, 4), (2, 7, 4), (3, 2, 4), (3, 3, 4)])
+def test_transfers(bh, d, k, N):
+    L = workload.level_of(N)
+    P = mg.prolongation(d, k, N // 2)
+    with make_ctx(bh, d, k, L) as ctx:
+        nf, nc = ctx.num_unknowns(L), ctx.num_unknowns(L - 1)
+        xc = workload.vector_uniform(nc, 1)
+        xf = workload.vector_uniform(nf, 2)
+        XF = cuda(xf)
+        ctx.prolongate_add(L, cuda(xc), XF)
+        assert relerr(host(XF), xf + P @ xc) <= 1e-12
+        BC = torch.empty(nc, dtype=torch.float64, device="cuda")
+        ctx.restrict(L, cuda(xf), BC)
+        assert relerr(host(BC), P.T @ xf) <= 1e-12
+
+
+SMOOTH_CASES = [
+    (2, 2, 8, "avs", "inexact"), (2, 3, 8, "avs", "inexact"), (2, 5, 4, "avs", "inexact"),
+    (2, 7, 4, "avs", "inexact"), (2, 2, 16, "mvs", "inexact"), (2, 4, 8, "mvs", "inexact"),
+    (2, 6, 4, "mvs", "inexact"), (2, 3, 8, "mvs", "exact"), (2, 4, 4, "avs", "exact"),
+    (3, 2, 4, "avs", "inexact"), (3, 2, 8, "mvs", "inexact"), (3, 3, 4, "mvs", "inexact"),
+    (3, 2, 4, "mvs", "exact"), (2, 3, 2, "mvs", "inexact"), (3, 4, 2, "avs", "inexact"),
+]
+
+
+@pytest.mark.parametrize("d,k,N,kind,ls", SMOOTH_CASES)
+def test_one_smoothing_step(bh, d, k, N, kind, ls):
+    L = workload.level_of(N)
+    A = oracle_A(d, k, N)
+    loc = oracle_local(d, k, N, ls)
+    omega = smoothers.default_omega(kind, d, ls)
+    n = A.shape[0]
+    b = workload.rhs_uniform(n, seed=5)
+    x = workload.vector_uniform(n, seed=6)
+    ref = smoothers.smooth(kind, A, loc, b, x, omega, 1)
+    variants = [bh.MVS_COLORED] if kind == "mvs" else [bh.AVS_ATOMIC, bh.AVS_COLORED]
+    for sm in variants:
+        with make_ctx(bh, d, k, L, smoother=sm, local_solver=bh.EXACT if ls == "exact" else bh.FDM) as ctx:
+            X = cuda(x)
+            ctx.smooth(L, X, cuda(b), 1)
+            assert relerr(host(X) - x, ref - x) <= 1e-10, sm
+
+
+def test_colored_avs_is_deterministic_and_equals_atomic(bh):
+    d, k, L = 2, 3, 4
+    n = (k * 2 ** L - 1) ** d
+    b, x = workload.rhs_uniform(n, 1), workload.vector_uniform(n, 2)
+    outs = []
+    for sm in (bh.AVS_COLORED, bh.AVS_COLORED, bh.AVS_ATOMIC):
+        with make_ctx(bh, d, k, L, smoother=sm) as ctx:
+            X = cuda(x)
+            ctx.smooth(L, X, cuda(b), 2)
+            outs.append(host(X))
+    assert np.array_equal(outs[0], outs[1])
+    assert relerr(outs[2], outs[0]) <= 1e-13
+
+
+@pytest.mark.parametrize("d,k,L,kind,ls", [(2, 2, 3, "mvs", "inexact"), (2, 3, 3, "avs", "inexact"),
+                                          (2, 4, 2, "mvs", "exact"), (3, 2, 3, "mvs", "inexact")])
+def test_one_vcycle(bh, d, k, L, kind, ls):
+    steps = 2 if kind == "avs" else 1
+    H = mg.Hierarchy(d, k, L, smoother=kind, local_solver=ls, pre=steps, post=steps)
+    n = H.A[L].shape[0]
+    b = workload.rhs_uniform(n, 11)
+    x = workload.vector_uniform(n, 12)
+    ref = H.vcycle(L, x.copy(), b)
+    sm = bh.MVS_COLORED if kind == "mvs" else bh.AVS_ATOMIC
+    with make_ctx(bh, d, k, L, smoother=sm, pre_steps=steps, post_steps=steps,
+                  local_solver=bh.EXACT if ls == "exact" else bh.FDM) as ctx:
+        X = cuda(x)
+        ctx.vcycle(L, X, cuda(b))
+        assert relerr(host(X), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("d,k,L,side", [(2, 2, 4, "right"), (2, 3, 4, "right"), (2, 5, 3, "right"),
+                                        (2, 3, 4, "left"), (3, 2, 3, "right"), (3, 3, 2, "left")])
+def test_solve_matches_oracle(bh, d, k, L, side):
+    H = mg.Hierarchy(d, k, L)
+    b = assemble.load_vector(d, k, 2 ** L, assemble.manufactured_f)
+    xr, it_ref, hist, rr_ref = krylov.gmres(H.A[L], b, H.preconditioner, 1e-8, side=side)
+    with make_ctx(bh, d, k, L, gmres_side=bh.LEFT if side == "left" else bh.RIGHT) as ctx:
+        X = torch.empty(len(b), dtype=torch.float64, device="cuda")
+        it, rr = ctx.solve(cuda(b), X, 1e-8, 100)
+    assert abs(it - it_ref) <= 1
+    if side == "right":
+        assert rr <= 1.0001e-8
+    assert relerr(host(X), xr) <= 1e-6
+
+
+@pytest.mark.parametrize("d,k,L", [(2, 2, 5), (2, 3, 5), (2, 4, 4), (3, 2, 3), (3, 3, 3)])
+def test_mixed_precision_solve(bh, d, k, L):
+    """FP32 V-cycle inside FP64 GMRES (Sec. 5.2, shown there for Q2-Q4): the
+    same 1e-8 reduction with at most one more iteration than FP64."""
+    n = (k * 2 ** L - 1) ** d
+    b = workload.rhs_uniform(n, 21)
+    for side in (bh.RIGHT, bh.LEFT):
+        res = {}
+        for prec in (bh.FP64, bh.MIXED_FP32):
+            with make_ctx(bh, d, k, L, precision=prec, gmres_side=side) as ctx:
+                X = torch.empty(n, dtype=torch.float64, device="cuda")
+                res[prec] = ctx.solve(cuda(b), X, 1e-8, 100) + (host(X),)
+        it64, rr64, x64 = res[bh.FP64]
+        it32, rr32, x32 = res[bh.MIXED_FP32]
+        if side == bh.RIGHT:
+            assert rr32 <= 1.0001e-8 and rr64 <= 1.0001e-8
+        assert it32 <= it64 + 1, (side, it32, it64)
+        assert relerr(x32, x64) <= 1e-5
+
+
+def test_mixed_vcycle_error_against_fp64_oracle(bh):
+    d, k, L = 2, 4, 4
+    H = mg.Hierarchy(d, k, L)
+    n = H.A[L].shape[0]
+    b = workload.rhs_uniform(n, 31)
+    ref = H.vcycle(L, np.zeros(n), b)
+    with make_ctx(bh, d, k, L, precision=bh.MIXED_FP32) as ctx:
+        X = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.vcycle(L, X, cuda(b))
+        err = relerr(host(X), ref)
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("d,k,N", [(2, 2, 8), (2, 5, 4), (3, 3, 4)])
+def test_rhs(bh, d, k, N):
+    L = workload.level_of(N)
+    with make_ctx(bh, d, k, L) as ctx:
+        n = ctx.num_unknowns(L)
+        for kind, f in ((bh.RHS_MANUFACTURED, assemble.manufactured_f),
+                        (bh.RHS_PAPER_SINE, assemble.paper_sine_f)):
+            B = torch.empty(n, dtype=torch.float64, device="cuda")
+            ctx.rhs(L, kind, B)
+            assert relerr(host(B), assemble.load_vector(d, k, N, f)) <= 1e-12
+
+
+def test_small_config_end_to_end(bh):
+    """The 8 x 8 Q2 problem: apply, one AVS step and the full solve."""
+    d, k, N = workload.SMALL_2D[0]
+    L = workload.level_of(N)
+    b = assemble.load_vector(d, k, N, assemble.manufactured_f)
+    A = oracle_A(d, k, N)
+    with make_ctx(bh, d, k, L, smoother=bh.AVS_ATOMIC, pre_steps=2, post_steps=2,
+                  gmres_side=bh.RIGHT) as ctx:
+        B = torch.empty(len(b), dtype=torch.float64, device="cuda")
+        ctx.rhs(L, bh.RHS_MANUFACTURED, B)
+        assert relerr(host(B), b) <= 1e-12
+        X = torch.empty_like(B)
+        it, rr = ctx.solve(B, X, 1e-8, 100)
+        assert rr <= 1.0001e-8
+        u = np.linalg.solve(A.toarray(), b)
+        assert relerr(host(X), u) <= 1e-7
+
+
+def test_full_size_apply_and_sampled_avs(bh):
+    """2D Q4 on 512 x 512 cells (the sweep workload): the whole apply against
+    the oracle's Kronecker form, and one AVS step on 64 sampled nodes whose
+    patch solves the oracle computes one by one."""
+    d, k, N = 2, 4, 512
+    L = workload.level_of(N)
+    n1 = k * N - 1
+    with make_ctx(bh, d, k, L, smoother=bh.AVS_ATOMIC) as ctx:
+        n = ctx.num_unknowns(L)
+        x = workload.vector_uniform(n, 1)
+        b = workload.rhs_uniform(n, 2)
+        X, B = cuda(x), cuda(b)
+        Y = torch.empty_like(X)
+        ctx.apply_A(L, X, Y)
+        Aop = kron.KronOperator(d, k, N)
+        Ax = Aop @ x
+        assert relerr(host(Y), Ax) <= 1e-12
+        ctx.smooth(L, X, B, 1)
+        got = host(X)
+    r = b - Ax
+    M1, _, B1 = kron.global_1d(k, N)
+    rng = np.random.default_rng(7)
+    omega = 0.25
+    for idx in rng.integers(0, n, 64):
+        iy, ix = divmod(int(idx), n1)
+        gx, gy = ix + 1, iy + 1
+        expect = x[idx]
+        # patches containing node (gx, gy): vertices v with k(v-1) < g < k(v+1)
+        vxs = [v for v in range(1, N) if k * (v - 1) < gx < k * (v + 1)]
+        vys = [v for v in range(1, N) if k * (v - 1) < gy < k * (v + 1)]
+        for vy in vys:
+            for vx in vxs:
+                sx = np.arange(k * (vx - 1), k * (vx + 1) - 1)
+                sy = np.arange(k * (vy - 1), k * (vy + 1) - 1)
+                Mx, Bx = M1[np.ix_(sx, sx)], B1[np.ix_(sx, sx)]
+                My, By = M1[np.ix_(sy, sy)], B1[np.ix_(sy, sy)]
+                At = np.kron(My, Bx) + np.kron(By, Mx)
+                rv = r.reshape(n1, n1)[np.ix_(sy, sx)].ravel()
+                yv = np.linalg.solve(At, rv).reshape(len(sy), len(sx))
+                expect += omega * yv[iy - sy[0], ix - sx[0]]
+        assert abs(got[idx] - expect) <= 1e-10 * max(abs(expect), np.abs(r).max() * 1e-3)
+
+
+def test_edge_cases(bh):
+    d, k, L = 2, 2, 3
+    with make_ctx(bh, d, k, L) as ctx:
+        n = ctx.num_unknowns(L)
+        X = torch.ones(n, dtype=torch.float64, device="cuda")
+        it, rr = ctx.solve(torch.zeros(n, dtype=torch.float64, device="cuda"), X)
+        assert it == 0 and rr == 0.0 and float(X.abs().max()) == 0.0
+        with pytest.raises(bh.BiharmError):
+            ctx.apply_A(L + 1, X, X.clone())
+        with pytest.raises(bh.BiharmError):
+            ctx.apply_A(L, X, X)          # aliasing is rejected
+        with pytest.raises(ValueError):
+            ctx.apply_A(L, X[:-1], X[:-1].clone())
+        with pytest.raises(bh.BiharmError):
+            ctx.prolongate_add(1, X, X)   # no level below the coarse one
+        bad = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        with pytest.raises(bh.BiharmError):
+            ctx.solve(bad, X)
+        # level 1 (N = 2): one patch; the V-cycle is the exact coarse solve
+        n1 = ctx.num_unknowns(1)
+        b1 = workload.rhs_uniform(n1, 3)
+        X1 = torch.zeros(n1, dtype=torch.float64, device="cuda")
+        ctx.vcycle(1, X1, cuda(b1))
+        assert relerr(host(X1), np.linalg.solve(oracle_A(d, k, 2).toarray(), b1)) <= 1e-12
