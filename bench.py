@@ -1,0 +1,365 @@
+"""Benchmark of the GB300 C0IP biharmonic multigrid (arXiv 2412.05082).
+
+One step = one pass of the whole hot path over the workload: for every
+problem of the 2D sweep (Q2-Q4 on 512^2 cells, Q5-Q7 on 256^2 cells), an
+FP64 MG-GMRES solve to a 1e-8 relative reduction (colored MVS, one pre- and
+one post-smoothing step, fast-diagonalization local solvers, left
+preconditioning: the protocol of Sec. 5.1), which runs apply_A, the residual,
+the patch gather / solve / scatter, the transfers, the V-cycle and GMRES.
+
+value = sum of the paper's DoF counts (kN+1)^2 solved / device time (CUDA
+events), the solve inputs resident in HBM; L2 is flushed (256 MiB write)
+before every timed step.  e2e = the same through bh_solve_host with pinned
+host buffers (copies inside the timed region).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 run one process per GPU (torchrun); the solves are independent
+replicas (weak scaling, no collective on the data path).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workload  # noqa: E402
+
+METRIC = "DoF/s: C0IP apply, patch smoother, MG-GMRES solve to 1e-8; serve p50/p99 latency"
+UNIT = "DoF/s"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 2 DFMA / clk / SM at 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12  # 128 FFMA / clk / SM
+
+
+def config_for(problems, precision="fp64"):
+    return {
+        "workload": "2D C0IP biharmonic sweep (paper sizes): Q2-Q4 on 512^2 and Q5-Q7 on 256^2 "
+                    "cells; MG-GMRES to 1e-8 (colored MVS 1+1, FDM local solver, left "
+                    "preconditioning, restart 50), %s" % precision,
+        "problems": [{"d": d, "k": k, "cells": N, "dofs": workload.paper_dofs(d, k, N)}
+                     for d, k, N in problems],
+        "dof_count": "(kN+1)^d including boundary nodes (the paper's convention)",
+        "rhs": "i.i.d. uniform[-1,1] (PCG64, seed = k)",
+        "l2": "flushed before every timed step (256 MiB write)",
+    }
+
+
+def flop_per_unknown_apply(d, k):
+    """FP64 flops of one apply_A / residual per unknown: the band nonzeros of
+    the sum-factorized sweeps (2 flops per FMA).  Per output cell of k rows the
+    M and L bands hold k^2 + 2k entries and B 3k^2 + 2k (5k + 6 per row for the
+    three together); 2D: one x-split (M, L, B) and one y-combination (B, L, M):
+    2 (5k + 6) FMAs per unknown; 3D: x-split 5k+6, y-mix 8k+12, z 5k+6."""
+    fma = 2 * (5 * k + 6) if d == 2 else (5 * k + 6) + (8 * k + 12) + (5 * k + 6)
+    return 2 * fma
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(budget_s=20.0):
+    """Time the CPU oracle (as it stands) on a bounded sample of the workload in
+    a child process with one BLAS thread: MG-GMRES solves of the same sweep
+    family (2D, k = 2..7, same smoother, local solver and GMRES protocol) at
+    the level N = 16 the oracle finishes in seconds."""
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+import workload
+from oracle import mg, krylov
+t_tot, dofs, done = 0.0, 0, []
+for k in range(2, 8):
+    L = 4
+    H = mg.Hierarchy(2, k, L)
+    n = (k * 2 ** L - 1) ** 2
+    b = workload.rhs_uniform(n, k)
+    t0 = time.perf_counter()
+    x, it, hist, rr = krylov.gmres(H.A[L], b, H.preconditioner, 1e-8, side="left")
+    t_tot += time.perf_counter() - t0
+    dofs += workload.paper_dofs(2, k, 2 ** L)
+    done.append(k)
+    if t_tot > %f:
+        break
+print(json.dumps({"t": t_tot, "dofs": dofs, "ks": done}))
+""" % (ROOT, budget_s)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=600)
+    if res.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + res.stderr.strip().splitlines()[-1][:200]}
+    r = json.loads(res.stdout.strip().splitlines()[-1])
+    return {"value": r["dofs"] / r["t"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "oracle MG-GMRES solves (MVS 1+1, inexact local solvers by dense LU, left "
+                      "preconditioning, 1e-8) of the 2D sweep family at N = 16 cells, k = %s; "
+                      "paper DoF count / CPU time, one thread" % r["ks"],
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle timed as it stands, each step a bounded
+    sample of the workload (2D, k = 2..7, N = 8: one MG-GMRES solve each)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import krylov, mg
+    problems = [(2, k, 8) for k in range(2, 8)]
+    hier = {k: mg.Hierarchy(2, k, 3) for _, k, _ in problems}
+    rhs = {k: workload.rhs_uniform((k * 8 - 1) ** 2, k) for _, k, _ in problems}
+
+    def step():
+        for _, k, _ in problems:
+            H = hier[k]
+            krylov.gmres(H.A[3], rhs[k], H.preconditioner, 1e-8, side="left")
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    dofs = sum(workload.paper_dofs(*p) for p in problems) * args.steps
+    value = dofs / dt
+    sample = ("oracle MG-GMRES solves of the 2D sweep family at N = 8 cells, k = 2..7, per step "
+              "(paper DoF count / CPU time, one thread)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": config_for(workload.SWEEP_2D),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-breakdown", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        # the oracle needs no GPU: keep this process off the devices entirely
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        return run_reference(args)
+
+    # the CPU baseline runs in a child process started before any CUDA call
+    cpu = None
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    import torch
+    import paper_2412_05082_gb300 as bh
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+
+    problems = workload.SWEEP_2D
+    ctxs, rhs, xs, hostb, hostx = [], [], [], [], []
+    for d, k, N in problems:
+        L = workload.level_of(N)
+        ctx = bh.Context(bh.default_params(d, k, L), stream)
+        n = ctx.num_unknowns()
+        b = workload.rhs_uniform(n, k)
+        ctxs.append(ctx)
+        rhs.append(torch.tensor(b, dtype=torch.float64, device=dev))
+        xs.append(torch.empty(n, dtype=torch.float64, device=dev))
+        hostb.append(torch.tensor(b, dtype=torch.float64).pin_memory())
+        hostx.append(torch.empty(n, dtype=torch.float64).pin_memory())
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    iters = {}
+
+    def step():
+        for (d, k, N), ctx, b, x in zip(problems, ctxs, rhs, xs):
+            iters[k] = ctx.solve(b, x, 1e-8, 200)
+
+    def step_host():
+        for ctx, b, x in zip(ctxs, hostb, hostx):
+            ctx.solve_host(b, x, 1e-8, 200)
+
+    def timed(fn, steps):
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return ts
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = bh.kernel_launches()
+    with Clocks(local_rank) as clk:
+        ts = timed(step, args.steps)
+    launches = bh.kernel_launches() - launches0
+    t_total = sum(ts)
+    if dist:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t)
+        dist.barrier()
+    dofs_step = sum(workload.paper_dofs(*p) for p in problems)
+    value = dofs_step * args.steps * world / t_total
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    step_host()
+    te = timed(step_host, args.steps)
+    t_e2e = sum(te)
+    if dist:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t)
+    bytes_h2d = sum(8 * c.num_unknowns() for c in ctxs)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_for(problems),
+        "e2e": {"value": dofs_step * args.steps * world / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": bytes_h2d, "d2h_bytes_per_step": bytes_h2d},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "iterations": {str(k): {"iters": it, "true_relres": rr} for k, (it, rr) in iters.items()},
+    }
+
+    # dominant kernel: the apply_A / residual sweeps (8 per MVS step, 16+ per V-cycle)
+    def time_op(fn, reps=10):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.median(ts)
+
+    roof_k = 4
+    i4 = [p[1] for p in problems].index(roof_k)
+    d, k, N = problems[i4]
+    L = workload.level_of(N)
+    ctx = ctxs[i4]
+    n = ctx.num_unknowns()
+    r = torch.empty(n, dtype=torch.float64, device=dev)
+    t_res = time_op(lambda: ctx.residual(L, xs[i4], rhs[i4], r), 20)
+    flops = flop_per_unknown_apply(d, k) * n
+    achieved = flops / t_res / 1e12
+    result["roofline"] = {
+        "kernel": "residual r = b - A x: sweep_kernel x-split + y-combine (2 launches), 2D Q4 512^2",
+        "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+        "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (derived; no FP64 entry in "
+                       "the measured peaks file)",
+        "flops_per_unknown": flop_per_unknown_apply(d, k), "unknowns": n,
+        "launch_ms": t_res * 1e3,
+    }
+
+    if not args.no_breakdown:
+        bd = {}
+        for (d, k, N), ctx, b, x in zip(problems, ctxs, rhs, xs):
+            L = workload.level_of(N)
+            dofs = workload.paper_dofs(d, k, N)
+            n = ctx.num_unknowns()
+            y = torch.empty(n, dtype=torch.float64, device=dev)
+            row = {"dofs": dofs, "solve_iters": iters[k][0]}
+            row["apply"] = dofs / time_op(lambda: ctx.apply_A(L, b, y))
+            for sm, name in ((bh.AVS_ATOMIC, "avs_atomic"), (bh.AVS_COLORED, "avs_colored"),
+                             (bh.MVS_COLORED, "mvs")):
+                with bh.Context(bh.default_params(d, k, L, smoother=sm), stream) as c2:
+                    row[name + "_step"] = dofs / time_op(lambda: c2.smooth(L, y, b, 1), 5)
+            row["solve_fp64"] = dofs / time_op(lambda: ctx.solve(b, x, 1e-8, 200), 3)
+            if k <= 4:  # the paper's mixed-precision range (Q2-Q4, Sec. 5.2)
+                with bh.Context(bh.default_params(d, k, L, precision=bh.MIXED_FP32), stream) as c2:
+                    itm = c2.solve(b, x, 1e-8, 200, raise_on_noconv=False)
+                    row["solve_mixed"] = dofs / time_op(
+                        lambda: c2.solve(b, x, 1e-8, 200, raise_on_noconv=False), 3)
+                    row["mixed_iters"] = itm[0]
+            bd["k%d" % k] = row
+        result["breakdown_dofs_per_s"] = bd
+    if cpu is not None:
+        result["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    for c in ctxs:
+        c.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
