@@ -75,7 +75,7 @@ typedef struct {
   int post_steps;
   double omega;      /* damping; <= 0: Sec. 5.1 defaults (AVS 1/4 in 2D, 0.1 in 3D
                         (1/8 exact); MVS 1 in 2D, 0.7 in 3D) */
-  int precision;     /* BH_FP64 | BH_MIXED_FP32 */
+  int precision;     /* BH_FP64 | BH_MIXED_FP32 (needs gmres_side = BH_RIGHT) */
   int gmres_restart; /* restart length m (default 50) */
   int gmres_side;    /* BH_LEFT (default) | BH_RIGHT */
   int coarse;        /* BH_COARSE_EXACT (default) | BH_COARSE_SMOOTH */

@@ -475,6 +475,10 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
   if (p.pre_steps < 0 || p.post_steps < 0) return fail(BH_EINVAL, "negative smoothing steps");
   if (p.gmres_side < 0 || p.gmres_side > 1) return fail(BH_EINVAL, "unknown GMRES side");
   if (p.coarse < 0 || p.coarse > 1) return fail(BH_EINVAL, "unknown coarse solver");
+  if (p.precision == BH_MIXED_FP32 && p.gmres_side == BH_LEFT)
+    return fail(BH_EINVAL,
+                "the FP32 V-cycle is not a fixed linear operator (its rounding varies): mixed "
+                "precision needs the flexible right-preconditioned GMRES, gmres_side = BH_RIGHT");
   const int d = p.dim, k = p.degree;
   if (!(p.gamma > 0.0)) p.gamma = k * (k + 1.0);
   if (!(p.omega > 0.0)) {

@@ -178,22 +178,28 @@ def test_solve_matches_oracle(bh, d, k, L, side):
 
 @pytest.mark.parametrize("d,k,L", [(2, 2, 5), (2, 3, 5), (2, 4, 4), (3, 2, 3), (3, 3, 3)])
 def test_mixed_precision_solve(bh, d, k, L):
-    """FP32 V-cycle inside FP64 GMRES (Sec. 5.2, shown there for Q2-Q4): the
-    same 1e-8 reduction with at most one more iteration than FP64."""
+    """FP32 V-cycle inside flexible FP64 GMRES (Sec. 5.2, shown there for
+    Q2-Q4): the same 1e-8 true residual, at most one more iteration than FP64,
+    and the same solution (both within 1e-6 of the dense solve)."""
     n = (k * 2 ** L - 1) ** d
     b = workload.rhs_uniform(n, 21)
-    for side in (bh.RIGHT, bh.LEFT):
-        res = {}
-        for prec in (bh.FP64, bh.MIXED_FP32):
-            with make_ctx(bh, d, k, L, precision=prec, gmres_side=side) as ctx:
-                X = torch.empty(n, dtype=torch.float64, device="cuda")
-                res[prec] = ctx.solve(cuda(b), X, 1e-8, 100) + (host(X),)
-        it64, rr64, x64 = res[bh.FP64]
-        it32, rr32, x32 = res[bh.MIXED_FP32]
-        if side == bh.RIGHT:
-            assert rr32 <= 1.0001e-8 and rr64 <= 1.0001e-8
-        assert it32 <= it64 + 1, (side, it32, it64)
-        assert relerr(x32, x64) <= 1e-5
+    exact = np.linalg.solve(oracle_A(d, k, 2 ** L).toarray(), b)
+    res = {}
+    for prec in (bh.FP64, bh.MIXED_FP32):
+        with make_ctx(bh, d, k, L, precision=prec, gmres_side=bh.RIGHT) as ctx:
+            X = torch.empty(n, dtype=torch.float64, device="cuda")
+            res[prec] = ctx.solve(cuda(b), X, 1e-8, 100) + (host(X),)
+    it64, rr64, x64 = res[bh.FP64]
+    it32, rr32, x32 = res[bh.MIXED_FP32]
+    assert rr32 <= 1.0001e-8 and rr64 <= 1.0001e-8
+    assert it32 <= it64 + 1, (it32, it64)
+    assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
+
+
+def test_mixed_precision_requires_flexible_gmres(bh):
+    with pytest.raises(bh.BiharmError) as e:
+        make_ctx(bh, 2, 2, 3, precision=bh.MIXED_FP32, gmres_side=bh.LEFT)
+    assert "flexible" in str(e.value)
 
 
 def test_mixed_vcycle_error_against_fp64_oracle(bh):
@@ -202,7 +208,7 @@ def test_mixed_vcycle_error_against_fp64_oracle(bh):
     n = H.A[L].shape[0]
     b = workload.rhs_uniform(n, 31)
     ref = H.vcycle(L, np.zeros(n), b)
-    with make_ctx(bh, d, k, L, precision=bh.MIXED_FP32) as ctx:
+    with make_ctx(bh, d, k, L, precision=bh.MIXED_FP32, gmres_side=bh.RIGHT) as ctx:
         X = torch.zeros(n, dtype=torch.float64, device="cuda")
         ctx.vcycle(L, X, cuda(b))
         err = relerr(host(X), ref)
