@@ -172,6 +172,29 @@ bh_status bh_setup_1d(int degree, double gamma, int cells, int which, double* ou
  * m = 2k - 1, with S^T M_v S = I and S^T B_v S = diag(lambda). */
 bh_status bh_setup_fdm(int degree, double gamma, int type, double* S, double* lambda);
 
+/* y = A_l x like bh_apply_A, for callers that cannot allocate device memory:
+ * for example a plugin inside a framework that owns every device allocation
+ * and forbids allocation while it executes, or a latency-critical loop that
+ * cannot afford the synchronization of cudaMalloc.  The paper has no
+ * counterpart; it is a deployment variant of the apply_A kernel.
+ *  - Needs no context and allocates nothing: the operator tables are built on
+ *    the host stack per call and the sweep intermediates live in one static
+ *    device array of 64 MiB (8 Mi doubles) that every GPU loading the library
+ *    holds until the process exits.
+ *  - Size limit: 3 (2D) or 6 (3D) times n^d must fit in that array, i.e. at
+ *    most 2,796,202 unknowns in 2D and 1,398,101 in 3D, n = k 2^level - 1;
+ *    larger problems fail with BH_EINVAL and a message naming the limit.
+ *  - dim, degree, level, gamma as in bh_params (gamma <= 0: k(k+1)); x_dev,
+ *    y_dev: n^d FP64 device values, caller-owned, not aliased; stream: the
+ *    cudaStream_t to enqueue on (asynchronous).
+ *  - Every call shares the array: calls whose kernels may overlap on the GPU
+ *    (other streams, other host threads) race and must be serialized by the
+ *    caller.  Nothing in the array needs to start at zero.
+ *  - The first call on a device resolves the array's device address (with
+ *    that device current); make that first call before any stream capture. */
+bh_status bh_apply_A_noalloc(int dim, int degree, int level, double gamma,
+                             const double* x_dev, double* y_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

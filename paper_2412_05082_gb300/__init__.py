@@ -63,6 +63,7 @@ SIGNATURES = {
     "bh_kernel_launches": (_c.c_longlong, []),
     "bh_setup_1d": (_I, [_I, _D, _I, _I, _P]),
     "bh_setup_fdm": (_I, [_I, _D, _I, _P, _P]),
+    "bh_apply_A_noalloc": (_I, [_I, _I, _I, _D, _P, _P, _P]),
 }
 
 _lib = None
@@ -124,6 +125,17 @@ def setup_fdm(degree, gamma, ptype):
     lam = np.zeros(m)
     _check(load().bh_setup_fdm(degree, gamma, ptype, S.ctypes.data, lam.ctypes.data))
     return S, lam
+
+
+def apply_A_noalloc(dim, degree, level, gamma, x, y, stream=None):
+    """y = A_level x without any device allocation (static scratch array
+    shared by all calls: serialize calls that could overlap on the GPU)."""
+    import torch
+    n = (degree * 2 ** level - 1) ** dim
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load().bh_apply_A_noalloc(dim, degree, level, gamma, _dev(x, n, "x"),
+                                     _dev(y, n, "y"), ctypes.c_void_p(stream.cuda_stream)))
 
 
 def _dev(t, n, name):

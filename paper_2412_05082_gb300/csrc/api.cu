@@ -50,6 +50,11 @@ struct Level {
 
 }  // namespace
 
+namespace bh {
+// message returned by bh_last_error() on this thread (used by noalloc.cu)
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace bh
+
 struct bh_ctx {
   bh_params p{};
   cudaStream_t st = nullptr;
