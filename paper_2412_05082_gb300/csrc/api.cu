@@ -171,7 +171,13 @@ bh_status smooth_t(bh_ctx* c, int l, T* x, const T* b, int steps, bool x_zero) {
   const int d = c->p.dim, nc = c->ncolors();
   for (int s = 0; s < steps; ++s) {
     const bool zero = x_zero && s == 0;
-    if (c->p.smoother == BH_MVS_COLORED) {
+    if (c->p.smoother == BH_MVS_COLORED && d == 2 && c->p.local_solver == BH_FDM) {
+      // fused kernel: local residual, fast diagonalization and update per patch
+      for (int col = 0; col < nc; ++col)
+        CK(Ops<T>::mvs_color(TypeOf<T>::tab(c), L.g, x, b, L.verts + L.coff[col],
+                             L.coff[col + 1] - L.coff[col], L.ascale, c->p.omega * L.pscale,
+                             c->st));
+    } else if (c->p.smoother == BH_MVS_COLORED) {
       for (int col = 0; col < nc; ++col) {
         const T* r = b;
         if (!(zero && col == 0)) {
@@ -544,11 +550,17 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
     const int Nm = L.g.N - 1;
     const int64_t nv = ipow64(Nm, d);
     std::vector<int> ids[16];
+    // inside a color: patches away from the boundary first, then the rest, so
+    // that thread blocks of the patch kernels see one code path
+    std::vector<int> edge[16];
     for (int64_t vid = 0; vid < nv; ++vid) {
       int v[3] = {(int)(vid % Nm) + 1, (int)((vid / Nm) % Nm) + 1,
                   d == 3 ? (int)(vid / ((int64_t)Nm * Nm)) + 1 : 0};
-      ids[color_of(v, d)].push_back((int)vid);
+      bool inner = true;
+      for (int a = 0; a < d; ++a) inner &= v[a] >= 2 && v[a] <= Nm - 1;
+      (inner ? ids : edge)[color_of(v, d)].push_back((int)vid);
     }
+    for (int col = 0; col < 16; ++col) ids[col].insert(ids[col].end(), edge[col].begin(), edge[col].end());
     std::vector<int> all;
     all.reserve(nv);
     for (int col = 0; col < c->ncolors(); ++col) {

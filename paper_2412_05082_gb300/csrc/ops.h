@@ -41,6 +41,12 @@ struct Ops {
                                const int* verts, int count, double scale, bool atomic,
                                cudaStream_t st);
 
+  // One color of the colored MVS, fused (2D, fast diagonalization): for every
+  // patch v in verts, x_v += pscale * A~_v,ref^-1 R_v (b - ascale * A_ref x).
+  static cudaError_t mvs_color(const void* tab, const LevelGeom& g, T* x, const T* b,
+                               const int* verts, int count, double ascale, double pscale,
+                               cudaStream_t st);
+
   // x += scale * sum_{v in verts} R_v^T Ainv[combo(v)] R_v r  (dense exact inverse;
   // Ainv holds 4^d slots of m^d x m^d matrices, slot = sum_a type_a 4^a).
   static cudaError_t patch_exact(const LevelGeom& g, const T* Ainv, const T* r, T* x,

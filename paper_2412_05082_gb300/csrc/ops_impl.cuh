@@ -7,12 +7,14 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "mvs.cuh"
 
 namespace bh {
 
 template <typename T, int K>
 struct HostTables {
   Tables<T, K> t;
+  MvsTab<T, K> mvs;  // operator + FDM tables for the fused MVS kernel
   T* dinv = nullptr;  // device, 4^d slots x m^d reciprocals of the eigenvalue sums
   int d = 0;
 };
@@ -36,6 +38,8 @@ static void* make_tables_k(const Setup1D& s, int d) {
   }
   for (int r = 0; r < 2 * K; ++r)
     for (int q = 0; q <= K; ++q) h->t.xfer.P[r][q] = (T)s.prolong[r * (K + 1) + q];
+  h->mvs.op = h->t.op;
+  h->mvs.fdm = h->t.fdm;
   // reciprocal eigenvalue sums per type combination (FP64, then converted)
   int md = 1, slots = 1;
   for (int a = 0; a < d; ++a) {
@@ -219,6 +223,49 @@ cudaError_t Ops<T>::patch_fdm(const void* tab, const LevelGeom& g, const T* r, T
     BH_K_DISPATCH(g.k, BH_CALL)
 #undef BH_CALL
   }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int K>
+static cudaError_t mvs_color_k(const void* tabp, const LevelGeom& g, T* x, const T* b,
+                               const int* verts, int count, double ascale, double pscale,
+                               cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const auto* h = static_cast<const HostTables<T, K>*>(tabp);
+  MvsArgs<T> a{};
+  a.x = x;
+  a.b = b;
+  a.verts = verts;
+  a.count = count;
+  a.N = g.N;
+  a.n = g.n;
+  a.ascale = ascale;
+  a.pscale = pscale;
+  a.dinv = h->dinv;
+  using C = Mvs2Cfg<T, K>;
+  // patches per block: enough blocks for two waves on 152 SMs, at most PB_MAX
+  int pb = (count + 2 * 152 - 1) / (2 * 152);
+  pb = pb < 1 ? 1 : (pb > C::PB_MAX ? C::PB_MAX : pb);
+  a.pb = pb;
+  // opt in to the dynamic shared memory once per instantiation (thread-safe static init)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      mvs2_color_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)C::smem_bytes(C::PB_MAX));
+  if (attr != cudaSuccess) return attr;
+  mvs2_color_kernel<T, K><<<(unsigned)((count + pb - 1) / pb), 256, C::smem_bytes(pb), st>>>(
+      h->mvs, a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::mvs_color(const void* tab, const LevelGeom& g, T* x, const T* b,
+                              const int* verts, int count, double ascale, double pscale,
+                              cudaStream_t st) {
+  if (g.d != 2) return cudaErrorInvalidValue;
+#define BH_CALL(KK) return mvs_color_k<T, KK>(tab, g, x, b, verts, count, ascale, pscale, st)
+  BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
   return cudaErrorInvalidValue;
 }
 
