@@ -17,8 +17,8 @@
 //   x-split: T_M on the 4k+1 window rows, T_L and T_B on the 2k+1 middle rows
 //   y-combine: m^2 residual values, (5k+6) FMAs each
 //   FDM: 4 m^3 FMAs + m^2 scalings
-// Every stage is split into single output points; a warp's points share the
-// row position q inside the cell, so the band loops are uniform and unrolled.
+// Every stage is split into half-lines or single points so that all threads of
+// a warp run the same FP64 instruction stream.
 #pragma once
 #include "kernels.cuh"
 
@@ -68,37 +68,74 @@ __device__ __forceinline__ T band_dot(const T* c, const T* v, int stride) {
   return s;
 }
 
-template <typename T, int K, int Q>
-__device__ __forceinline__ void xsplit_point(const T* sM, const T* sL, const T* sB, int cls,
-                                             const T* xr, T* tm, T* tl, T* tb, bool mid) {
+// Half-lines: the 2k-1 patch positions along an axis split into half 0 =
+// positions 1..k (the k-1 nodes inside cell v-1 and the vertex) and half 1 =
+// positions k+1..2k-1 (inside cell v).  A thread handles one half-line with
+// its row positions q unrolled at compile time, so all threads of a warp run
+// the same FP64 instruction stream (masked lanes would still occupy the FP64
+// pipe).  cls(pos) is q for patches away from the boundary and the row class
+// of the global node otherwise.
+template <int K, int HALF>
+struct Half {
+  static constexpr int J0 = HALF == 0 ? 1 : K + 1;
+  static constexpr int J1 = HALF == 0 ? K : 2 * K - 1;
+};
+
+// T_P[pos] = (P x)(pos) along a window row for P = M (OPS = 1) or P = L, B (OPS = 2)
+template <typename T, int K, int HALF, int OPS>
+__device__ __forceinline__ void xsplit_half(const T* sM, const T* sL, const T* sB, bool canon,
+                                            int g0, int N, const T* xr, T* o0, T* o1) {
   constexpr int BW = 4 * K + 1;
-  *tm = band_dot<T, K, 0, Q>(sM + cls * BW, xr, 1);
-  if (mid) {
-    *tl = band_dot<T, K, 1, Q>(sL + cls * BW, xr, 1);
-    *tb = band_dot<T, K, 2, Q>(sB + cls * BW, xr, 1);
+#pragma unroll
+  for (int j = Half<K, HALF>::J0; j <= Half<K, HALF>::J1; ++j) {
+    const int q = j % K;
+    const int cls = canon ? q : row_class<K>(g0 + j, N);
+    if (OPS == 1) {
+      T s = T(0);
+#pragma unroll
+      for (int t = band_lo(0, j % K, K); t <= band_hi(0, j % K, K); ++t)
+        s = fma(sM[cls * BW + t + 2 * K], xr[j + t], s);
+      o0[j - 1] = s;
+    } else {
+      T sl = T(0), sb = T(0);
+#pragma unroll
+      for (int t = band_lo(1, j % K, K); t <= band_hi(1, j % K, K); ++t)
+        sl = fma(sL[cls * BW + t + 2 * K], xr[j + t], sl);
+#pragma unroll
+      for (int t = band_lo(2, j % K, K); t <= band_hi(2, j % K, K); ++t)
+        sb = fma(sB[cls * BW + t + 2 * K], xr[j + t], sb);
+      o0[j - 1] = sl;
+      o1[j - 1] = sb;
+    }
   }
 }
 
-template <typename T, int K, int Q>
-__device__ __forceinline__ T ycombine_point(const T* sM, const T* sL, const T* sB, int cls,
-                                            const T* cm, const T* cl, const T* cb, int stride) {
-  constexpr int BW = 4 * K + 1;
-  return band_dot<T, K, 2, Q>(sB + cls * BW, cm, stride) +
-         T(2) * band_dot<T, K, 1, Q>(sL + cls * BW, cl, stride) +
-         band_dot<T, K, 0, Q>(sM + cls * BW, cb, stride);
-}
-
-// compile-time dispatch over the row position q = 0..K-1 (uniform per warp)
-#define BH_Q_SWITCH(q, CALL)                         \
-  switch (q) {                                       \
-    case 0: CALL(0); break;                          \
-    case 1: if constexpr (K > 1) { CALL(1); } break; \
-    case 2: if constexpr (K > 2) { CALL(2); } break; \
-    case 3: if constexpr (K > 3) { CALL(3); } break; \
-    case 4: if constexpr (K > 4) { CALL(4); } break; \
-    case 5: if constexpr (K > 5) { CALL(5); } break; \
-    case 6: if constexpr (K > 6) { CALL(6); } break; \
+// r_i = b_i - ascale (B T_M + 2 L T_L + M T_B)_i along a patch column; cm = T_M
+// column at window row K (patch position 0), cl, cb = T_L, T_B columns at their
+// row 0 (window row K), stride M between rows; bcol = b at patch position 0 of
+// the column (stride n), rcol = residual column (stride M).
+template <typename T, int K, int HALF>
+__device__ __forceinline__ void ycombine_half(const T* sM, const T* sL, const T* sB, bool canon,
+                                              int g0, int N, const T* cm, const T* cl,
+                                              const T* cb, const T* bcol, int64_t n, T asc,
+                                              T* rcol) {
+  constexpr int BW = 4 * K + 1, M = 2 * K - 1;
+#pragma unroll
+  for (int i = Half<K, HALF>::J0; i <= Half<K, HALF>::J1; ++i) {
+    const int q = i % K;
+    const int cls = canon ? q : row_class<K>(g0 + i, N);
+    T sb = T(0), sl = T(0), sm = T(0);
+#pragma unroll
+    for (int t = band_lo(2, i % K, K); t <= band_hi(2, i % K, K); ++t)
+      sb = fma(sB[cls * BW + t + 2 * K], cm[(i + t) * M], sb);
+#pragma unroll
+    for (int t = band_lo(0, i % K, K); t <= band_hi(0, i % K, K); ++t) {
+      sl = fma(sL[cls * BW + t + 2 * K], cl[(i + t) * M], sl);
+      sm = fma(sM[cls * BW + t + 2 * K], cb[(i + t) * M], sm);
+    }
+    rcol[(i - 1) * M] = bcol[(int64_t)(i - 1) * n] - asc * (sb + T(2) * sl + sm);
   }
+}
 
 template <typename T, int K>
 __global__ void __launch_bounds__(256) mvs2_color_kernel(const __grid_constant__ MvsTab<T, K> tab,
@@ -149,39 +186,48 @@ __global__ void __launch_bounds__(256) mvs2_color_kernel(const __grid_constant__
                                                        : T(0);
   }
   __syncthreads();
-  // x-split, one point (patch column j, patch p, window row wy) per item; j outermost
-  for (int e = threadIdx.x; e < M * np * W; e += blockDim.x) {
-    const int wy = e % W, p = (e / W) % np, j = e / (W * np) + 1;
-    const int q = j % K;
-    const int gx = K * (sV[p][0] - 1) + j;
-    const int cls = sTy[p][0] == 0 ? q : row_class<K>(gx, N);
-    const bool mid = wy >= K && wy <= 3 * K;
-    const int r = mid ? wy - K : 0;
-    const T* xr = sX + (p * W + wy) * W + K + j;
-    T* tm = sTM + (p * W + wy) * M + (j - 1);
-    T* tl = sTL + (p * WM + r) * M + (j - 1);
-    T* tb = sTB + (p * WM + r) * M + (j - 1);
-#define BH_CALL(QQ) xsplit_point<T, K, QQ>(sM, sL, sB, cls, xr, tm, tl, tb, mid)
-    BH_Q_SWITCH(q, BH_CALL)
-#undef BH_CALL
+  // x-split: T_M on every window row, one half-line (half, patch, row) per item
+  for (int e = threadIdx.x; e < 2 * np * W; e += blockDim.x) {
+    const int half = e / (np * W), p = (e / W) % np, wy = e % W;
+    const T* xr = sX + (p * W + wy) * W + K;  // xr[j] = window column K + j
+    T* tm = sTM + (p * W + wy) * M;
+    const bool canon = sTy[p][0] == 0;
+    const int g0 = K * (sV[p][0] - 1);       // global node of patch position j: g0 + j
+    if (half == 0)
+      xsplit_half<T, K, 0, 1>(sM, sL, sB, canon, g0, N, xr, tm, nullptr);
+    else
+      xsplit_half<T, K, 1, 1>(sM, sL, sB, canon, g0, N, xr, tm, nullptr);
+  }
+  // T_L and T_B on the 2k+1 middle window rows
+  for (int e = threadIdx.x; e < 2 * np * WM; e += blockDim.x) {
+    const int half = e / (np * WM), p = (e / WM) % np, r = e % WM;
+    const T* xr = sX + (p * W + K + r) * W + K;
+    T* tl = sTL + (p * WM + r) * M;
+    T* tb = sTB + (p * WM + r) * M;
+    const bool canon = sTy[p][0] == 0;
+    const int g0 = K * (sV[p][0] - 1);
+    if (half == 0)
+      xsplit_half<T, K, 0, 2>(sM, sL, sB, canon, g0, N, xr, tl, tb);
+    else
+      xsplit_half<T, K, 1, 2>(sM, sL, sB, canon, g0, N, xr, tl, tb);
   }
   __syncthreads();
-  // y-combination and residual r = b - A x on the patch nodes; patch row i outermost
+  // y-combination and residual r = b - A x on the patch nodes, one half-column per item
   const T asc = (T)a.ascale;
-  for (int e = threadIdx.x; e < M * np * M; e += blockDim.x) {
-    const int j = e % M, p = (e / M) % np, i = e / (M * np) + 1;
-    const int q = i % K;
-    const int gy = K * (sV[p][1] - 1) + i;
-    const int cls = sTy[p][1] == 0 ? q : row_class<K>(gy, N);
-    const T* cm = sTM + (p * W + K + i) * M + j;
-    const T* cl = sTL + (p * WM + i) * M + j;
-    const T* cb = sTB + (p * WM + i) * M + j;
-    T y = T(0);
-#define BH_CALL(QQ) y = ycombine_point<T, K, QQ>(sM, sL, sB, cls, cm, cl, cb, M)
-    BH_Q_SWITCH(q, BH_CALL)
-#undef BH_CALL
+  for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
+    const int half = e / (np * M), p = (e / M) % np, j = e % M;
+    const T* cm = sTM + (p * W + K) * M + j;
+    const T* cl = sTL + (p * WM) * M + j;
+    const T* cb = sTB + (p * WM) * M + j;
+    const bool canon = sTy[p][1] == 0;
+    const int g0 = K * (sV[p][1] - 1);
     const int gx = K * (sV[p][0] - 1) + j + 1;
-    sR[(p * M + (i - 1)) * M + j] = a.b[(int64_t)(gy - 1) * n + (gx - 1)] - asc * y;
+    const T* bcol = a.b + (int64_t)g0 * n + (gx - 1);  // b at patch position 1 (global row g0 + 1)
+    T* rcol = sR + p * M * M + j;
+    if (half == 0)
+      ycombine_half<T, K, 0>(sM, sL, sB, canon, g0, N, cm, cl, cb, bcol, n, asc, rcol);
+    else
+      ycombine_half<T, K, 1>(sM, sL, sB, canon, g0, N, cm, cl, cb, bcol, n, asc, rcol);
   }
   __syncthreads();
   // fast diagonalization: F = R S_x (rows), R = S_y^T F scaled (columns)
