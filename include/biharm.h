@@ -172,6 +172,43 @@ bh_status bh_setup_1d(int degree, double gamma, int cells, int which, double* ou
  * m = 2k - 1, with S^T M_v S = I and S^T B_v S = diag(lambda). */
 bh_status bh_setup_fdm(int degree, double gamma, int type, double* S, double* lambda);
 
+/* ---- batched form (no counterpart in the paper: a deployment form of the
+ * same solver) ------------------------------------------------------------
+ * Many independent 2D problems with their own degree and level, solved
+ * together.  Every level operation of their V-cycles runs as ONE launch over
+ * all problems (a work list of (problem, range) entries dispatched on the
+ * degree); the patch work of one color is one persistent launch over the
+ * tiles of all problems; the lockstep V-cycle is captured once as a CUDA
+ * graph; GMRES (left preconditioning) runs in lockstep with one host
+ * synchronization per iteration for the whole batch.  Each problem follows
+ * the arithmetic of its own context, so its result matches bh_solve on the
+ * same parameters up to rounding order. */
+typedef struct bh_batch bh_batch;
+
+/* count problems, params[i] each: dim 2, BH_MVS_COLORED, BH_FDM, BH_FP64,
+ * BH_COARSE_EXACT, BH_LEFT (BH_EINVAL otherwise).  Allocates every hierarchy,
+ * builds the work lists and captures the V-cycle graph.  Synchronous. */
+bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_batch** out);
+bh_status bh_batch_destroy(bh_batch* batch);
+
+/* Tile shape of the patch kernel for one degree: patches per thread block
+ * (1..32, bounded by the shared-memory budget).  Rebuilds the work lists and
+ * re-captures the graph.  Used by the autotuner. */
+bh_status bh_batch_set_tile(bh_batch* batch, int degree, int patches_per_block);
+
+/* Mean device time (ms, CUDA events) of one batched V-cycle graph launch on
+ * the current right-hand sides, over reps launches after one warm-up. */
+bh_status bh_batch_vcycle_time(bh_batch* batch, int reps, double* ms);
+
+/* Solve all problems: b_dev[i], x_dev[i] are host arrays of device pointers
+ * (n_i FP64 values each).  iters[i], relres[i] (true relative residual)
+ * receive each problem's result.  BH_ENOCONV if any problem missed rtol. */
+bh_status bh_batch_solve(bh_batch* batch, const double* const* b_dev, double* const* x_dev,
+                         double rtol, int maxit, int* iters, double* relres);
+
+/* Kernel and graph launches issued by the batch so far. */
+bh_status bh_batch_stats(const bh_batch* batch, long long* launches);
+
 /* y = A_l x like bh_apply_A, for callers that cannot allocate device memory:
  * for example a plugin inside a framework that owns every device allocation
  * and forbids allocation while it executes, or a latency-critical loop that

@@ -64,6 +64,12 @@ SIGNATURES = {
     "bh_setup_1d": (_I, [_I, _D, _I, _I, _P]),
     "bh_setup_fdm": (_I, [_I, _D, _I, _P, _P]),
     "bh_apply_A_noalloc": (_I, [_I, _I, _I, _D, _P, _P, _P]),
+    "bh_batch_create": (_I, [_c.POINTER(Params), _I, _P, _c.POINTER(_P)]),
+    "bh_batch_destroy": (_I, [_P]),
+    "bh_batch_set_tile": (_I, [_P, _I, _I]),
+    "bh_batch_vcycle_time": (_I, [_P, _I, _c.POINTER(_D)]),
+    "bh_batch_solve": (_I, [_P, _P, _P, _D, _I, _P, _P]),
+    "bh_batch_stats": (_I, [_P, _c.POINTER(_c.c_longlong)]),
 }
 
 _lib = None
@@ -244,3 +250,64 @@ class Context:
         buf = ctypes.create_string_buffer(4096)
         _check(load().bh_stats(self.handle, buf, len(buf)))
         return json.loads(buf.value.decode())
+
+
+class Batch:
+    """Many independent 2D problems solved together (batched form): one launch
+    per level operation over all problems, the lockstep V-cycle as a CUDA
+    graph, lockstep GMRES."""
+
+    def __init__(self, params_list, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.params = list(params_list)
+        arr = (Params * len(self.params))(*self.params)
+        h = ctypes.c_void_p()
+        _check(load().bh_batch_create(arr, len(self.params), ctypes.c_void_p(stream.cuda_stream),
+                                      ctypes.byref(h)))
+        self._h = h
+
+    def sizes(self):
+        return [(p.degree * 2 ** p.level - 1) ** p.dim for p in self.params]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(load().bh_batch_destroy(self._h))
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_tile(self, degree, patches_per_block):
+        _check(load().bh_batch_set_tile(self._h, degree, patches_per_block))
+
+    def vcycle_time(self, reps=5):
+        ms = ctypes.c_double()
+        _check(load().bh_batch_vcycle_time(self._h, reps, ctypes.byref(ms)))
+        return ms.value
+
+    def launches(self):
+        n = ctypes.c_longlong()
+        _check(load().bh_batch_stats(self._h, ctypes.byref(n)))
+        return n.value
+
+    def solve(self, bs, xs, rtol=1e-8, maxit=50, raise_on_noconv=True):
+        P = len(self.params)
+        sizes = self.sizes()
+        bp = (ctypes.c_void_p * P)(*[_dev(b, n, "b").value for b, n in zip(bs, sizes)])
+        xp = (ctypes.c_void_p * P)(*[_dev(x, n, "x").value for x, n in zip(xs, sizes)])
+        it = (ctypes.c_int * P)()
+        rr = (ctypes.c_double * P)()
+        st = load().bh_batch_solve(self._h, ctypes.cast(bp, ctypes.c_void_p),
+                                   ctypes.cast(xp, ctypes.c_void_p), rtol, maxit,
+                                   ctypes.cast(it, ctypes.c_void_p), ctypes.cast(rr, ctypes.c_void_p))
+        if st != BH_ENOCONV or raise_on_noconv:
+            _check(st)
+        return list(it), list(rr)

@@ -1,0 +1,87 @@
+"""Autotuner for the batched form's tile shapes.
+
+For every degree k (2D) it times the batched V-cycle graph of a small batch of
+problems of that degree at a representative size for each candidate tile
+shape (patches per thread block of the fused multiplicative-smoother kernel)
+and keeps the fastest.  Results are cached as JSON keyed by dimension, degree
+and device architecture, in $BIHARM_TUNE_CACHE or ~/.cache/biharm_gb300/tiles.json.
+"""
+
+import json
+import os
+
+CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16, 24, 32)
+
+
+def cache_path():
+    p = os.environ.get("BIHARM_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "biharm_gb300", "tiles.json")
+
+
+def _arch():
+    import torch
+    cap = torch.cuda.get_device_capability()
+    return "sm_%d%d_%s" % (cap[0], cap[1], torch.cuda.get_device_name().replace(" ", "_"))
+
+
+def load_cache():
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(c):
+    p = cache_path()
+    os.makedirs(os.path.dirname(p), exist_ok=True)
+    tmp = p + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(c, f, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def tune_degree(k, level=None, problems=4, reps=5, verbose=False):
+    """Best patches-per-block for degree k; returns (best, {pb: ms})."""
+    import torch
+    import paper_2412_05082_gb300 as bh
+    if level is None:  # about 2e5 unknowns per problem
+        level = max(2, min(9, int(round(__import__("math").log2(450.0 / k)))))
+    params = [bh.default_params(2, k, level) for _ in range(problems)]
+    times = {}
+    with bh.Batch(params) as batch:
+        for pb in CANDIDATES:
+            try:
+                batch.set_tile(k, pb)
+            except bh.BiharmError:
+                continue
+            times[pb] = batch.vcycle_time(reps)
+            if verbose:
+                print("k=%d pb=%d: %.3f ms" % (k, pb, times[pb]))
+    torch.cuda.synchronize()
+    best = min(times, key=times.get)
+    return best, times
+
+
+def tiles_for(degrees, refresh=False, verbose=False):
+    """{k: patches per block} for the 2D degrees, tuned once per device."""
+    cache = load_cache()
+    arch = _arch()
+    out, dirty = {}, False
+    for k in sorted(set(degrees)):
+        key = "d2_k%d_%s" % (k, arch)
+        if refresh or key not in cache:
+            best, times = tune_degree(k, verbose=verbose)
+            cache[key] = {"patches_per_block": best, "ms": times}
+            dirty = True
+        out[k] = int(cache[key]["patches_per_block"])
+    if dirty:
+        save_cache(cache)
+    return out
+
+
+def apply(batch, degrees, refresh=False):
+    for k, pb in tiles_for(degrees, refresh).items():
+        batch.set_tile(k, pb)

@@ -1,0 +1,1050 @@
+// Batched form: many independent 2D problems (different degrees and levels)
+// solved together.  Every level operation of the V-cycle processes all
+// problems in ONE launch: the launch walks a precomputed work list of
+// (problem, range) entries and dispatches on the problem's degree.  The
+// smoother's patch work is one persistent launch per color over the tiles of
+// all problems, with the tile shape (patches per block) chosen per degree by
+// the autotuner.  The V-cycle runs in lockstep by depth (depth t works on
+// level L_p - t of every problem p) and is captured once as a CUDA graph;
+// GMRES (left preconditioning, the paper's protocol) runs in lockstep with a
+// per-problem activity mask, one host synchronization per iteration for all
+// problems.  Every problem follows exactly the arithmetic of its own context,
+// so a result does not depend on the other problems of the batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "biharm.h"
+#include "ctx.h"
+#include "ops_impl.cuh"
+
+namespace bh {
+void set_last_error(const std::string& msg);  // api.cu
+}
+
+using namespace bh;
+
+namespace {
+
+using T = double;
+
+bh_status berr(bh_status s, const std::string& msg) {
+  set_last_error(msg);
+  return s;
+}
+
+#define BCK(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return berr(BH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+#define BCKS(call)              \
+  do {                          \
+    bh_status s_ = (call);      \
+    if (s_ != BH_OK) return s_; \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device side
+// ---------------------------------------------------------------------------
+struct Meta {          // per problem, indexed by problem id
+  const int* k;        // degree
+  const void* const* tabs;  // Tables<T, K>* (device)
+  const int* active;   // 0: problem finished, skip it
+};
+
+// first index p with prefix[p + 1] > tid (prefix[0] = 0, increasing)
+__device__ __forceinline__ int find_seg(const int64_t* prefix, int n, int64_t tid) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= tid)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+#define BH_KSWITCH(k, CALL) \
+  switch (k) {              \
+    case 2: CALL(2); break; \
+    case 3: CALL(3); break; \
+    case 4: CALL(4); break; \
+    case 5: CALL(5); break; \
+    case 6: CALL(6); break; \
+    case 7: CALL(7); break; \
+  }
+
+template <int KIND>
+__global__ void __launch_bounds__(128) sweep_batch_kernel(Meta m, const SweepArgs<T>* args,
+                                                          const int64_t* prefix, const int* pid,
+                                                          int n) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= prefix[n]) return;
+  const int s = find_seg(prefix, n, tid);
+  const int p = pid[s];
+  if (!m.active[p]) return;
+  const int64_t local = tid - prefix[s];
+#define BH_CALL(KK) \
+  sweep_thread<T, KK, KIND>(static_cast<const Tables<T, KK>*>(m.tabs[p])->op, args[s], local)
+  BH_KSWITCH(m.k[p], BH_CALL)
+#undef BH_CALL
+}
+
+template <bool PROLONG>
+__global__ void __launch_bounds__(128) xfer_batch_kernel(Meta m, const XferArgs<T>* args,
+                                                         const int64_t* prefix, const int* pid,
+                                                         int n) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= prefix[n]) return;
+  const int s = find_seg(prefix, n, tid);
+  const int p = pid[s];
+  if (!m.active[p]) return;
+  const int64_t local = tid - prefix[s];
+#define BH_CALL(KK)                                                                          \
+  if (PROLONG)                                                                               \
+    prolong_thread<T, KK>(static_cast<const Tables<T, KK>*>(m.tabs[p])->xfer, args[s], local); \
+  else                                                                                       \
+    restrict_thread<T, KK>(static_cast<const Tables<T, KK>*>(m.tabs[p])->xfer, args[s], local)
+  BH_KSWITCH(m.k[p], BH_CALL)
+#undef BH_CALL
+}
+
+struct Tile {
+  int s;      // index into the op's problem list
+  int first;  // first patch of the color list
+  int count;
+};
+
+__global__ void __launch_bounds__(256) mvs2_batch_kernel(Meta m, const MvsArgs<T>* args,
+                                                         const int* pid, const Tile* tiles,
+                                                         int ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {  // persistent over the tiles
+    __syncthreads();  // the previous tile's last stage still reads shared memory
+    const Tile tl = tiles[t];
+    const int p = pid[tl.s];
+    if (!m.active[p]) continue;
+#define BH_CALL(KK)                                                            \
+  {                                                                            \
+    const auto* tb = static_cast<const Tables<T, KK>*>(m.tabs[p]);             \
+    mvs2_tile<T, KK>(tb->op, tb->fdm, args[tl.s], tl.first, tl.count, smem_raw); \
+  }
+    BH_KSWITCH(m.k[p], BH_CALL)
+#undef BH_CALL
+  }
+}
+
+struct Symv {    // coarse solve x = scale A b, A dense symmetric (n x n)
+  const double* A;
+  const T* b;
+  T* x;
+  int n;
+  double scale;
+};
+
+__global__ void coarse_batch_kernel(Meta m, const Symv* ops, const int* pid, int count) {
+  const int s = blockIdx.y;
+  if (s >= count || !m.active[pid[s]]) return;
+  const Symv o = ops[s];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= o.n) return;
+  double acc = 0.0;
+  for (int j = 0; j < o.n; ++j) acc = fma(o.A[(int64_t)j * o.n + i], (double)o.b[j], acc);
+  o.x[i] = (T)(o.scale * acc);
+}
+
+struct Vec {  // one problem's vector operands: y + yslot * ys, x + xslot * xs, n values
+  T* y;
+  const T* x;
+  int64_t n;
+  int64_t ys, xs;
+};
+
+// zero, copy, y += c x, y = x / sqrt(c): one launch over the concatenation
+enum VecOp { kZero = 0, kCopy = 1, kAxpyDev = 2, kScaleInvSqrt = 3 };
+
+__global__ void vec_batch_kernel(Meta m, const Vec* v, const int64_t* prefix, const int* pid,
+                                 int n, int op, const double* coef, int cstride, int cslot,
+                                 double sign, int yslot, int xslot) {
+  const int64_t total = prefix[n];
+  for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
+       tid += (int64_t)gridDim.x * blockDim.x) {
+    const int s = find_seg(prefix, n, tid);
+    const int p = pid[s];
+    if (!m.active[p]) continue;
+    const int64_t i = tid - prefix[s];
+    const Vec o = v[s];
+    T* y = o.y + yslot * o.ys;
+    const T* x = o.x + xslot * o.xs;
+    switch (op) {
+      case kZero: y[i] = T(0); break;
+      case kCopy: y[i] = x[i]; break;
+      case kAxpyDev: y[i] = fma(sign * coef[p * cstride + cslot], x[i], y[i]); break;
+      default: y[i] = x[i] / sqrt(coef[p * cstride + cslot]); break;
+    }
+  }
+}
+
+// deterministic per-problem dot products: fixed chunks, then a fixed-order sum
+constexpr int kChunk = 8192;
+
+__global__ void dot_batch_partial(Meta m, const Vec* v, const int64_t* cprefix, const int* pid,
+                                  int n, double* partials, int yslot, int xslot) {
+  const int64_t c = blockIdx.x;
+  if (c >= cprefix[n]) return;
+  const int s = find_seg(cprefix, n, c);
+  const int p = pid[s];
+  double acc = 0.0;
+  if (m.active[p]) {
+    const Vec o = v[s];
+    const T* y = o.y + yslot * o.ys;
+    const T* x = o.x + xslot * o.xs;
+    const int64_t i0 = (c - cprefix[s]) * kChunk;
+    const int64_t i1 = min(o.n, i0 + kChunk);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc = fma(y[i], x[i], acc);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    partials[c] = t;
+  }
+}
+
+__global__ void dot_batch_final(const int64_t* cprefix, const int* pid, int n,
+                                const double* partials, double* out, int cstride, int cslot) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double t = 0.0;
+  for (int64_t c = cprefix[s]; c < cprefix[s + 1]; ++c) t += partials[c];
+  out[pid[s] * cstride + cslot] = t;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <typename A>
+struct DevArray {  // a device copy of a host vector
+  A* d = nullptr;
+  int n = 0;
+};
+
+struct SweepOp {       // one batched sweep launch
+  DevArray<SweepArgs<T>> args;
+  DevArray<int64_t> prefix;
+  DevArray<int> pid;
+  int64_t total = 0;
+};
+
+struct XferOp {
+  DevArray<XferArgs<T>> args;
+  DevArray<int64_t> prefix;
+  DevArray<int> pid;
+  int64_t total = 0;
+};
+
+struct MvsOp {
+  DevArray<MvsArgs<T>> args;
+  DevArray<int> pid;
+  DevArray<Tile> tiles;
+  size_t smem = 0;
+};
+
+struct VecOpList {
+  DevArray<Vec> v;
+  DevArray<int64_t> prefix;   // element prefix
+  DevArray<int64_t> cprefix;  // chunk prefix (dots)
+  DevArray<int> pid;
+  int64_t total = 0, chunks = 0;
+};
+
+struct Depth {  // operations at depth t of the lockstep V-cycle
+  bool smooth = false, coarse = false;
+  MvsOp mvs[8];
+  SweepOp res_x, res_y;
+  XferOp restr[2], prol[2];
+  VecOpList zero_coarse;  // x at level - 1
+  DevArray<Symv> symv;
+  DevArray<int> symv_pid;
+  int nsymv = 0, maxn_symv = 0;
+};
+
+struct SolvePlan {  // GMRES work lists built once per batch
+  std::vector<SweepOp> apply_x;  // per j: V_j -> scratch
+  SweepOp apply_y;               // scratch -> b_L
+  SweepOp resid_x, resid_y;      // x -> scratch, b - A x -> r_L (pointers refreshed per call)
+  VecOpList ww, wV, Vw, rr;      // w.w, (w, V_i), V_i <- w, r.r
+  VecOpList zero_x, copy_b, bnorm, xV;  // caller vectors (refreshed per call)
+  std::vector<Vec> h_zero_x, h_copy_b, h_bnorm, h_xV;
+  std::vector<SweepArgs<T>> h_rx, h_ry;
+  std::vector<double> hd, hcoef;
+};
+
+}  // namespace
+
+struct bh_batch {
+  int P = 0;
+  cudaStream_t st = nullptr;    // the batch's own non-blocking stream (graph capture needs one)
+  cudaStream_t user = nullptr;  // the caller's stream: solves wait for its pending work
+  cudaEvent_t ev = nullptr;
+  std::vector<bh_ctx*> ctx;
+  std::vector<int> k, L;
+  int m = 0;  // GMRES restart = max iterations
+  int tile[8] = {0};  // patches per block per degree (0 = default)
+  // device meta
+  int* d_k = nullptr;
+  const void** d_tabs = nullptr;
+  int* d_active = nullptr;
+  double* d_dots = nullptr;      // [P][m + 2]
+  double* d_coef = nullptr;      // [P][m]
+  double* d_partials = nullptr;
+  int64_t max_chunks = 0;
+  std::vector<Depth> depth;
+  std::vector<void*> allocs;
+  SolvePlan* plan = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long launches = 0;
+  std::vector<int> last_iters;
+};
+
+namespace {
+
+template <typename A>
+bh_status upload(bh_batch* b, const std::vector<A>& h, DevArray<A>& d) {
+  d.n = (int)h.size();
+  d.d = nullptr;
+  if (h.empty()) return BH_OK;
+  if (cudaMalloc(&d.d, h.size() * sizeof(A)) != cudaSuccess) {
+    cudaGetLastError();
+    return berr(BH_ENOMEM, "cudaMalloc failed in batch setup");
+  }
+  b->allocs.push_back(d.d);
+  BCK(cudaMemcpy(d.d, h.data(), h.size() * sizeof(A), cudaMemcpyHostToDevice));
+  return BH_OK;
+}
+
+Meta meta(const bh_batch* b) { return Meta{b->d_k, b->d_tabs, b->d_active}; }
+
+unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
+
+SweepArgs<T> sweep_args(const Level& Lv, int axis, const T* in0, const T* in1, const T* in2,
+                        T* o0, T* o1, T* o2, const T* bvec, int mode) {
+  SweepArgs<T> a{};
+  a.d = 2;
+  a.N = Lv.g.N;
+  a.n = Lv.g.n;
+  a.lines = Lv.g.nd / Lv.g.n;
+  a.stride = axis == 0 ? 1 : Lv.g.n;
+  a.axis = axis;
+  a.scale = Lv.ascale;
+  a.mode = mode;
+  a.b = bvec;
+  a.in[0] = in0;
+  a.in[1] = in1;
+  a.in[2] = in2;
+  a.out[0] = o0;
+  a.out[1] = o1;
+  a.out[2] = o2;
+  return a;
+}
+
+// build a sweep op over (problem id, args) pairs
+bh_status make_sweep(bh_batch* b, const std::vector<std::pair<int, SweepArgs<T>>>& items,
+                     SweepOp& op) {
+  std::vector<SweepArgs<T>> args;
+  std::vector<int64_t> prefix{0};
+  std::vector<int> pid;
+  for (auto& it : items) {
+    args.push_back(it.second);
+    pid.push_back(it.first);
+    prefix.push_back(prefix.back() + it.second.lines * it.second.N);
+  }
+  op.total = prefix.back();
+  BCKS(upload(b, args, op.args));
+  BCKS(upload(b, prefix, op.prefix));
+  BCKS(upload(b, pid, op.pid));
+  return BH_OK;
+}
+
+template <bool PROLONG>
+XferArgs<T> xfer_args(int axis, const LevelGeom& fine, const T* in, T* out, bool add) {
+  const int K = fine.k, Nc = fine.N / 2, nc = K * Nc - 1, nf = fine.n;
+  XferArgs<T> a{};
+  a.in = in;
+  a.out = out;
+  a.d = 2;
+  a.axis = axis;
+  a.Nc = Nc;
+  a.nc = nc;
+  a.nf = nf;
+  a.add = add;
+  int din[2], dout[2];
+  for (int i = 0; i < 2; ++i) {
+    // pass 0 maps coarse x (prolongation) / fine x (restriction) of axis 0
+    const int before = PROLONG ? nc : nf, after = PROLONG ? nf : nc;
+    din[i] = i < axis ? after : before;
+    dout[i] = i <= axis ? after : before;
+  }
+  int64_t si = 1, so = 1;
+  for (int i = 0; i < 3; ++i) {
+    a.dims_in[i] = i < 2 ? din[i] : 1;
+    a.dims_out[i] = i < 2 ? dout[i] : 1;
+    a.str_in[i] = si;
+    a.str_out[i] = so;
+    si *= a.dims_in[i];
+    so *= a.dims_out[i];
+  }
+  a.lines = din[1 - axis];
+  return a;
+}
+
+bh_status make_xfer(bh_batch* b, const std::vector<std::pair<int, XferArgs<T>>>& items, XferOp& op) {
+  std::vector<XferArgs<T>> args;
+  std::vector<int64_t> prefix{0};
+  std::vector<int> pid;
+  for (auto& it : items) {
+    args.push_back(it.second);
+    pid.push_back(it.first);
+    prefix.push_back(prefix.back() + it.second.lines * it.second.Nc);
+  }
+  op.total = prefix.back();
+  BCKS(upload(b, args, op.args));
+  BCKS(upload(b, prefix, op.prefix));
+  BCKS(upload(b, pid, op.pid));
+  return BH_OK;
+}
+
+// per-call lists: same shape every call, pointers refreshed with an async copy
+bh_status refresh_vec(bh_batch* b, const std::vector<std::pair<int, Vec>>& items, VecOpList& op,
+                      std::vector<Vec>& host) {
+  host.clear();
+  for (auto& it : items) host.push_back(it.second);
+  BCK(cudaMemcpyAsync(op.v.d, host.data(), host.size() * sizeof(Vec), cudaMemcpyHostToDevice,
+                      b->st));
+  return BH_OK;
+}
+
+bh_status make_vec(bh_batch* b, const std::vector<std::pair<int, Vec>>& items, VecOpList& op) {
+  std::vector<Vec> v;
+  std::vector<int64_t> prefix{0}, cprefix{0};
+  std::vector<int> pid;
+  for (auto& it : items) {
+    v.push_back(it.second);
+    pid.push_back(it.first);
+    prefix.push_back(prefix.back() + it.second.n);
+    cprefix.push_back(cprefix.back() + (it.second.n + kChunk - 1) / kChunk);
+  }
+  op.total = prefix.back();
+  op.chunks = cprefix.back();
+  BCKS(upload(b, v, op.v));
+  BCKS(upload(b, prefix, op.prefix));
+  BCKS(upload(b, cprefix, op.cprefix));
+  BCKS(upload(b, pid, op.pid));
+  return BH_OK;
+}
+
+int mvs_pb(const bh_batch* b, int k) {
+  if (b->tile[k] > 0) return b->tile[k];
+  return 4;  // default before tuning
+}
+
+size_t mvs_smem(int k, int pb) {
+  switch (k) {
+    case 2: return Mvs2Cfg<T, 2>::smem_bytes(pb);
+    case 3: return Mvs2Cfg<T, 3>::smem_bytes(pb);
+    case 4: return Mvs2Cfg<T, 4>::smem_bytes(pb);
+    case 5: return Mvs2Cfg<T, 5>::smem_bytes(pb);
+    case 6: return Mvs2Cfg<T, 6>::smem_bytes(pb);
+    default: return Mvs2Cfg<T, 7>::smem_bytes(pb);
+  }
+}
+
+int mvs_pb_max(int k) {
+  switch (k) {
+    case 2: return Mvs2Cfg<T, 2>::PB_MAX;
+    case 3: return Mvs2Cfg<T, 3>::PB_MAX;
+    case 4: return Mvs2Cfg<T, 4>::PB_MAX;
+    case 5: return Mvs2Cfg<T, 5>::PB_MAX;
+    case 6: return Mvs2Cfg<T, 6>::PB_MAX;
+    default: return Mvs2Cfg<T, 7>::PB_MAX;
+  }
+}
+
+// the lockstep V-cycle's work lists (depends on the tile shapes)
+bh_status build_depths(bh_batch* b) {
+  const int P = b->P;
+  const int T_ = *std::max_element(b->L.begin(), b->L.end());
+  b->depth.assign(T_, Depth());
+  for (int t = 0; t < T_; ++t) {
+    Depth& D = b->depth[t];
+    std::vector<std::pair<int, SweepArgs<T>>> rx, ry;
+    std::vector<std::pair<int, XferArgs<T>>> r0, r1, p0, p1;
+    std::vector<std::pair<int, Vec>> zc;
+    std::vector<Symv> sv;
+    std::vector<int> svp;
+    std::vector<std::vector<MvsArgs<T>>> margs(8);
+    std::vector<std::vector<int>> mpid(8);
+    std::vector<std::vector<Tile>> mtiles(8);
+    size_t smem = 0;
+    for (int p = 0; p < P; ++p) {
+      const int l = b->L[p] - t;
+      if (l < 1) continue;
+      bh_ctx* c = b->ctx[p];
+      Level& Lv = c->lv[l];
+      if (l == 1) {
+        sv.push_back(Symv{c->coarse_inv, Lv.b64, Lv.x64, c->coarse_n, Lv.pscale});
+        svp.push_back(p);
+        D.maxn_symv = std::max(D.maxn_symv, c->coarse_n);
+        continue;
+      }
+      Level& Lc = c->lv[l - 1];
+      T* s0 = c->scr64;
+      T* s1 = c->scr64 + Lv.g.nd;
+      T* s2 = c->scr64 + 2 * Lv.g.nd;
+      rx.push_back({p, sweep_args(Lv, 0, Lv.x64, nullptr, nullptr, s0, s1, s2, nullptr, kStore)});
+      ry.push_back({p, sweep_args(Lv, 1, s0, s1, s2, Lv.r64, nullptr, nullptr, Lv.b64, kResidual)});
+      r0.push_back({p, xfer_args<false>(0, Lv.g, Lv.r64, c->xs64[0], false)});
+      r1.push_back({p, xfer_args<false>(1, Lv.g, c->xs64[0], Lc.b64, false)});
+      p0.push_back({p, xfer_args<true>(0, Lv.g, Lc.x64, c->xs64[0], false)});
+      p1.push_back({p, xfer_args<true>(1, Lv.g, c->xs64[0], Lv.x64, true)});
+      zc.push_back({p, Vec{Lc.x64, nullptr, Lc.g.nd, 0, 0}});
+      const int k = b->k[p];
+      const int pb = std::min(mvs_pb(b, k), mvs_pb_max(k));
+      smem = std::max(smem, mvs_smem(k, pb));
+      const DevTables dt = Ops<T>::device_tables(c->tab64, k);
+      for (int col = 0; col < 8; ++col) {
+        MvsArgs<T> a{};
+        a.x = Lv.x64;
+        a.b = Lv.b64;
+        a.verts = Lv.verts + Lv.coff[col];
+        a.count = Lv.coff[col + 1] - Lv.coff[col];
+        a.N = Lv.g.N;
+        a.n = Lv.g.n;
+        a.pb = pb;
+        a.ascale = Lv.ascale;
+        a.pscale = c->p.omega * Lv.pscale;
+        a.dinv = static_cast<const T*>(dt.dinv);
+        const int s = (int)margs[col].size();
+        margs[col].push_back(a);
+        mpid[col].push_back(p);
+        for (int f = 0; f < a.count; f += pb) mtiles[col].push_back(Tile{s, f, std::min(pb, a.count - f)});
+      }
+    }
+    D.smooth = !rx.empty();
+    D.coarse = !sv.empty();
+    if (D.smooth) {
+      BCKS(make_sweep(b, rx, D.res_x));
+      BCKS(make_sweep(b, ry, D.res_y));
+      BCKS(make_xfer(b, r0, D.restr[0]));
+      BCKS(make_xfer(b, r1, D.restr[1]));
+      BCKS(make_xfer(b, p0, D.prol[0]));
+      BCKS(make_xfer(b, p1, D.prol[1]));
+      BCKS(make_vec(b, zc, D.zero_coarse));
+      for (int col = 0; col < 8; ++col) {
+        BCKS(upload(b, margs[col], D.mvs[col].args));
+        BCKS(upload(b, mpid[col], D.mvs[col].pid));
+        BCKS(upload(b, mtiles[col], D.mvs[col].tiles));
+        D.mvs[col].smem = smem;
+      }
+    }
+    if (D.coarse) {
+      BCKS(upload(b, sv, D.symv));
+      BCKS(upload(b, svp, D.symv_pid));
+      D.nsymv = (int)sv.size();
+    }
+  }
+  return BH_OK;
+}
+
+// ---- launches (all on b->st, graph-capturable) ---------------------------------
+cudaError_t run_sweep(bh_batch* b, const SweepOp& op, int kind) {
+  if (op.total == 0) return cudaSuccess;
+  const unsigned g = blocks_for(op.total, 128);
+  if (kind == 0)
+    sweep_batch_kernel<0><<<g, 128, 0, b->st>>>(meta(b), op.args.d, op.prefix.d, op.pid.d, op.pid.n);
+  else
+    sweep_batch_kernel<2><<<g, 128, 0, b->st>>>(meta(b), op.args.d, op.prefix.d, op.pid.d, op.pid.n);
+  b->launches++;
+  g_kernel_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_xfer(bh_batch* b, const XferOp& op, bool prolong) {
+  if (op.total == 0) return cudaSuccess;
+  const unsigned g = blocks_for(op.total, 128);
+  if (prolong)
+    xfer_batch_kernel<true><<<g, 128, 0, b->st>>>(meta(b), op.args.d, op.prefix.d, op.pid.d, op.pid.n);
+  else
+    xfer_batch_kernel<false><<<g, 128, 0, b->st>>>(meta(b), op.args.d, op.prefix.d, op.pid.d, op.pid.n);
+  b->launches++;
+  g_kernel_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_vec(bh_batch* b, const VecOpList& op, int kind, const double* coef, int cstride,
+                    int cslot, double sign, int yslot = 0, int xslot = 0) {
+  if (op.total == 0) return cudaSuccess;
+  int64_t g = blocks_for(op.total, 256);
+  if (g > 152 * 16) g = 152 * 16;
+  vec_batch_kernel<<<(unsigned)g, 256, 0, b->st>>>(meta(b), op.v.d, op.prefix.d, op.pid.d,
+                                                   op.pid.n, kind, coef, cstride, cslot, sign,
+                                                   yslot, xslot);
+  b->launches++;
+  g_kernel_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+cudaError_t run_dot(bh_batch* b, const VecOpList& op, int cslot, int yslot = 0, int xslot = 0) {
+  if (op.chunks == 0) return cudaSuccess;
+  dot_batch_partial<<<(unsigned)op.chunks, 256, 0, b->st>>>(meta(b), op.v.d, op.cprefix.d,
+                                                          op.pid.d, op.pid.n, b->d_partials,
+                                                          yslot, xslot);
+  dot_batch_final<<<blocks_for(op.pid.n, 64), 64, 0, b->st>>>(op.cprefix.d, op.pid.d, op.pid.n,
+                                                             b->d_partials, b->d_dots, b->m + 2,
+                                                             cslot);
+  b->launches += 2;
+  g_kernel_launches.fetch_add(2);
+  return cudaGetLastError();
+}
+
+cudaError_t run_mvs(bh_batch* b, const MvsOp& op) {
+  if (op.tiles.n == 0) return cudaSuccess;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mvs2_batch_kernel, 256,
+                                                                op.smem);
+  if (e != cudaSuccess) return e;
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(op.tiles.n, std::max(1, per_sm) * sms));
+  mvs2_batch_kernel<<<grid, 256, op.smem, b->st>>>(meta(b), op.args.d, op.pid.d, op.tiles.d,
+                                                   op.tiles.n);
+  b->launches++;
+  g_kernel_launches.fetch_add(1);
+  return cudaGetLastError();
+}
+
+// lockstep V-cycle from depth t: x_L = MG(b_L) with x_L zero on entry
+cudaError_t vcycle_from(bh_batch* b, int t) {
+  if (t >= (int)b->depth.size()) return cudaSuccess;
+  Depth& D = b->depth[t];
+  cudaError_t e;
+  if (D.coarse) {
+    dim3 grid(blocks_for(D.maxn_symv, 128), D.nsymv);
+    coarse_batch_kernel<<<grid, 128, 0, b->st>>>(meta(b), D.symv.d, D.symv_pid.d, D.nsymv);
+    b->launches++;
+    g_kernel_launches.fetch_add(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (!D.smooth) return cudaSuccess;
+  for (int col = 0; col < 8; ++col)
+    if ((e = run_mvs(b, D.mvs[col])) != cudaSuccess) return e;
+  if ((e = run_sweep(b, D.res_x, 0)) != cudaSuccess) return e;
+  if ((e = run_sweep(b, D.res_y, 2)) != cudaSuccess) return e;
+  if ((e = run_xfer(b, D.restr[0], false)) != cudaSuccess) return e;
+  if ((e = run_xfer(b, D.restr[1], false)) != cudaSuccess) return e;
+  if ((e = run_vec(b, D.zero_coarse, kZero, nullptr, 0, 0, 0.0)) != cudaSuccess) return e;
+  if ((e = vcycle_from(b, t + 1)) != cudaSuccess) return e;
+  if ((e = run_xfer(b, D.prol[0], true)) != cudaSuccess) return e;
+  if ((e = run_xfer(b, D.prol[1], true)) != cudaSuccess) return e;
+  for (int col = 0; col < 8; ++col)
+    if ((e = run_mvs(b, D.mvs[col])) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+bh_status capture_vcycle(bh_batch* b) {
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  // the V-cycle starts from x_L = 0 on the finest level of every problem
+  std::vector<std::pair<int, Vec>> zf;
+  for (int p = 0; p < b->P; ++p) {
+    Level& F = b->ctx[p]->lv[b->L[p]];
+    zf.push_back({p, Vec{F.x64, nullptr, F.g.nd, 0, 0}});
+  }
+  VecOpList zero_fine;
+  BCKS(make_vec(b, zf, zero_fine));
+  BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = run_vec(b, zero_fine, kZero, nullptr, 0, 0, 0.0);
+  if (e == cudaSuccess) e = vcycle_from(b, 0);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return berr(BH_ECUDA, std::string("V-cycle capture failed: ") +
+                              cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  b->graph = g;
+  BCK(cudaGraphInstantiate(&b->gexec, g, 0));
+  return BH_OK;
+}
+
+bh_status set_active(bh_batch* b, const std::vector<int>& act) {
+  BCK(cudaMemcpyAsync(b->d_active, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice,
+                      b->st));
+  BCK(cudaStreamSynchronize(b->st));  // act is a host temporary
+  return BH_OK;
+}
+
+bh_status prepare(bh_batch* b) {
+  // mvs kernel: allow the largest dynamic shared memory any tile shape needs
+  size_t smem = 0;
+  for (int p = 0; p < b->P; ++p)
+    smem = std::max(smem, mvs_smem(b->k[p], std::min(mvs_pb(b, b->k[p]), mvs_pb_max(b->k[p]))));
+  BCK(cudaFuncSetAttribute(mvs2_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem));
+  BCKS(build_depths(b));
+  return capture_vcycle(b);
+}
+
+bh_status ensure_plan(bh_batch* b) {
+  if (b->plan) return BH_OK;
+  const int P = b->P, m = b->m;
+  for (int p = 0; p < P; ++p) {  // Krylov basis V_0..V_m per problem
+    bh_ctx* c = b->ctx[p];
+    if (!c->V) {
+      const int64_t n = c->lv[b->L[p]].g.nd;
+      if (cudaMalloc(&c->V, (size_t)(m + 1) * n * sizeof(double)) != cudaSuccess) {
+        c->V = nullptr;
+        cudaGetLastError();
+        return berr(BH_ENOMEM, "Krylov basis allocation failed");
+      }
+      c->dev_allocs.push_back(c->V);
+    }
+  }
+  SolvePlan* S = new (std::nothrow) SolvePlan();
+  if (!S) return berr(BH_ENOMEM, "host allocation failed");
+  b->plan = S;
+  S->apply_x.resize(m);
+  std::vector<std::pair<int, SweepArgs<T>>> ay, rx, ry;
+  std::vector<std::vector<std::pair<int, SweepArgs<T>>>> ax(m);
+  std::vector<std::pair<int, Vec>> ww, wV, Vw, rr, z;
+  for (int p = 0; p < P; ++p) {
+    bh_ctx* c = b->ctx[p];
+    Level& F = c->lv[b->L[p]];
+    const int64_t n = F.g.nd;
+    T* s0 = c->scr64;
+    T* s1 = s0 + n;
+    T* s2 = s1 + n;
+    for (int j = 0; j < m; ++j)
+      ax[j].push_back({p, sweep_args(F, 0, c->V + (int64_t)j * n, nullptr, nullptr, s0, s1, s2,
+                                     nullptr, kStore)});
+    ay.push_back({p, sweep_args(F, 1, s0, s1, s2, F.b64, nullptr, nullptr, nullptr, kStore)});
+    rx.push_back({p, sweep_args(F, 0, F.x64, nullptr, nullptr, s0, s1, s2, nullptr, kStore)});
+    ry.push_back({p, sweep_args(F, 1, s0, s1, s2, F.r64, nullptr, nullptr, F.b64, kResidual)});
+    ww.push_back({p, Vec{F.x64, F.x64, n, 0, 0}});
+    wV.push_back({p, Vec{F.x64, c->V, n, 0, n}});
+    Vw.push_back({p, Vec{c->V, F.x64, n, n, 0}});
+    rr.push_back({p, Vec{F.r64, F.r64, n, 0, 0}});
+    z.push_back({p, Vec{F.x64, nullptr, n, 0, 0}});
+  }
+  for (int j = 0; j < m; ++j) BCKS(make_sweep(b, ax[j], S->apply_x[j]));
+  BCKS(make_sweep(b, ay, S->apply_y));
+  BCKS(make_sweep(b, rx, S->resid_x));
+  BCKS(make_sweep(b, ry, S->resid_y));
+  BCKS(make_vec(b, ww, S->ww));
+  BCKS(make_vec(b, wV, S->wV));
+  BCKS(make_vec(b, Vw, S->Vw));
+  BCKS(make_vec(b, rr, S->rr));
+  BCKS(make_vec(b, z, S->zero_x));
+  BCKS(make_vec(b, z, S->copy_b));
+  BCKS(make_vec(b, z, S->bnorm));
+  BCKS(make_vec(b, z, S->xV));
+  S->hd.assign((size_t)P * (m + 2), 0.0);
+  S->hcoef.assign((size_t)P * (m + 2), 0.0);
+  return BH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_batch** out) {
+  if (!params || !out || count < 1) return berr(BH_EINVAL, "bh_batch_create: bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    const bh_params& p = params[i];
+    if (p.dim != 2) return berr(BH_EINVAL, "bh_batch_create: the batched form supports 2D problems");
+    if (p.smoother != BH_MVS_COLORED || p.local_solver != BH_FDM || p.precision != BH_FP64 ||
+        p.coarse != BH_COARSE_EXACT || p.gmres_side != BH_LEFT)
+      return berr(BH_EINVAL, "bh_batch_create: the batched form runs colored MVS with FDM local "
+                             "solvers, FP64, the exact coarse solve and left-preconditioned GMRES");
+  }
+  bh_batch* b = new (std::nothrow) bh_batch();
+  if (!b) return berr(BH_ENOMEM, "host allocation failed");
+  b->P = count;
+  b->user = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return berr(BH_ECUDA, "bh_batch_create: stream creation failed");
+  }
+  auto bail = [&](bh_status s) {
+    bh_batch_destroy(b);
+    return s;
+  };
+  int m = 0;
+  for (int i = 0; i < count; ++i) m = std::max(m, params[i].gmres_restart > 0 ? params[i].gmres_restart : 50);
+  b->m = m;
+  for (int i = 0; i < count; ++i) {
+    bh_params p = params[i];
+    p.gmres_restart = m;
+    bh_ctx* c = nullptr;
+    bh_status s = bh_create(&p, stream, &c);
+    if (s != BH_OK) return bail(s);
+    b->ctx.push_back(c);
+    b->k.push_back(p.degree);
+    b->L.push_back(p.level);
+  }
+  std::vector<const void*> tabs;
+  for (int p = 0; p < count; ++p) tabs.push_back(Ops<T>::device_tables(b->ctx[p]->tab64, b->k[p]).tables);
+  DevArray<int> dk;
+  DevArray<const void*> dt;
+  bh_status s;
+  if ((s = upload(b, b->k, dk)) || (s = upload(b, tabs, dt))) return bail(s);
+  b->d_k = dk.d;
+  b->d_tabs = dt.d;
+  std::vector<int> act(count, 1);
+  DevArray<int> da;
+  if ((s = upload(b, act, da))) return bail(s);
+  b->d_active = da.d;
+  std::vector<double> zeros((size_t)count * (m + 2), 0.0);
+  DevArray<double> dd, dc;
+  if ((s = upload(b, zeros, dd)) || (s = upload(b, zeros, dc))) return bail(s);
+  b->d_dots = dd.d;
+  b->d_coef = dc.d;
+  int64_t chunks = 0;
+  for (int p = 0; p < count; ++p)
+    chunks += (b->ctx[p]->lv[b->L[p]].g.nd + kChunk - 1) / kChunk;
+  std::vector<double> pz((size_t)chunks + 1, 0.0);
+  DevArray<double> dp;
+  if ((s = upload(b, pz, dp))) return bail(s);
+  b->d_partials = dp.d;
+  if ((s = prepare(b))) return bail(s);
+  *out = b;
+  return BH_OK;
+}
+
+bh_status bh_batch_destroy(bh_batch* b) {
+  if (!b) return berr(BH_EINVAL, "null batch");
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (void* p : b->allocs) cudaFree(p);
+  for (bh_ctx* c : b->ctx) bh_destroy(c);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b->plan;
+  delete b;
+  return BH_OK;
+}
+
+bh_status bh_batch_set_tile(bh_batch* b, int degree, int patches_per_block) {
+  if (!b || degree < 2 || degree > 7 || patches_per_block < 1 || patches_per_block > 32)
+    return berr(BH_EINVAL, "bh_batch_set_tile: bad arguments");
+  if (patches_per_block > mvs_pb_max(degree))
+    return berr(BH_EINVAL, "bh_batch_set_tile: tile exceeds the shared-memory budget (max " +
+                               std::to_string(mvs_pb_max(degree)) + " patches for this degree)");
+  b->tile[degree] = patches_per_block;
+  return prepare(b);
+}
+
+bh_status bh_batch_vcycle_time(bh_batch* b, int reps, double* ms) {
+  if (!b || reps < 1 || !ms) return berr(BH_EINVAL, "bad arguments");
+  std::vector<int> act(b->P, 1);
+  BCKS(set_active(b, act));
+  BCK(cudaEventRecord(b->ev, b->user));
+  BCK(cudaStreamWaitEvent(b->st, b->ev, 0));
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  BCK(cudaGraphLaunch(b->gexec, b->st));
+  BCK(cudaEventRecord(e0, b->st));
+  for (int r = 0; r < reps; ++r) BCK(cudaGraphLaunch(b->gexec, b->st));
+  BCK(cudaEventRecord(e1, b->st));
+  BCK(cudaEventSynchronize(e1));
+  float t = 0.f;
+  BCK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / reps;
+  return BH_OK;
+}
+
+bh_status bh_batch_solve(bh_batch* b, const double* const* b_dev, double* const* x_dev,
+                         double rtol, int maxit, int* iters, double* relres) {
+  if (!b || !b_dev || !x_dev || !iters || !relres || !(rtol > 0.0) || maxit < 1)
+    return berr(BH_EINVAL, "bh_batch_solve: bad arguments");
+  const int P = b->P, m = std::min(b->m, maxit);
+  const int cs = b->m + 2;  // stride of the dots and coefficient arrays
+  BCKS(ensure_plan(b));
+  SolvePlan& S = *b->plan;
+  // inputs written on the caller's stream must be complete before the batch reads them
+  BCK(cudaEventRecord(b->ev, b->user));
+  BCK(cudaStreamWaitEvent(b->st, b->ev, 0));
+  // caller vectors: x (zeroed, updated), b (copied to b_L, norm, residual)
+  {
+    std::vector<std::pair<int, Vec>> lx, lb, lbb, lxv;
+    for (int p = 0; p < P; ++p) {
+      bh_ctx* c = b->ctx[p];
+      Level& F = c->lv[b->L[p]];
+      const int64_t n = F.g.nd;
+      lx.push_back({p, Vec{x_dev[p], nullptr, n, 0, 0}});
+      lb.push_back({p, Vec{F.b64, b_dev[p], n, 0, 0}});
+      lbb.push_back({p, Vec{const_cast<double*>(b_dev[p]), b_dev[p], n, 0, 0}});
+      lxv.push_back({p, Vec{x_dev[p], c->V, n, 0, n}});
+    }
+    BCKS(refresh_vec(b, lx, S.zero_x, S.h_zero_x));
+    BCKS(refresh_vec(b, lb, S.copy_b, S.h_copy_b));
+    BCKS(refresh_vec(b, lbb, S.bnorm, S.h_bnorm));
+    BCKS(refresh_vec(b, lxv, S.xV, S.h_xV));
+    S.h_rx.clear();
+    S.h_ry.clear();
+    for (int p = 0; p < P; ++p) {
+      bh_ctx* c = b->ctx[p];
+      Level& F = c->lv[b->L[p]];
+      T* s0 = c->scr64;
+      T* s1 = s0 + F.g.nd;
+      T* s2 = s1 + F.g.nd;
+      S.h_rx.push_back(sweep_args(F, 0, x_dev[p], nullptr, nullptr, s0, s1, s2, nullptr, kStore));
+      S.h_ry.push_back(sweep_args(F, 1, s0, s1, s2, F.r64, nullptr, nullptr, b_dev[p], kResidual));
+    }
+    BCK(cudaMemcpyAsync(S.resid_x.args.d, S.h_rx.data(), P * sizeof(SweepArgs<T>),
+                        cudaMemcpyHostToDevice, b->st));
+    BCK(cudaMemcpyAsync(S.resid_y.args.d, S.h_ry.data(), P * sizeof(SweepArgs<T>),
+                        cudaMemcpyHostToDevice, b->st));
+  }
+  std::vector<int> act(P, 1);
+  BCKS(set_active(b, act));
+  BCK(run_vec(b, S.zero_x, kZero, nullptr, 0, 0, 0.0));
+  // r0 = M^-1 b: b_L = b, V-cycle into x_L; beta = ||x_L||, ||b||
+  BCK(run_vec(b, S.copy_b, kCopy, nullptr, 0, 0, 0.0));
+  BCK(cudaGraphLaunch(b->gexec, b->st));
+  b->launches++;
+  BCK(run_dot(b, S.ww, 0));
+  BCK(run_dot(b, S.bnorm, 1));
+  std::vector<double>& hd = S.hd;
+  BCK(cudaMemcpyAsync(hd.data(), b->d_dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st));
+  BCK(cudaStreamSynchronize(b->st));
+  std::vector<double> beta(P), bnorm(P);
+  for (int p = 0; p < P; ++p) {
+    beta[p] = std::sqrt(hd[(size_t)p * cs]);
+    bnorm[p] = std::sqrt(hd[(size_t)p * cs + 1]);
+    if (!std::isfinite(bnorm[p])) return berr(BH_EINVAL, "right-hand side is not finite");
+    if (!(bnorm[p] > 0.0) || !(beta[p] > 0.0)) act[p] = 0;
+  }
+  BCKS(set_active(b, act));
+  BCK(run_vec(b, S.Vw, kScaleInvSqrt, b->d_dots, cs, 0, 1.0, 0, 0));  // V_0 = x_L / beta
+  std::vector<std::vector<double>> H(P, std::vector<double>((size_t)(m + 1) * m, 0.0));
+  std::vector<std::vector<double>> cn(P, std::vector<double>(m)), sn(P, std::vector<double>(m)),
+      g(P, std::vector<double>(m + 1, 0.0));
+  std::vector<int> done_j(P, 0), conv(P, 0);
+  for (int p = 0; p < P; ++p) g[p][0] = beta[p];
+  for (int j = 0; j < m; ++j) {
+    bool any = false;
+    for (int p = 0; p < P; ++p) any |= act[p] != 0;
+    if (!any) break;
+    BCK(run_sweep(b, S.apply_x[j], 0));  // b_L = A V_j
+    BCK(run_sweep(b, S.apply_y, 2));
+    BCK(cudaGraphLaunch(b->gexec, b->st));  // w = x_L = M^-1 b_L
+    b->launches++;
+    for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
+      BCK(run_dot(b, S.wV, i, 0, i));
+      BCK(run_vec(b, S.wV, kAxpyDev, b->d_dots, cs, i, -1.0, 0, i));
+    }
+    BCK(run_dot(b, S.ww, j + 1));
+    BCK(cudaMemcpyAsync(hd.data(), b->d_dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    bool changed = false;
+    for (int p = 0; p < P; ++p) {
+      if (!act[p]) continue;
+      auto Hij = [&](int i, int jj) -> double& { return H[p][(size_t)i * m + jj]; };
+      for (int i = 0; i <= j; ++i) Hij(i, j) = hd[(size_t)p * cs + i];
+      const double hn = std::sqrt(hd[(size_t)p * cs + j + 1]);
+      Hij(j + 1, j) = hn;
+      for (int i = 0; i < j; ++i) {
+        const double tt = cn[p][i] * Hij(i, j) + sn[p][i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[p][i] * Hij(i, j) + cn[p][i] * Hij(i + 1, j);
+        Hij(i, j) = tt;
+      }
+      const double rho = std::hypot(Hij(j, j), Hij(j + 1, j));
+      cn[p][j] = Hij(j, j) / rho;
+      sn[p][j] = Hij(j + 1, j) / rho;
+      Hij(j, j) = rho;
+      Hij(j + 1, j) = 0.0;
+      g[p][j + 1] = -sn[p][j] * g[p][j];
+      g[p][j] = cn[p][j] * g[p][j];
+      done_j[p] = j + 1;
+      const double est = std::fabs(g[p][j + 1]);
+      if (!std::isfinite(est)) return berr(BH_ENOCONV, "batched GMRES: non-finite residual");
+      if (est <= rtol * beta[p] || hn == 0.0 || j + 1 >= m) {
+        conv[p] = est <= rtol * beta[p] || hn == 0.0;
+        act[p] = 0;
+        changed = true;
+      }
+    }
+    if (changed) BCKS(set_active(b, act));
+    BCK(run_vec(b, S.Vw, kScaleInvSqrt, b->d_dots, cs, j + 1, 1.0, j + 1, 0));  // V_{j+1}
+  }
+  // x = V y (back substitution on the host), then the true residuals
+  std::vector<double>& coef = S.hcoef;
+  std::fill(coef.begin(), coef.end(), 0.0);
+  int jmax = 0;
+  for (int p = 0; p < P; ++p) {
+    const int jd = done_j[p];
+    jmax = std::max(jmax, jd);
+    for (int i = jd - 1; i >= 0; --i) {
+      double sacc = g[p][i];
+      for (int jj = i + 1; jj < jd; ++jj) sacc -= H[p][(size_t)i * m + jj] * coef[(size_t)p * cs + jj];
+      coef[(size_t)p * cs + i] = sacc / H[p][(size_t)i * m + i];
+    }
+  }
+  for (int p = 0; p < P; ++p) act[p] = bnorm[p] > 0.0 ? 1 : 0;
+  BCKS(set_active(b, act));
+  BCK(cudaMemcpyAsync(b->d_coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice,
+                      b->st));
+  for (int i = 0; i < jmax; ++i) BCK(run_vec(b, S.xV, kAxpyDev, b->d_coef, cs, i, 1.0, 0, i));
+  BCK(run_sweep(b, S.resid_x, 0));
+  BCK(run_sweep(b, S.resid_y, 2));
+  BCK(run_dot(b, S.rr, 0));
+  BCK(cudaMemcpyAsync(hd.data(), b->d_dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st));
+  BCK(cudaStreamSynchronize(b->st));
+  bool all_conv = true;
+  b->last_iters = done_j;
+  for (int p = 0; p < P; ++p) {
+    iters[p] = done_j[p];
+    relres[p] = bnorm[p] > 0.0 ? std::sqrt(hd[(size_t)p * cs]) / bnorm[p] : 0.0;
+    if (bnorm[p] > 0.0 && !conv[p]) all_conv = false;
+  }
+  if (!all_conv) return berr(BH_ENOCONV, "batched GMRES: some problems did not reach the tolerance");
+  return BH_OK;
+}
+
+bh_status bh_batch_stats(const bh_batch* b, long long* launches) {
+  if (!b || !launches) return berr(BH_EINVAL, "bad arguments");
+  *launches = b->launches;
+  return BH_OK;
+}
+
+}  // extern "C"

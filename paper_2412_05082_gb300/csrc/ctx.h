@@ -1,0 +1,56 @@
+// Context internals shared by api.cu (single problem) and batch.cu (batched
+// form): one multigrid hierarchy with its device buffers and tables.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "biharm.h"
+#include "ops.h"
+#include "setup.h"
+
+namespace bh {
+
+struct Level {
+  LevelGeom g{};
+  double ascale = 0;  // A_l = ascale * A_ref      (h^(d-4))
+  double pscale = 0;  // A_v^-1 = pscale * A_ref^-1 (h^(4-d))
+  double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
+  float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+  int* verts = nullptr;  // vertex ids sorted by color
+  int coff[17] = {0};    // color offsets into verts
+};
+
+}  // namespace bh
+
+struct bh_ctx {
+  bh_params p{};
+  cudaStream_t st = nullptr;
+  bh::Setup1D s;
+  void* tab64 = nullptr;
+  void* tab32 = nullptr;
+  std::vector<bh::Level> lv;  // index = level, lv[0] unused
+  double* scr64 = nullptr;
+  float* scr32 = nullptr;
+  double* xs64[2] = {nullptr, nullptr};
+  float* xs32[2] = {nullptr, nullptr};
+  double* coarse_inv = nullptr;
+  int coarse_n = 0;
+  double* ainv64 = nullptr;
+  float* ainv32 = nullptr;
+  // GMRES workspace (allocated on first solve)
+  int m = 0;
+  double* V = nullptr;
+  double* Z = nullptr;
+  double* w = nullptr;
+  double* t = nullptr;
+  double* dots = nullptr;
+  double* partials = nullptr;
+  double* hdots = nullptr;  // pinned host
+  std::vector<void*> dev_allocs;
+  // stats
+  long long n_apply = 0, n_smooth = 0, n_vcycle = 0, n_solve = 0;
+  int last_iters = 0;
+  double last_relres = 0;
+  int ncolors() const { return p.dim == 2 ? 8 : 16; }
+};

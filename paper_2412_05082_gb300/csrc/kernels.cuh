@@ -202,12 +202,10 @@ __device__ __forceinline__ void sweep_cell(const OpTab<T, K>& tab, const SweepAr
   }
 }
 
+// one thread of a sweep: thread index tid in [0, lines * N)
 template <typename T, int K, int KIND>
-__global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ OpTab<T, K> tab,
-                                                    const SweepArgs<T> a) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = a.lines * a.N;
-  if (tid >= total) return;
+__device__ __forceinline__ void sweep_thread(const OpTab<T, K>& tab, const SweepArgs<T>& a,
+                                             int64_t tid) {
   int64_t line;
   int c;
   if (a.axis == 0) {  // consecutive threads: consecutive cells of one line
@@ -231,6 +229,14 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ OpTa
     }
     sweep_cell<T, K, KIND, false>(tab, a, base, c, cls);
   }
+}
+
+template <typename T, int K, int KIND>
+__global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ OpTab<T, K> tab,
+                                                    const SweepArgs<T> a) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= a.lines * a.N) return;
+  sweep_thread<T, K, KIND>(tab, a, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -447,10 +453,8 @@ struct XferArgs {
 // prolongation along an axis: thread <-> (line, coarse cell C); fine nodes
 // 2KC + r (r = 0..2K-1) from coarse nodes KC + q (q = 0..K).
 template <typename T, int K>
-__global__ void __launch_bounds__(128) prolong_kernel(const __grid_constant__ XferTab<T, K> tab,
-                                                      const XferArgs<T> a) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= a.lines * a.Nc) return;
+__device__ __forceinline__ void prolong_thread(const XferTab<T, K>& tab, const XferArgs<T>& a,
+                                               int64_t tid) {
   int64_t line;
   int C;
   if (a.axis == 0) {
@@ -481,13 +485,18 @@ __global__ void __launch_bounds__(128) prolong_kernel(const __grid_constant__ Xf
   }
 }
 
+template <typename T, int K>
+__global__ void __launch_bounds__(128) prolong_kernel(const __grid_constant__ XferTab<T, K> tab,
+                                                      const XferArgs<T> a) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < a.lines * a.Nc) prolong_thread<T, K>(tab, a, tid);
+}
+
 // restriction along an axis: thread <-> (line, coarse cell C); coarse nodes KC+q
 // (q = 0..K-1) from the fine nodes 2K(C-1) .. 2KC + 2K - 1.
 template <typename T, int K>
-__global__ void __launch_bounds__(128) restrict_kernel(const __grid_constant__ XferTab<T, K> tab,
-                                                       const XferArgs<T> a) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= a.lines * a.Nc) return;
+__device__ __forceinline__ void restrict_thread(const XferTab<T, K>& tab, const XferArgs<T>& a,
+                                                int64_t tid) {
   int64_t line;
   int C;
   if (a.axis == 0) {
@@ -519,6 +528,13 @@ __global__ void __launch_bounds__(128) restrict_kernel(const __grid_constant__ X
     for (int r = 0; r < 2 * K; ++r) s = fma(tab.P[r][q], w[2 * K + r], s);
     a.out[bo + (int64_t)(g - 1) * so] = s;
   }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(128) restrict_kernel(const __grid_constant__ XferTab<T, K> tab,
+                                                       const XferArgs<T> a) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < a.lines * a.Nc) restrict_thread<T, K>(tab, a, tid);
 }
 
 template <typename T>

@@ -137,12 +137,15 @@ __device__ __forceinline__ void ycombine_half(const T* sM, const T* sL, const T*
   }
 }
 
+// Patches first .. first + np - 1 of a.verts by one thread block; tables read
+// from `op` / `fdm` (kernel parameters or device memory) into shared memory.
+// smem_raw: dynamic shared memory of at least Mvs2Cfg::smem_bytes(a.pb) bytes.
 template <typename T, int K>
-__global__ void __launch_bounds__(256) mvs2_color_kernel(const __grid_constant__ MvsTab<T, K> tab,
-                                                         const MvsArgs<T> a) {
+__device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T, K>& fdm,
+                                          const MvsArgs<T>& a, int first, int np,
+                                          unsigned char* smem_raw) {
   using C = Mvs2Cfg<T, K>;
   constexpr int M = C::M, W = C::W, WM = C::WM, NC = C::NC, BW = C::BW, MM = M * M;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sM = reinterpret_cast<T*>(smem_raw);
   T* sL = sM + NC * BW;
   T* sB = sL + NC * BW;
@@ -156,16 +159,14 @@ __global__ void __launch_bounds__(256) mvs2_color_kernel(const __grid_constant__
   T* sF = sR + pb * MM;        // [pb][M][M]
   __shared__ int sV[32][2], sTy[32][2], sCombo[32];
 
-  const int first = blockIdx.x * pb;
-  const int np = min(pb, a.count - first);
   if (np <= 0) return;
   const int N = a.N, n = a.n;
   for (int e = threadIdx.x; e < NC * BW; e += blockDim.x) {
-    sM[e] = (&tab.op.M[0][0])[e];
-    sL[e] = (&tab.op.L[0][0])[e];
-    sB[e] = (&tab.op.B[0][0])[e];
+    sM[e] = (&op.M[0][0])[e];
+    sL[e] = (&op.L[0][0])[e];
+    sB[e] = (&op.B[0][0])[e];
   }
-  for (int e = threadIdx.x; e < 4 * MM; e += blockDim.x) sS[e] = (&tab.fdm.S[0][0][0])[e];
+  for (int e = threadIdx.x; e < 4 * MM; e += blockDim.x) sS[e] = (&fdm.S[0][0][0])[e];
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
     const int vid = a.verts[first + p];
     const int v0 = vid % (N - 1) + 1, v1 = vid / (N - 1) + 1;
@@ -273,6 +274,14 @@ __global__ void __launch_bounds__(256) mvs2_color_kernel(const __grid_constant__
     const int gx = K * (sV[p][0] - 1) + j + 1, gy = K * (sV[p][1] - 1) + i + 1;
     a.x[(int64_t)(gy - 1) * n + (gx - 1)] += ps * s;
   }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) mvs2_color_kernel(const __grid_constant__ MvsTab<T, K> tab,
+                                                         const MvsArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int first = blockIdx.x * a.pb;
+  mvs2_tile<T, K>(tab.op, tab.fdm, a, first, min(a.pb, a.count - first), smem_raw);
 }
 
 }  // namespace bh

@@ -25,12 +25,20 @@ inline int apply_scratch_arrays(int d) { return d == 2 ? 3 : 6; }
 
 enum ApplyMode { kStore = 0, kResidual = 1 };
 
+// device copies of a context's tables: `tables` points to Tables<T, K> in
+// device memory, `dinv` to the reciprocal eigenvalue sums
+struct DevTables {
+  const void* tables;
+  const void* dinv;
+};
+
 template <typename T>
 struct Ops {
   // Kernel-parameter tables (1D class tables, FDM eigendata, prolongation)
   // converted to T; opaque, freed with free_tables.
   static void* make_tables(const Setup1D& s, int d);
   static void free_tables(void* tab, int k);
+  static DevTables device_tables(const void* tab, int k);
 
   // mode kStore: y = scale * A_ref x; mode kResidual: y = b - scale * A_ref x.
   static cudaError_t apply(const void* tab, const LevelGeom& g, const T* x, const T* b, T* y,

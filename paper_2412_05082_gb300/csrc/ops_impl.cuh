@@ -15,6 +15,7 @@ template <typename T, int K>
 struct HostTables {
   Tables<T, K> t;
   MvsTab<T, K> mvs;  // operator + FDM tables for the fused MVS kernel
+  Tables<T, K>* dev = nullptr;  // device copy of t (batched kernels read it from memory)
   T* dinv = nullptr;  // device, 4^d slots x m^d reciprocals of the eigenvalue sums
   int d = 0;
 };
@@ -59,10 +60,17 @@ static void* make_tables_k(const Setup1D& s, int d) {
       dinv[(size_t)slot * md + l] = (T)(1.0 / sum);
     }
   h->d = d;
+  if (cudaMalloc(&h->dev, sizeof(Tables<T, K>)) != cudaSuccess ||
+      cudaMemcpy(h->dev, &h->t, sizeof(Tables<T, K>), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(h->dev);
+    delete h;
+    return nullptr;
+  }
   if (cudaMalloc(&h->dinv, dinv.size() * sizeof(T)) != cudaSuccess ||
       cudaMemcpy(h->dinv, dinv.data(), dinv.size() * sizeof(T), cudaMemcpyHostToDevice) !=
           cudaSuccess) {
     cudaFree(h->dinv);
+    cudaFree(h->dev);
     delete h;
     return nullptr;
   }
@@ -101,7 +109,27 @@ template <typename T, int K>
 static void free_tables_k(void* p) {
   auto* h = static_cast<HostTables<T, K>*>(p);
   cudaFree(h->dinv);
+  cudaFree(h->dev);
   delete h;
+}
+
+template <typename T, int K>
+static DevTables device_tables_k(const void* p) {
+  const auto* h = static_cast<const HostTables<T, K>*>(p);
+  return DevTables{h->dev, h->dinv};
+}
+
+template <typename T>
+DevTables Ops<T>::device_tables(const void* p, int k) {
+  switch (k) {
+    case 2: return device_tables_k<T, 2>(p);
+    case 3: return device_tables_k<T, 3>(p);
+    case 4: return device_tables_k<T, 4>(p);
+    case 5: return device_tables_k<T, 5>(p);
+    case 6: return device_tables_k<T, 6>(p);
+    case 7: return device_tables_k<T, 7>(p);
+  }
+  return DevTables{nullptr, nullptr};
 }
 
 template <typename T>
