@@ -209,6 +209,60 @@ bh_status bh_batch_solve(bh_batch* batch, const double* const* b_dev, double* co
 /* Kernel and graph launches issued by the batch so far. */
 bh_status bh_batch_stats(const bh_batch* batch, long long* launches);
 
+/* ---- serving form (no counterpart in the paper: a deployment form) --------
+ * A request loop of solves with continuous batching: `slots` worker threads
+ * each run one solve at a time on a resident hierarchy (pooled by dim,
+ * degree, level and precision; each with its own CUDA stream), so solves of
+ * different slots overlap on the device.  A request whose shape has no idle
+ * hierarchy is admitted when the footprint estimate of a new one fits the
+ * memory budget, after evicting idle hierarchies least recently used first;
+ * otherwise it waits for running solves to release memory.  A request starts
+ * as soon as a slot and its memory are free.  Precision: the FP32 V-cycle in
+ * flexible FP64 GMRES for degrees <= mixed_max_degree, FP64 otherwise; right
+ * preconditioning (true residual).  A request's result does not depend on the
+ * other requests in flight. */
+typedef struct bh_server bh_server;
+
+typedef struct {
+  int slots;                /* concurrent solves (worker threads), 1..64 */
+  double mem_budget_bytes;  /* device memory the resident hierarchies may use */
+  int mixed_max_degree;     /* FP32 V-cycle for k <= this, FP64 above (default 4) */
+  double rtol;              /* GMRES relative tolerance (default 1e-8) */
+  int maxit;                /* GMRES iteration limit (default 200) */
+  int gmres_restart;        /* restart length (default 30) */
+  int64_t queue_capacity;   /* submissions beyond this many queued fail with BH_EBUSY */
+} bh_server_config;
+
+typedef struct {
+  int status;        /* bh_status of the solve (BH_ENOMEM: larger than the budget) */
+  int iters;
+  double relres;     /* true relative residual */
+  double latency_s;  /* completion - submission */
+  double service_s;  /* time on a slot (the solve itself) */
+} bh_server_result;
+
+/* Defaults: 4 slots, 80 % of the currently free device memory, above. */
+bh_status bh_server_default_config(bh_server_config* cfg);
+bh_status bh_server_create(const bh_server_config* cfg, bh_server** out);
+
+/* Queue a solve of the (dim, degree, level) problem with right-hand side b_host
+ * (n host doubles); the solution is written to x_host.  Both host buffers stay
+ * owned by the caller and must stay valid until bh_server_wait returns for
+ * the ticket.  Returns at once with *ticket. */
+bh_status bh_server_submit(bh_server* server, int dim, int degree, int level,
+                           const double* b_host, double* x_host, int64_t* ticket);
+
+/* Wait up to timeout_s seconds (< 0: forever) for a ticket; fills *result and
+ * releases the ticket.  BH_ETIMEOUT if still running. */
+bh_status bh_server_wait(bh_server* server, int64_t ticket, double timeout_s,
+                         bh_server_result* result);
+
+/* Queue, slot and memory counters as a JSON object. */
+bh_status bh_server_stats(bh_server* server, char* buf, size_t len);
+
+/* Finish the queued requests, stop the workers, free every hierarchy. */
+bh_status bh_server_destroy(bh_server* server);
+
 /* y = A_l x like bh_apply_A, for callers that cannot allocate device memory:
  * for example a plugin inside a framework that owns every device allocation
  * and forbids allocation while it executes, or a latency-critical loop that

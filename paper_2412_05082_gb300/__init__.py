@@ -72,6 +72,27 @@ SIGNATURES = {
     "bh_batch_stats": (_I, [_P, _c.POINTER(_c.c_longlong)]),
 }
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("mem_budget_bytes", ctypes.c_double),
+                ("mixed_max_degree", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("gmres_restart", ctypes.c_int),
+                ("queue_capacity", ctypes.c_int64)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("relres", ctypes.c_double),
+                ("latency_s", ctypes.c_double), ("service_s", ctypes.c_double)]
+
+
+SIGNATURES.update({
+    "bh_server_default_config": (_I, [_c.POINTER(ServerConfig)]),
+    "bh_server_create": (_I, [_c.POINTER(ServerConfig), _c.POINTER(_P)]),
+    "bh_server_submit": (_I, [_P, _I, _I, _I, _P, _P, _c.POINTER(_I64)]),
+    "bh_server_wait": (_I, [_P, _I64, _D, _c.POINTER(ServerResult)]),
+    "bh_server_stats": (_I, [_P, _c.c_char_p, _c.c_size_t]),
+    "bh_server_destroy": (_I, [_P]),
+})
+
 _lib = None
 
 
@@ -311,3 +332,62 @@ class Batch:
         if st != BH_ENOCONV or raise_on_noconv:
             _check(st)
         return list(it), list(rr)
+
+
+class Server:
+    """Continuous-batching solve server (resident hierarchies, admission by
+    device-memory footprint, overlapping solves on several slots)."""
+
+    def __init__(self, **cfg):
+        c = ServerConfig()
+        _check(load().bh_server_default_config(ctypes.byref(c)))
+        for k, v in cfg.items():
+            if not hasattr(c, k):
+                raise KeyError(k)
+            setattr(c, k, v)
+        self.config = c
+        h = ctypes.c_void_p()
+        _check(load().bh_server_create(ctypes.byref(c), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, dim, degree, level, b, x):
+        """b, x: contiguous float64 numpy arrays (kept alive until wait)."""
+        import numpy as np
+        n = (degree * 2 ** level - 1) ** dim
+        for a in (b, x):
+            if not isinstance(a, np.ndarray) or a.dtype != np.float64 or a.size != n \
+                    or not a.flags.c_contiguous:
+                raise ValueError("b and x must be contiguous float64 arrays with %d values" % n)
+        t = ctypes.c_int64()
+        _check(load().bh_server_submit(self._h, dim, degree, level, b.ctypes.data, x.ctypes.data,
+                                       ctypes.byref(t)))
+        self._keep[t.value] = (b, x)
+        return t.value
+
+    def wait(self, ticket, timeout=-1.0):
+        r = ServerResult()
+        _check(load().bh_server_wait(self._h, ticket, timeout, ctypes.byref(r)))
+        self._keep.pop(ticket, None)
+        return {"status": r.status, "iters": r.iters, "relres": r.relres,
+                "latency_s": r.latency_s, "service_s": r.service_s}
+
+    def stats(self):
+        import json
+        buf = ctypes.create_string_buffer(4096)
+        _check(load().bh_server_stats(self._h, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(load().bh_server_destroy(self._h))
+            self._h = None
+            self._keep.clear()
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
