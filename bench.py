@@ -149,6 +149,86 @@ print(json.dumps({"t": t_tot, "dofs": dofs, "ks": done}))
             "host_cpus": os.cpu_count()}
 
 
+def measure_batched(bh, torch, stream):
+    """The batched form on 64 independent 2D problems (k ~ U{2..7}, levels
+    with 1e4-1e6 DoFs, seed 1234): one solve of all of them in lockstep with
+    autotuned tiles, against the same problems solved one after another."""
+    from paper_2412_05082_gb300 import autotune
+    import time
+    probs = workload.batch_problems(64, 1234)
+    tiles = autotune.tiles_for([k for _, k, _ in probs])
+    params = [bh.default_params(d, k, L) for d, k, L in probs]
+    bs = [torch.tensor(workload.rhs_uniform((k * 2 ** L - 1) ** 2, i), dtype=torch.float64,
+                       device="cuda") for i, (d, k, L) in enumerate(probs)]
+    xs = [torch.empty_like(b) for b in bs]
+    dofs = sum(workload.paper_dofs(d, k, 2 ** L) for d, k, L in probs)
+    with bh.Batch(params, stream) as batch:
+        for k, pb in tiles.items():
+            batch.set_tile(k, pb)
+        batch.solve(bs, xs, 1e-8, 50)
+        torch.cuda.synchronize()
+        l0 = batch.launches()
+        t0 = time.perf_counter()
+        its, rr = batch.solve(bs, xs, 1e-8, 50)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        launches = batch.launches() - l0
+    ctxs = [bh.Context(p, stream) for p in params]
+    for c, b, x in zip(ctxs, bs, xs):
+        c.solve(b, x, 1e-8, 50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its1 = [c.solve(b, x, 1e-8, 50)[0] for c, b, x in zip(ctxs, bs, xs)]
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    return {"workload": "64 independent 2D problems, k ~ U{2..7}, levels with 1e4-1e6 DoFs "
+                        "(seed 1234), uniform[-1,1] RHS, FP64 MG-GMRES (MVS, left) to 1e-8",
+            "dofs": dofs, "value": dofs / tb, "unit": UNIT, "seconds": tb,
+            "launches_per_solve": launches, "tiles_patches_per_block": tiles,
+            "sequential_value": dofs / ts, "speedup_vs_sequential": ts / tb,
+            "iterations_equal_to_sequential": sum(a == b for a, b in zip(its, its1)),
+            "max_iters": max(its)}
+
+
+def measure_serving(bh, nreq):
+    """The serving form on the first nreq requests of the Poisson stream
+    (rate 200/s, seed 2024; 2D and 3D, k = 2..7, 1e4-2e7 DoFs), replayed at
+    their arrival times: p50/p99 latency and throughput with 8 slots, against
+    the same requests solved one after another on one slot (FP64)."""
+    import time
+    import numpy as np
+    reqs = workload.serving_requests(1000, 200.0, 2024)[:nreq]
+    rhs = [workload.rhs_uniform((k * 2 ** L - 1) ** d, s) for _, d, k, L, s in reqs]
+    dofs = sum(workload.paper_dofs(d, k, 2 ** L) for _, d, k, L, _ in reqs)
+    out = {"workload": "first %d requests of the Poisson stream (200 req/s, seed 2024), 2D and "
+                       "3D, k = 2..7, 1e4-2e7 DoFs, uniform[-1,1] RHS, to 1e-8 (true residual)"
+                       % nreq, "dofs": dofs}
+    for slots, mixed in ((8, 4), (1, 0)):
+        xs = [np.zeros_like(b) for b in rhs]
+        with bh.Server(slots=slots, mixed_max_degree=mixed) as srv:
+            start = time.perf_counter()
+            tickets = []
+            for (ta, d, k, L, _), b, x in zip(reqs, rhs, xs):
+                while time.perf_counter() - start < ta:
+                    time.sleep(0.0002)
+                tickets.append(srv.submit(d, k, L, b, x))
+            res = [srv.wait(t) for t in tickets]
+            wall = time.perf_counter() - start
+            st = srv.stats()
+        lat = np.array([r["latency_s"] for r in res])
+        key = "served" if slots > 1 else "plain_fp64_one_slot"
+        out[key] = {"slots": slots, "precision": "FP32 V-cycle for k<=4, FP64 above" if mixed
+                    else "FP64", "value": dofs / wall, "unit": UNIT, "wall_s": wall,
+                    "p50_latency_s": float(np.percentile(lat, 50)),
+                    "p99_latency_s": float(np.percentile(lat, 99)),
+                    "failed": int(sum(r["status"] != 0 for r in res)),
+                    "max_relres": float(max(r["relres"] for r in res)),
+                    "hierarchies_created": st["created"], "evictions": st["evictions"]}
+    return out
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle timed as it stands, each step a bounded
     sample of the workload (2D, k = 2..7, N = 8: one MG-GMRES solve each)."""
@@ -194,6 +274,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and serving measurements")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests of the Poisson stream replayed by the serving measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         # the oracle needs no GPU: keep this process off the devices entirely
@@ -358,6 +442,9 @@ def main():
                     row["mixed_right_iters"] = itm[0]
             bd["k%d" % k] = row
         result["breakdown_dofs_per_s"] = bd
+    if not args.no_forms:
+        result["batched"] = measure_batched(bh, torch, stream)
+        result["serving"] = measure_serving(bh, args.serve_requests)
     if cpu is not None:
         result["cpu_baseline"] = cpu
     if rank == 0:
