@@ -1,16 +1,19 @@
 """Benchmark of the GB300 C0IP biharmonic multigrid (arXiv 2412.05082).
 
-One step = one pass of the whole hot path over the workload: for every
-problem of the 2D sweep (Q2-Q4 on 512^2 cells, Q5-Q7 on 256^2 cells), an
-FP64 MG-GMRES solve to a 1e-8 relative reduction (colored MVS, one pre- and
-one post-smoothing step, fast-diagonalization local solvers, left
+One step = one pass of the whole hot path over the workload: the six
+problems of the 2D sweep (Q2-Q4 on 512^2 cells, Q5-Q7 on 256^2 cells), each
+solved by FP64 MG-GMRES to a 1e-8 relative reduction (colored MVS, one pre-
+and one post-smoothing step, fast-diagonalization local solvers, left
 preconditioning: the protocol of Sec. 5.1), which runs apply_A, the residual,
-the patch gather / solve / scatter, the transfers, the V-cycle and GMRES.
+the patch gather / solve / scatter, the transfers, the V-cycle and GMRES.  The
+six solves run as one batch (bh_batch_solve: each level operation one launch
+over all problems, the lockstep V-cycle replayed as a CUDA graph); every
+problem takes the iterations and arithmetic of its own solve.
 
 value = sum of the paper's DoF counts (kN+1)^2 solved / device time (CUDA
 events), the solve inputs resident in HBM; L2 is flushed (256 MiB write)
-before every timed step.  e2e = the same through bh_solve_host with pinned
-host buffers (copies inside the timed region).
+before every timed step.  e2e = the same through bh_batch_solve_host with
+pinned host buffers (copies inside the timed region).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 run one process per GPU (torchrun); the solves are independent
@@ -41,7 +44,7 @@ def config_for(problems, precision="fp64"):
     return {
         "workload": "2D C0IP biharmonic sweep (paper sizes): Q2-Q4 on 512^2 and Q5-Q7 on 256^2 "
                     "cells; MG-GMRES to 1e-8 (colored MVS 1+1, FDM local solver, left "
-                    "preconditioning, restart 50), %s" % precision,
+                    "preconditioning, restart 50), %s; the six solves run as one batch" % precision,
         "problems": [{"d": d, "k": k, "cells": N, "dofs": workload.paper_dofs(d, k, N)}
                      for d, k, N in problems],
         "dof_count": "(kN+1)^d including boundary nodes (the paper's convention)",
@@ -58,6 +61,18 @@ def flop_per_unknown_apply(d, k):
     2 (5k + 6) FMAs per unknown; 3D: x-split 5k+6, y-mix 8k+12, z 5k+6."""
     fma = 2 * (5 * k + 6) if d == 2 else (5 * k + 6) + (8 * k + 12) + (5 * k + 6)
     return 2 * fma
+
+
+def mvs2_fma_per_patch(k):
+    """FP64 FMAs of the fused 2D colored-MVS kernel per patch (m = 2k-1,
+    window 4k+1): x-split T_M on the window rows and T_L, T_B on the 2k+1
+    middle rows, y-combination on the m^2 patch nodes, four FDM contractions
+    and the eigenvalue scaling.  Band sums over the m patch positions: M and L
+    hold (2k+1) + (2k-2)(k+1) entries, B (4k+1) + (2k-2)(3k+1)."""
+    m, w, wm = 2 * k - 1, 4 * k + 1, 2 * k + 1
+    sm = (2 * k + 1) + (2 * k - 2) * (k + 1)
+    sb = (4 * k + 1) + (2 * k - 2) * (3 * k + 1)
+    return w * sm + wm * sm + wm * sb + m * (sb + 2 * sm) + 4 * m ** 3 + m * m
 
 
 class Clocks:
@@ -304,6 +319,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     problems = workload.SWEEP_2D
+    from paper_2412_05082_gb300 import autotune
+    tiles = autotune.tiles_for([k for _, k, _ in problems])
     ctxs, rhs, xs, hostb, hostx = [], [], [], [], []
     for d, k, N in problems:
         L = workload.level_of(N)
@@ -315,16 +332,20 @@ def main():
         xs.append(torch.empty(n, dtype=torch.float64, device=dev))
         hostb.append(torch.tensor(b, dtype=torch.float64).pin_memory())
         hostx.append(torch.empty(n, dtype=torch.float64).pin_memory())
+    batch = bh.Batch([bh.default_params(d, k, workload.level_of(N)) for d, k, N in problems],
+                     stream)
+    for k, pb in tiles.items():
+        batch.set_tile(k, pb)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     iters = {}
 
     def step():
-        for (d, k, N), ctx, b, x in zip(problems, ctxs, rhs, xs):
-            iters[k] = ctx.solve(b, x, 1e-8, 200)
+        its, rrs = batch.solve(rhs, xs, 1e-8, 50)
+        for (d, k, N), it, rr in zip(problems, its, rrs):
+            iters[k] = (it, rr)
 
     def step_host():
-        for ctx, b, x in zip(ctxs, hostb, hostx):
-            ctx.solve_host(b, x, 1e-8, 200)
+        batch.solve_host(hostb, hostx, 1e-8, 50)
 
     def timed(fn, steps):
         ts = []
@@ -378,7 +399,7 @@ def main():
         "iterations": {str(k): {"iters": it, "true_relres": rr} for k, (it, rr) in iters.items()},
     }
 
-    # dominant kernel: the apply_A / residual sweeps (8 per MVS step, 16+ per V-cycle)
+    # dominant kernel: the fused colored-MVS kernel (8 launches per smoothing step)
     def time_op(fn, reps=10):
         fn()
         ts = []
@@ -397,20 +418,29 @@ def main():
     d, k, N = problems[i4]
     L = workload.level_of(N)
     ctx = ctxs[i4]
-    n = ctx.num_unknowns()
-    r = torch.empty(n, dtype=torch.float64, device=dev)
-    t_res = time_op(lambda: ctx.residual(L, xs[i4], rhs[i4], r), 20)
-    flops = flop_per_unknown_apply(d, k) * n
-    achieved = flops / t_res / 1e12
+    xr = torch.zeros_like(xs[i4])
+    t_step = time_op(lambda: ctx.smooth(L, xr, rhs[i4], 1), 10)
+    patches = (N - 1) ** 2
+    flops_launch = 2 * mvs2_fma_per_patch(k) * patches / 8   # one launch = one color
+    achieved = flops_launch / (t_step / 8) / 1e12
     result["roofline"] = {
-        "kernel": "residual r = b - A x: sweep_kernel x-split + y-combine (2 launches), 2D Q4 512^2",
+        "kernel": "mvs2_color_kernel (fused colored MVS: local residual + FDM + update), "
+                  "2D Q4 512^2, one launch per color",
         "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
         "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (derived; no FP64 entry in "
                        "the measured peaks file)",
-        "flops_per_unknown": flop_per_unknown_apply(d, k), "unknowns": n,
-        "launch_ms": t_res * 1e3,
+        "fma_per_patch": mvs2_fma_per_patch(k), "patches_per_launch": patches / 8,
+        "launch_ms": t_step / 8 * 1e3,
     }
+    n4 = ctx.num_unknowns()
+    r4 = torch.empty(n4, dtype=torch.float64, device=dev)
+    t_res = time_op(lambda: ctx.residual(L, xs[i4], rhs[i4], r4), 20)
+    result["roofline_residual_sweeps"] = {
+        "kernel": "sweep_kernel x-split + y-combine (residual), 2D Q4 512^2", "bound": "alu",
+        "achieved": flop_per_unknown_apply(d, k) * n4 / t_res / 1e12, "peak": FP64_PEAK_TFLOPS,
+        "unit": "TFLOP/s",
+        "frac": flop_per_unknown_apply(d, k) * n4 / t_res / 1e12 / FP64_PEAK_TFLOPS}
 
     if not args.no_breakdown:
         bd = {}
@@ -420,12 +450,13 @@ def main():
             n = ctx.num_unknowns()
             y = torch.empty(n, dtype=torch.float64, device=dev)
             row = {"dofs": dofs, "solve_iters": iters[k][0]}
+            row["true_relres"] = iters[k][1]
             row["apply"] = dofs / time_op(lambda: ctx.apply_A(L, b, y))
             for sm, name in ((bh.AVS_ATOMIC, "avs_atomic"), (bh.AVS_COLORED, "avs_colored"),
                              (bh.MVS_COLORED, "mvs")):
                 with bh.Context(bh.default_params(d, k, L, smoother=sm), stream) as c2:
                     row[name + "_step"] = dofs / time_op(lambda: c2.smooth(L, y, b, 1), 5)
-            row["solve_fp64"] = dofs / time_op(lambda: ctx.solve(b, x, 1e-8, 200), 3)
+            row["solve_fp64_single"] = dofs / time_op(lambda: ctx.solve(b, x, 1e-8, 200), 3)
             # flexible right-preconditioned GMRES on the true residual: FP64 and
             # the FP32 V-cycle of Sec. 5.2 (shown there for Q2-Q4) side by side
             with bh.Context(bh.default_params(d, k, L, gmres_side=bh.RIGHT), stream) as c2:
@@ -451,6 +482,7 @@ def main():
         print(json.dumps(result), flush=True)
     for c in ctxs:
         c.close()
+    batch.close()
     if dist:
         dist.destroy_process_group()
     return 0

@@ -206,6 +206,12 @@ bh_status bh_batch_vcycle_time(bh_batch* batch, int reps, double* ms);
 bh_status bh_batch_solve(bh_batch* batch, const double* const* b_dev, double* const* x_dev,
                          double rtol, int maxit, int* iters, double* relres);
 
+/* bh_batch_solve with host buffers: b_host[i], x_host[i] (pinned or pageable)
+ * are copied through device staging buffers inside the call.  Synchronous. */
+bh_status bh_batch_solve_host(bh_batch* batch, const double* const* b_host,
+                              double* const* x_host, double rtol, int maxit, int* iters,
+                              double* relres);
+
 /* Kernel and graph launches issued by the batch so far. */
 bh_status bh_batch_stats(const bh_batch* batch, long long* launches);
 

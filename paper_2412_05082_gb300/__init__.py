@@ -70,6 +70,7 @@ SIGNATURES = {
     "bh_batch_vcycle_time": (_I, [_P, _I, _c.POINTER(_D)]),
     "bh_batch_solve": (_I, [_P, _P, _P, _D, _I, _P, _P]),
     "bh_batch_stats": (_I, [_P, _c.POINTER(_c.c_longlong)]),
+    "bh_batch_solve_host": (_I, [_P, _P, _P, _D, _I, _P, _P]),
 }
 
 class ServerConfig(ctypes.Structure):
@@ -318,6 +319,26 @@ class Batch:
         n = ctypes.c_longlong()
         _check(load().bh_batch_stats(self._h, ctypes.byref(n)))
         return n.value
+
+    def solve_host(self, bs, xs, rtol=1e-8, maxit=50):
+        """bs, xs: contiguous float64 host arrays (numpy or CPU tensors)."""
+        import numpy as np
+        P = len(self.params)
+        arrs = []
+        for a, n in zip(list(bs) + list(xs), self.sizes() * 2):
+            arr = a.numpy() if hasattr(a, "numpy") else a
+            if arr.dtype != np.float64 or arr.size != n or not arr.flags.c_contiguous:
+                raise ValueError("host buffers must be contiguous float64 arrays of the right size")
+            arrs.append(arr)
+        bp = (ctypes.c_void_p * P)(*[a.ctypes.data for a in arrs[:P]])
+        xp = (ctypes.c_void_p * P)(*[a.ctypes.data for a in arrs[P:]])
+        it = (ctypes.c_int * P)()
+        rr = (ctypes.c_double * P)()
+        _check(load().bh_batch_solve_host(self._h, ctypes.cast(bp, ctypes.c_void_p),
+                                          ctypes.cast(xp, ctypes.c_void_p), rtol, maxit,
+                                          ctypes.cast(it, ctypes.c_void_p),
+                                          ctypes.cast(rr, ctypes.c_void_p)))
+        return list(it), list(rr)
 
     def solve(self, bs, xs, rtol=1e-8, maxit=50, raise_on_noconv=True):
         P = len(self.params)

@@ -316,7 +316,9 @@ struct bh_batch {
   SolvePlan* plan = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  long long launches = 0;
+  std::vector<double*> stage_b, stage_x;  // device staging for bh_batch_solve_host
+  long long launches = 0;        // kernels run by the batch (graph replays count their nodes)
+  long long graph_kernels = 0;   // kernel nodes of the captured V-cycle graph
   std::vector<int> last_iters;
 };
 
@@ -683,17 +685,25 @@ bh_status capture_vcycle(bh_batch* b) {
   }
   VecOpList zero_fine;
   BCKS(make_vec(b, zf, zero_fine));
+  const long long before = b->launches, before_g = g_kernel_launches.load();
   BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = run_vec(b, zero_fine, kZero, nullptr, 0, 0, 0.0);
   if (e == cudaSuccess) e = vcycle_from(b, 0);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+  // captured kernels run when the graph is replayed and are counted then
+  g_kernel_launches.fetch_sub(b->launches - before);
+  b->launches = before;
+  (void)before_g;
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return berr(BH_ECUDA, std::string("V-cycle capture failed: ") +
                               cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
   b->graph = g;
+  size_t nodes = 0;
+  BCK(cudaGraphGetNodes(g, nullptr, &nodes));
+  b->graph_kernels = (long long)nodes;
   BCK(cudaGraphInstantiate(&b->gexec, g, 0));
   return BH_OK;
 }
@@ -940,7 +950,8 @@ bh_status bh_batch_solve(bh_batch* b, const double* const* b_dev, double* const*
   // r0 = M^-1 b: b_L = b, V-cycle into x_L; beta = ||x_L||, ||b||
   BCK(run_vec(b, S.copy_b, kCopy, nullptr, 0, 0, 0.0));
   BCK(cudaGraphLaunch(b->gexec, b->st));
-  b->launches++;
+  b->launches += b->graph_kernels;
+  g_kernel_launches.fetch_add(b->graph_kernels);
   BCK(run_dot(b, S.ww, 0));
   BCK(run_dot(b, S.bnorm, 1));
   std::vector<double>& hd = S.hd;
@@ -967,7 +978,8 @@ bh_status bh_batch_solve(bh_batch* b, const double* const* b_dev, double* const*
     BCK(run_sweep(b, S.apply_x[j], 0));  // b_L = A V_j
     BCK(run_sweep(b, S.apply_y, 2));
     BCK(cudaGraphLaunch(b->gexec, b->st));  // w = x_L = M^-1 b_L
-    b->launches++;
+    b->launches += b->graph_kernels;
+    g_kernel_launches.fetch_add(b->graph_kernels);
     for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
       BCK(run_dot(b, S.wV, i, 0, i));
       BCK(run_vec(b, S.wV, kAxpyDev, b->d_dots, cs, i, -1.0, 0, i));
@@ -1039,6 +1051,37 @@ bh_status bh_batch_solve(bh_batch* b, const double* const* b_dev, double* const*
   }
   if (!all_conv) return berr(BH_ENOCONV, "batched GMRES: some problems did not reach the tolerance");
   return BH_OK;
+}
+
+bh_status bh_batch_solve_host(bh_batch* b, const double* const* b_host, double* const* x_host,
+                              double rtol, int maxit, int* iters, double* relres) {
+  if (!b || !b_host || !x_host || !iters || !relres)
+    return berr(BH_EINVAL, "bh_batch_solve_host: bad arguments");
+  if (b->stage_b.empty()) {
+    for (int p = 0; p < b->P; ++p) {
+      const size_t bytes = b->ctx[p]->lv[b->L[p]].g.nd * sizeof(double);
+      double *db = nullptr, *dx = nullptr;
+      if (cudaMalloc(&db, bytes) != cudaSuccess || cudaMalloc(&dx, bytes) != cudaSuccess) {
+        cudaFree(db);
+        cudaGetLastError();
+        return berr(BH_ENOMEM, "staging allocation failed");
+      }
+      b->allocs.push_back(db);
+      b->allocs.push_back(dx);
+      b->stage_b.push_back(db);
+      b->stage_x.push_back(dx);
+    }
+  }
+  for (int p = 0; p < b->P; ++p)
+    BCK(cudaMemcpyAsync(b->stage_b[p], b_host[p], b->ctx[p]->lv[b->L[p]].g.nd * sizeof(double),
+                        cudaMemcpyHostToDevice, b->st));
+  bh_status s = bh_batch_solve(b, b->stage_b.data(), b->stage_x.data(), rtol, maxit, iters, relres);
+  if (s != BH_OK && s != BH_ENOCONV) return s;
+  for (int p = 0; p < b->P; ++p)
+    BCK(cudaMemcpyAsync(x_host[p], b->stage_x[p], b->ctx[p]->lv[b->L[p]].g.nd * sizeof(double),
+                        cudaMemcpyDeviceToHost, b->st));
+  BCK(cudaStreamSynchronize(b->st));
+  return s;
 }
 
 bh_status bh_batch_stats(const bh_batch* b, long long* launches) {
