@@ -427,7 +427,10 @@ def main():
         "kernel": "mvs2_color_kernel (fused colored MVS: local residual + FDM + update), "
                   "2D Q4 512^2, one launch per color",
         "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+        "frac": achieved / FP64_PEAK_TFLOPS,
+        # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in this
+        # configuration (profiles/mvs2_color_kernel_q4_512.md)
+        "traffic": 63.69e6, "traffic_unit": "bytes per launch",
         "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (derived; no FP64 entry in "
                        "the measured peaks file)",
         "fma_per_patch": mvs2_fma_per_patch(k), "patches_per_launch": patches / 8,
