@@ -429,7 +429,7 @@ def main():
         "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS,
         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in this
-        # configuration (profiles/mvs2_color_kernel_q4_512.md)
+        # configuration, from one ncu capture of the unchanged kernel
         "traffic": 63.69e6, "traffic_unit": "bytes per launch",
         "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (derived; no FP64 entry in "
                        "the measured peaks file)",
