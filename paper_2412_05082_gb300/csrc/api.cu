@@ -130,7 +130,7 @@ bh_status smooth_t(bh_ctx* c, int l, T* x, const T* b, int steps, bool x_zero) {
   const int d = c->p.dim, nc = c->ncolors();
   for (int s = 0; s < steps; ++s) {
     const bool zero = x_zero && s == 0;
-    if (c->p.smoother == BH_MVS_COLORED && d == 2 && c->p.local_solver == BH_FDM) {
+    if (c->p.smoother == BH_MVS_COLORED && c->p.local_solver == BH_FDM) {
       // fused kernel: local residual, fast diagonalization and update per patch
       for (int col = 0; col < nc; ++col)
         CK(Ops<T>::mvs_color(TypeOf<T>::tab(c), L.g, x, b, L.verts + L.coff[col],

@@ -49,7 +49,7 @@ struct Ops {
                                const int* verts, int count, double scale, bool atomic,
                                cudaStream_t st);
 
-  // One color of the colored MVS, fused (2D, fast diagonalization): for every
+  // One color of the colored MVS, fused (2D and 3D, fast diagonalization): for every
   // patch v in verts, x_v += pscale * A~_v,ref^-1 R_v (b - ascale * A_ref x).
   static cudaError_t mvs_color(const void* tab, const LevelGeom& g, T* x, const T* b,
                                const int* verts, int count, double ascale, double pscale,

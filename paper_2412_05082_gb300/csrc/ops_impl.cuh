@@ -8,6 +8,7 @@
 
 #include "kernels.cuh"
 #include "mvs.cuh"
+#include "mvs3.cuh"
 
 namespace bh {
 
@@ -286,14 +287,49 @@ static cudaError_t mvs_color_k(const void* tabp, const LevelGeom& g, T* x, const
   return cudaGetLastError();
 }
 
+template <typename T, int K>
+static cudaError_t mvs3_color_k(const void* tabp, const LevelGeom& g, T* x, const T* b,
+                                const int* verts, int count, double ascale, double pscale,
+                                cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const auto* h = static_cast<const HostTables<T, K>*>(tabp);
+  MvsArgs<T> a{};
+  a.x = x;
+  a.b = b;
+  a.verts = verts;
+  a.count = count;
+  a.N = g.N;
+  a.n = g.n;
+  a.ascale = ascale;
+  a.pscale = pscale;
+  a.dinv = h->dinv;
+  using C = Mvs3Cfg<T, K>;
+  int pb = (count + 2 * 152 - 1) / (2 * 152);
+  pb = pb < 1 ? 1 : (pb > C::PB_MAX ? C::PB_MAX : pb);
+  a.pb = pb;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      mvs3_color_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)C::smem_bytes(C::PB_MAX));
+  if (attr != cudaSuccess) return attr;
+  mvs3_color_kernel<T, K><<<(unsigned)((count + pb - 1) / pb), 256, C::smem_bytes(pb), st>>>(
+      h->mvs, a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t Ops<T>::mvs_color(const void* tab, const LevelGeom& g, T* x, const T* b,
                               const int* verts, int count, double ascale, double pscale,
                               cudaStream_t st) {
-  if (g.d != 2) return cudaErrorInvalidValue;
+  if (g.d == 2) {
 #define BH_CALL(KK) return mvs_color_k<T, KK>(tab, g, x, b, verts, count, ascale, pscale, st)
-  BH_K_DISPATCH(g.k, BH_CALL)
+    BH_K_DISPATCH(g.k, BH_CALL)
 #undef BH_CALL
+  } else {
+#define BH_CALL(KK) return mvs3_color_k<T, KK>(tab, g, x, b, verts, count, ascale, pscale, st)
+    BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  }
   return cudaErrorInvalidValue;
 }
 

@@ -109,6 +109,8 @@ SMOOTH_CASES = [
     (2, 6, 4, "mvs", "inexact"), (2, 3, 8, "mvs", "exact"), (2, 4, 4, "avs", "exact"),
     (3, 2, 4, "avs", "inexact"), (3, 2, 8, "mvs", "inexact"), (3, 3, 4, "mvs", "inexact"),
     (3, 2, 4, "mvs", "exact"), (2, 3, 2, "mvs", "inexact"), (3, 4, 2, "avs", "inexact"),
+    (3, 4, 4, "mvs", "inexact"), (3, 5, 4, "mvs", "inexact"), (3, 7, 2, "mvs", "inexact"),
+    (3, 6, 2, "mvs", "inexact"), (3, 3, 8, "mvs", "inexact"),
 ]
 
 
