@@ -9,7 +9,7 @@ A fine coefficient is the value of the coarse function at the fine support
 point; for tensor-product basis functions this is the Kronecker product of
 the 1D embedding matrices.  Restriction is its transpose.
 
-Coarse solver (Sec. 5.1 says "one smoothing step"): reading -- the default
+Coarse solver (Sec. 5.1 smooths the coarse grid once): reading -- the default
 solves the coarse system exactly (dense LU), which equals one exact-local-
 solver step with omega = 1 from a zero start because the coarse level is a
 single patch; coarse="smooth" applies one step of the level's smoother
