@@ -1,5 +1,5 @@
-"""Right-preconditioned restarted GMRES and the fractional iteration count
-(Sec. 5.1).
+"""Right-preconditioned restarted GMRES, preconditioned CG and the fractional
+iteration count (Sec. 5.1).
 
 The paper preconditions GMRES with one multigrid V-cycle and stops at a
 relative residual reduction of 1e-8; it does not state the restart length,
@@ -109,6 +109,47 @@ def gmres(A, b, M=None, rtol=1e-8, restart=50, maxit=1000, side="right"):
             break
         if side == "left":
             r = M(r)
+    return x, it, hist, np.linalg.norm(b - A @ x) / bnorm
+
+
+def cg(A, b, M=None, rtol=1e-8, maxit=1000, flexible=False):
+    """Preconditioned conjugate gradients (Sec. 5.1 pairs it with the additive
+    smoother, whose V-cycle is a symmetric preconditioner), x0 = 0.
+
+    Returns (x, iterations, history of ||r_j||_2, true relres).  The stopping
+    test is on the recursively updated, unpreconditioned residual,
+    ||r_j|| <= rtol ||r_0||, the convention of deal.II's CG that the paper's
+    tables follow.  flexible=True takes the Polak-Ribiere coefficient
+    beta_j = r_{j+1}.(z_{j+1} - z_j) / r_j.z_j, which keeps the method stable
+    when the preconditioner varies from one application to the next (the FP32
+    V-cycle); for a fixed preconditioner r_{j+1}.z_j = 0 and both coincide."""
+    if M is None:
+        M = lambda v: v
+    x = np.zeros(b.shape[0])
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, [0.0], 0.0
+    r = b.copy()
+    z = M(r)
+    p = z.copy()
+    rz = np.dot(r, z)
+    hist = [bnorm]
+    it = 0
+    while it < maxit:
+        q = A @ p
+        alpha = rz / np.dot(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        it += 1
+        rn = np.linalg.norm(r)
+        hist.append(rn)
+        if rn <= rtol * bnorm:
+            break
+        z_new = M(r)
+        rz_new = np.dot(r, z_new)
+        beta = (rz_new - np.dot(r, z)) / rz if flexible else rz_new / rz
+        p = z_new + beta * p
+        z, rz = z_new, rz_new
     return x, it, hist, np.linalg.norm(b - A @ x) / bnorm
 
 
