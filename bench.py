@@ -244,6 +244,41 @@ def measure_serving(bh, nreq):
     return out
 
 
+def breakdown_3d(bh, torch, dev, stream, time_op):
+    """The 3D sweep (Q2, Q3 on 128^3, Q4-Q7 on 64^3 cells): apply, one colored
+    MVS step (inexact; exact local solvers for k <= 4, whose dense inverses at
+    higher k take minutes to set up), the FP64 MG-GMRES solve and, for k <= 4,
+    the FP32 V-cycle inside flexible GMRES."""
+    out = {}
+    for d, k, N in workload.SWEEP_3D:
+        L = workload.level_of(N)
+        dofs = workload.paper_dofs(d, k, N)
+        row = {"dofs": dofs}
+        with bh.Context(bh.default_params(d, k, L), stream) as ctx:
+            n = ctx.num_unknowns()
+            b = torch.tensor(workload.rhs_uniform(n, k), dtype=torch.float64, device=dev)
+            x = torch.zeros_like(b)
+            y = torch.empty_like(b)
+            row["apply"] = dofs / time_op(lambda: ctx.apply_A(L, b, y), 5)
+            row["mvs_step"] = dofs / time_op(lambda: ctx.smooth(L, x, b, 1), 3)
+            it = ctx.solve(b, x, 1e-8, 100)
+            row["solve_fp64"] = dofs / time_op(lambda: ctx.solve(b, x, 1e-8, 100), 1)
+            row["solve_iters"], row["true_relres"] = it[0], it[1]
+        if k <= 4:
+            with bh.Context(bh.default_params(d, k, L, local_solver=bh.EXACT), stream) as c2:
+                row["mvs_exact_step"] = dofs / time_op(lambda: c2.smooth(L, x, b, 1), 3)
+            with bh.Context(bh.default_params(d, k, L, precision=bh.MIXED_FP32,
+                                              gmres_side=bh.RIGHT), stream) as c2:
+                itm = c2.solve(b, x, 1e-8, 100, raise_on_noconv=False)
+                row["solve_mixed_right"] = dofs / time_op(
+                    lambda: c2.solve(b, x, 1e-8, 100, raise_on_noconv=False), 1)
+                row["mixed_right_iters"] = itm[0]
+        del b, x, y
+        torch.cuda.empty_cache()
+        out["k%d" % k] = row
+    return out
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle timed as it stands, each step a bounded
     sample of the workload (2D, k = 2..7, N = 8: one MG-GMRES solve each)."""
@@ -459,6 +494,11 @@ def main():
                              (bh.MVS_COLORED, "mvs")):
                 with bh.Context(bh.default_params(d, k, L, smoother=sm), stream) as c2:
                     row[name + "_step"] = dofs / time_op(lambda: c2.smooth(L, y, b, 1), 5)
+            # exact local solvers (dense inverse per boundary-type combination)
+            for sm, name in ((bh.AVS_ATOMIC, "avs_exact"), (bh.MVS_COLORED, "mvs_exact")):
+                with bh.Context(bh.default_params(d, k, L, smoother=sm,
+                                                  local_solver=bh.EXACT), stream) as c2:
+                    row[name + "_step"] = dofs / time_op(lambda: c2.smooth(L, y, b, 1), 5)
             row["solve_fp64_single"] = dofs / time_op(lambda: ctx.solve(b, x, 1e-8, 200), 3)
             # flexible right-preconditioned GMRES on the true residual: FP64 and
             # the FP32 V-cycle of Sec. 5.2 (shown there for Q2-Q4) side by side
@@ -474,8 +514,16 @@ def main():
                     row["solve_mixed_right"] = dofs / time_op(
                         lambda: c2.solve(b, x, 1e-8, 200, raise_on_noconv=False), 3)
                     row["mixed_right_iters"] = itm[0]
+            # the additive smoother's protocol: two pre- and post-steps, CG
+            with bh.Context(bh.default_params(d, k, L, smoother=bh.AVS_ATOMIC, pre_steps=2,
+                                              post_steps=2, krylov=bh.CG), stream) as c2:
+                itc = c2.solve(b, x, 1e-8, 300, raise_on_noconv=False)
+                row["solve_avs2_cg"] = dofs / time_op(
+                    lambda: c2.solve(b, x, 1e-8, 300, raise_on_noconv=False), 2)
+                row["avs2_cg_iters"] = itc[0]
             bd["k%d" % k] = row
         result["breakdown_dofs_per_s"] = bd
+        result["breakdown3d_dofs_per_s"] = breakdown_3d(bh, torch, dev, stream, time_op)
     if not args.no_forms:
         result["batched"] = measure_batched(bh, torch, stream)
         result["serving"] = measure_serving(bh, args.serve_requests)

@@ -59,7 +59,12 @@ enum { BH_FP64 = 0, BH_MIXED_FP32 = 1 };
  * residual b - A x, whose FP64 rounding floor eps ||A|| ||x|| / ||b|| exceeds
  * 1e-8 on the paper's finest meshes. */
 enum { BH_RIGHT = 0, BH_LEFT = 1 };
-/* coarse solver on level 1 (Sec. 5.1: "one smoothing step"). */
+/* Krylov method of bh_solve (Sec. 5.1 pairs conjugate gradients with the
+ * additive smoother, whose V-cycle is symmetric, and GMRES with the
+ * multiplicative one). */
+enum { BH_GMRES = 0, BH_CG = 1 };
+/* coarse solver on level 1: the exact dense solve, or a single step of the
+ * level's smoother (Sec. 5.1). */
 enum { BH_COARSE_EXACT = 0, BH_COARSE_SMOOTH = 1 };
 /* right-hand sides for bh_rhs. */
 enum { BH_RHS_MANUFACTURED = 0, BH_RHS_PAPER_SINE = 1 };
@@ -79,6 +84,7 @@ typedef struct {
   int gmres_restart; /* restart length m (default 50) */
   int gmres_side;    /* BH_LEFT (default) | BH_RIGHT */
   int coarse;        /* BH_COARSE_EXACT (default) | BH_COARSE_SMOOTH */
+  int krylov;        /* BH_GMRES (default) | BH_CG (additive smoothers only) */
 } bh_params;
 
 /* Fill *out with the defaults above for (dim, degree, level): MVS, FDM,
@@ -127,14 +133,19 @@ bh_status bh_restrict(bh_ctx* ctx, int level, const double* rf_dev, double* bc_d
  * BH_MIXED_FP32).  In place on x_dev. */
 bh_status bh_vcycle(bh_ctx* ctx, int level, double* x_dev, const double* b_dev);
 
-/* Solve A_L x = b on the finest level with GMRES preconditioned by one V-cycle
- * (Sec. 5.1), x0 = 0, until the Givens estimate of the minimized residual
+/* Solve A_L x = b on the finest level with a Krylov method preconditioned by
+ * one V-cycle (Sec. 5.1), x0 = 0.
+ * BH_GMRES: until the Givens estimate of the minimized residual
  * (preconditioned for BH_LEFT, true for BH_RIGHT) has dropped by rtol relative
  * to its initial value, or maxit iterations.  Right preconditioning keeps the
- * preconditioned directions (flexible form), as the FP32 V-cycle requires.  On
- * return (synchronous) *iters holds the iteration count and *relres the true
- * ||b - A x|| / ||b|| in FP64.  BH_ENOCONV if rtol was not reached (x holds the
- * last iterate). */
+ * preconditioned directions (flexible form), as the FP32 V-cycle requires.
+ * BH_CG: preconditioned conjugate gradients until the recursively updated
+ * residual ||r_j|| <= rtol ||b||, or maxit iterations; with BH_MIXED_FP32 the
+ * Polak-Ribiere coefficient (flexible CG) is used.  BH_ENOCONV also if p.Ap
+ * <= 0 (the preconditioner is not positive definite).
+ * On return (synchronous) *iters holds the iteration count and *relres the
+ * true ||b - A x|| / ||b|| in FP64.  BH_ENOCONV if rtol was not reached (x
+ * holds the last iterate). */
 bh_status bh_solve(bh_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit,
                    int* iters, double* relres);
 
@@ -186,7 +197,7 @@ bh_status bh_setup_fdm(int degree, double gamma, int type, double* S, double* la
 typedef struct bh_batch bh_batch;
 
 /* count problems, params[i] each: dim 2, BH_MVS_COLORED, BH_FDM, BH_FP64,
- * BH_COARSE_EXACT, BH_LEFT (BH_EINVAL otherwise).  Allocates every hierarchy,
+ * BH_COARSE_EXACT, BH_LEFT, BH_GMRES (BH_EINVAL otherwise).  Allocates every hierarchy,
  * builds the work lists and captures the V-cycle graph.  Synchronous. */
 bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_batch** out);
 bh_status bh_batch_destroy(bh_batch* batch);

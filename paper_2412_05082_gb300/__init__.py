@@ -20,6 +20,7 @@ FDM, EXACT = 0, 1
 FP64, MIXED_FP32 = 0, 1
 RIGHT, LEFT = 0, 1
 COARSE_EXACT, COARSE_SMOOTH = 0, 1
+GMRES, CG = 0, 1
 RHS_MANUFACTURED, RHS_PAPER_SINE = 0, 1
 
 STATUS_NAMES = {0: "BH_OK", -1: "BH_EINVAL", -2: "BH_ENOMEM", -3: "BH_ECUDA",
@@ -38,7 +39,8 @@ class Params(ctypes.Structure):
                 ("local_solver", ctypes.c_int), ("pre_steps", ctypes.c_int),
                 ("post_steps", ctypes.c_int), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int), ("gmres_restart", ctypes.c_int),
-                ("gmres_side", ctypes.c_int), ("coarse", ctypes.c_int)]
+                ("gmres_side", ctypes.c_int), ("coarse", ctypes.c_int),
+                ("krylov", ctypes.c_int)]
 
 
 # every entry point of biharm.h with its ctypes signature

@@ -233,7 +233,21 @@ void destroy_ctx(bh_ctx* c) {
   delete c;
 }
 
+// device dot results, reduction partials and their pinned host copy
+bh_status ensure_scalars(bh_ctx* c) {
+  if (c->dots) return BH_OK;
+  const int cnt = std::max(1, c->p.gmres_restart) + 2;
+  CKS(dmalloc(c, &c->dots, (size_t)cnt));
+  CKS(dmalloc(c, &c->partials, (size_t)kDotBlocks));
+  if (cudaMallocHost((void**)&c->hdots, cnt * sizeof(double)) != cudaSuccess) {
+    c->hdots = nullptr;
+    return fail(BH_ENOMEM, "cudaMallocHost failed");
+  }
+  return BH_OK;
+}
+
 bh_status ensure_gmres(bh_ctx* c) {
+  CKS(ensure_scalars(c));
   if (c->V) return BH_OK;
   const int m = std::max(1, c->p.gmres_restart);
   const int64_t n = c->lv[c->p.level].g.nd;
@@ -242,12 +256,19 @@ bh_status ensure_gmres(bh_ctx* c) {
   CKS(dmalloc(c, &c->Z, (size_t)m * n));
   CKS(dmalloc(c, &c->w, (size_t)n));
   CKS(dmalloc(c, &c->t, (size_t)n));
-  CKS(dmalloc(c, &c->dots, (size_t)m + 2));
-  CKS(dmalloc(c, &c->partials, (size_t)kDotBlocks));
-  if (cudaMallocHost((void**)&c->hdots, (m + 2) * sizeof(double)) != cudaSuccess) {
-    c->hdots = nullptr;
-    return fail(BH_ENOMEM, "cudaMallocHost failed");
-  }
+  return BH_OK;
+}
+
+bh_status ensure_cg(bh_ctx* c) {
+  CKS(ensure_scalars(c));
+  if (c->cgv) return BH_OK;
+  return dmalloc(c, &c->cgv, (size_t)5 * c->lv[c->p.level].g.nd);
+}
+
+// copy the first cnt device dot results to the host (one synchronization)
+bh_status fetch_dots(bh_ctx* c, int cnt) {
+  CK(cudaMemcpyAsync(c->hdots, c->dots, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
   return BH_OK;
 }
 
@@ -287,8 +308,81 @@ bh_status arnoldi_column(bh_ctx* c, int j, double* hcol, double* hnorm) {
   return BH_OK;
 }
 
+// Preconditioned conjugate gradients, x0 = 0 (Sec. 5.1 uses it with the
+// additive smoother).  Stops on the recursively updated residual
+// ||r_j|| <= rtol ||b||.  The FP32 V-cycle is not a fixed linear operator, so
+// the mixed form takes the Polak-Ribiere coefficient
+// beta = r_{j+1}.(z_{j+1} - z_j) / r_j.z_j (flexible CG); for a fixed
+// preconditioner r_{j+1}.z_j = 0 and it equals r_{j+1}.z_{j+1} / r_j.z_j.
+bh_status solve_cg(bh_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters,
+                   double* relres) {
+  CKS(ensure_cg(c));
+  const int L = c->p.level;
+  Level& F = c->lv[L];
+  const int64_t n = F.g.nd;
+  const bool flexible = mixed(c);
+  double* r = c->cgv;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  double* zp = q + n;
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), c->st));
+  double bnorm;
+  CKS(norm2(c, b, &bnorm));
+  *iters = 0;
+  *relres = 0.0;
+  if (bnorm == 0.0) return BH_OK;
+  if (!std::isfinite(bnorm)) return fail(BH_EINVAL, "right-hand side is not finite");
+  CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CKS(precondition(c, r, z));
+  CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CK(vec_dot(r, z, n, c->partials, c->dots, c->st));
+  CKS(fetch_dots(c, 1));
+  double rz = c->hdots[0];
+  int it = 0;
+  double rn = bnorm;
+  while (it < maxit) {
+    CK(Ops<double>::apply(c->tab64, F.g, p, nullptr, q, F.ascale, kStore, c->scr64, c->st));
+    CK(vec_dot(p, q, n, c->partials, c->dots, c->st));
+    CKS(fetch_dots(c, 1));
+    const double pq = c->hdots[0];
+    if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rz))
+      return fail(BH_ENOCONV, "CG breakdown: p.Ap <= 0 or not finite after " +
+                                  std::to_string(it) + " iterations");
+    const double alpha = rz / pq;
+    CK(vec_axpy(x, alpha, p, n, c->st));
+    CK(vec_axpy(r, -alpha, q, n, c->st));
+    ++it;
+    CKS(norm2(c, r, &rn));
+    if (!std::isfinite(rn)) return fail(BH_ENOCONV, "CG breakdown: non-finite residual");
+    if (rn <= rtol * bnorm) break;
+    if (flexible) std::swap(z, zp);  // zp = z_j, z is overwritten by z_{j+1}
+    CKS(precondition(c, r, z));
+    CK(vec_dot(r, z, n, c->partials, c->dots, c->st));
+    if (flexible) CK(vec_dot(r, zp, n, c->partials, c->dots + 1, c->st));
+    CKS(fetch_dots(c, flexible ? 2 : 1));
+    const double rz_new = c->hdots[0];
+    const double beta = flexible ? (rz_new - c->hdots[1]) / rz : rz_new / rz;
+    CK(vec_xpay(p, beta, z, n, c->st));
+    rz = rz_new;
+  }
+  CKS(residual_t<double>(c, L, x, b, q));
+  double tn;
+  CKS(norm2(c, q, &tn));
+  *iters = it;
+  *relres = tn / bnorm;
+  c->n_solve++;
+  c->last_iters = it;
+  c->last_relres = *relres;
+  if (!(rn <= rtol * bnorm))
+    return fail(BH_ENOCONV, "CG stopped after " + std::to_string(it) +
+                                " iterations above the tolerance");
+  return BH_OK;
+}
+
 bh_status solve_dev(bh_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters,
                     double* relres) {
+  if (c->p.krylov == BH_CG) return solve_cg(c, b, x, rtol, maxit, iters, relres);
   CKS(ensure_gmres(c));
   const int L = c->p.level, m = c->m;
   Level& F = c->lv[L];
@@ -428,6 +522,7 @@ bh_status bh_default_params(int dim, int degree, int level, bh_params* out) {
   p.gmres_restart = 50;
   p.gmres_side = BH_LEFT;
   p.coarse = BH_COARSE_EXACT;
+  p.krylov = BH_GMRES;
   *out = p;
   return BH_OK;
 }
@@ -445,7 +540,12 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
   if (p.pre_steps < 0 || p.post_steps < 0) return fail(BH_EINVAL, "negative smoothing steps");
   if (p.gmres_side < 0 || p.gmres_side > 1) return fail(BH_EINVAL, "unknown GMRES side");
   if (p.coarse < 0 || p.coarse > 1) return fail(BH_EINVAL, "unknown coarse solver");
-  if (p.precision == BH_MIXED_FP32 && p.gmres_side == BH_LEFT)
+  if (p.krylov < 0 || p.krylov > 1) return fail(BH_EINVAL, "unknown Krylov method");
+  if (p.krylov == BH_CG && p.smoother == BH_MVS_COLORED)
+    return fail(BH_EINVAL,
+                "CG needs a symmetric preconditioner: the V-cycle with the additive smoother "
+                "(the multiplicative one goes with GMRES)");
+  if (p.krylov == BH_GMRES && p.precision == BH_MIXED_FP32 && p.gmres_side == BH_LEFT)
     return fail(BH_EINVAL,
                 "the FP32 V-cycle is not a fixed linear operator (its rounding varies): mixed "
                 "precision needs the flexible right-preconditioned GMRES, gmres_side = BH_RIGHT");

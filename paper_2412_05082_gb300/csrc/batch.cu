@@ -795,7 +795,7 @@ bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_b
     const bh_params& p = params[i];
     if (p.dim != 2) return berr(BH_EINVAL, "bh_batch_create: the batched form supports 2D problems");
     if (p.smoother != BH_MVS_COLORED || p.local_solver != BH_FDM || p.precision != BH_FP64 ||
-        p.coarse != BH_COARSE_EXACT || p.gmres_side != BH_LEFT)
+        p.coarse != BH_COARSE_EXACT || p.gmres_side != BH_LEFT || p.krylov != BH_GMRES)
       return berr(BH_EINVAL, "bh_batch_create: the batched form runs colored MVS with FDM local "
                              "solvers, FP64, the exact coarse solve and left-preconditioned GMRES");
   }

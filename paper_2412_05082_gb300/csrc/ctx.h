@@ -47,6 +47,8 @@ struct bh_ctx {
   double* dots = nullptr;
   double* partials = nullptr;
   double* hdots = nullptr;  // pinned host
+  // CG workspace (allocated on first CG solve): r, z, p, q, z_prev
+  double* cgv = nullptr;
   std::vector<void*> dev_allocs;
   // stats
   long long n_apply = 0, n_smooth = 0, n_vcycle = 0, n_solve = 0;

@@ -89,6 +89,8 @@ cudaError_t vec_axpy_dev(double* y, const double* a, double sign, const double* 
                          cudaStream_t st);
 // y = a x
 cudaError_t vec_scale(double* y, double a, const double* x, int64_t n, cudaStream_t st);
+// y = x + a y (x must not alias y)
+cudaError_t vec_xpay(double* y, double a, const double* x, int64_t n, cudaStream_t st);
 // r = b - y
 cudaError_t vec_sub(double* r, const double* b, const double* y, int64_t n, cudaStream_t st);
 // conversions

@@ -70,6 +70,12 @@ __global__ void axpy_dev_kernel(double* y, const double* a, double sign,
     y[i] = fma(c, x[i], y[i]);
 }
 
+__global__ void xpay_kernel(double* y, double a, const double* __restrict__ x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, y[i], x[i]);
+}
+
 __global__ void scale_kernel(double* y, double a, const double* __restrict__ x, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -129,6 +135,11 @@ cudaError_t vec_axpy(double* y, double a, const double* x, int64_t n, cudaStream
 cudaError_t vec_axpy_dev(double* y, const double* a, double sign, const double* x, int64_t n,
                          cudaStream_t st) {
   axpy_dev_kernel<<<grid1d(n, 256), 256, 0, st>>>(y, a, sign, x, n);
+  return launched();
+}
+
+cudaError_t vec_xpay(double* y, double a, const double* x, int64_t n, cudaStream_t st) {
+  xpay_kernel<<<grid1d(n, 256), 256, 0, st>>>(y, a, x, n);
   return launched();
 }
 

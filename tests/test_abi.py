@@ -51,9 +51,23 @@ def test_default_params_and_validation(lib):
     assert (p.dim, p.degree, p.level, p.smoother, p.local_solver) == (2, 3, 4, lib.MVS_COLORED, lib.FDM)
     assert p.pre_steps == 1 and p.post_steps == 1 and p.gmres_restart == 50
     assert p.gmres_side == lib.LEFT
+    assert p.krylov == lib.GMRES
     for bad in [(1, 3, 4), (2, 1, 4), (2, 8, 4), (3, 2, 0)]:
         with pytest.raises(lib.BiharmError):
             lib.default_params(*bad)
+
+
+@pytest.mark.parametrize("overrides,msg", [
+    ({"krylov": 2}, "Krylov"),
+    ({"krylov": 1}, "symmetric"),                       # CG with the multiplicative smoother
+    ({"precision": 1, "gmres_side": 1}, "flexible"),   # FP32 V-cycle with left GMRES
+])
+def test_create_rejects_inconsistent_options_before_touching_a_device(lib, overrides, msg):
+    # option checks run before device discovery, so they hold on a CPU-only host
+    import types
+    with pytest.raises(lib.BiharmError) as e:
+        lib.Context(lib.default_params(2, 2, 3, **overrides), types.SimpleNamespace(cuda_stream=0))
+    assert e.value.status == lib.BH_EINVAL and msg in str(e.value)
 
 
 @pytest.mark.parametrize("k", range(2, 8))

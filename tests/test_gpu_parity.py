@@ -198,6 +198,46 @@ def test_mixed_precision_solve(bh, d, k, L):
     assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
 
 
+@pytest.mark.parametrize("d,k,L,sm,ls", [(2, 2, 4, "atomic", "inexact"), (2, 3, 4, "colored", "exact"),
+                                         (2, 5, 3, "atomic", "inexact"), (2, 7, 3, "colored", "inexact"),
+                                         (3, 2, 3, "atomic", "inexact"), (3, 3, 2, "colored", "inexact")])
+def test_cg_solve_matches_oracle(bh, d, k, L, sm, ls):
+    """CG preconditioned by the V-cycle with two additive smoothing steps
+    (Sec. 5.1): same iterations (+-1), same stopping residual, same solution."""
+    H = mg.Hierarchy(d, k, L, smoother="avs", local_solver=ls, pre=2, post=2)
+    b = assemble.load_vector(d, k, 2 ** L, assemble.manufactured_f)
+    xr, it_ref, hist, rr_ref = krylov.cg(H.A[L], b, H.preconditioner, 1e-8)
+    with make_ctx(bh, d, k, L, smoother=bh.AVS_ATOMIC if sm == "atomic" else bh.AVS_COLORED,
+                  local_solver=bh.EXACT if ls == "exact" else bh.FDM, pre_steps=2, post_steps=2,
+                  krylov=bh.CG) as ctx:
+        X = torch.empty(len(b), dtype=torch.float64, device="cuda")
+        it, rr = ctx.solve(cuda(b), X, 1e-8, 300)
+    assert abs(it - it_ref) <= 1, (it, it_ref)
+    assert rr <= 1.5e-8 and rr_ref <= 1.5e-8
+    assert relerr(host(X), xr) <= 1e-6
+
+
+@pytest.mark.parametrize("d,k,L", [(2, 3, 4), (3, 2, 3)])
+def test_mixed_precision_cg(bh, d, k, L):
+    """FP32 V-cycle inside flexible (Polak-Ribiere) FP64 CG: the same 1e-8
+    reduction, at most one more iteration than FP64 CG, both within 1e-6 of
+    the dense solve."""
+    n = (k * 2 ** L - 1) ** d
+    b = workload.rhs_uniform(n, 31)
+    exact = np.linalg.solve(oracle_A(d, k, 2 ** L).toarray(), b)
+    res = {}
+    for prec in (bh.FP64, bh.MIXED_FP32):
+        with make_ctx(bh, d, k, L, smoother=bh.AVS_ATOMIC, pre_steps=2, post_steps=2,
+                      krylov=bh.CG, precision=prec) as ctx:
+            X = torch.empty(n, dtype=torch.float64, device="cuda")
+            res[prec] = ctx.solve(cuda(b), X, 1e-8, 300) + (host(X),)
+    it64, rr64, x64 = res[bh.FP64]
+    it32, rr32, x32 = res[bh.MIXED_FP32]
+    assert rr32 <= 1.5e-8 and rr64 <= 1.5e-8
+    assert it32 <= it64 + 1, (it32, it64)
+    assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
+
+
 def test_mixed_precision_requires_flexible_gmres(bh):
     with pytest.raises(bh.BiharmError) as e:
         make_ctx(bh, 2, 2, 3, precision=bh.MIXED_FP32, gmres_side=bh.LEFT)
