@@ -18,6 +18,7 @@
 
 #include <cstdint>
 
+#include "fdm_line.cuh"
 #include "ops.h"
 
 namespace bh {
@@ -329,46 +330,27 @@ __global__ void __launch_bounds__(256) patch_fdm_kernel(const __grid_constant__ 
   __syncthreads();
   T* in = bufA;
   T* out = bufB;
-  // forward transform: apply S^T along every axis
+  // S^T along every axis (the last one divides by the eigenvalue sums), then S
+  // along every axis; one half-line per item, folded for interior axes
+  constexpr int NL = MD / M;  // lines per axis and patch
 #pragma unroll
-  for (int ax = 0; ax < D; ++ax) {
+  for (int pass = 0; pass < 2 * D; ++pass) {
+    const int ax = pass < D ? pass : pass - D;
     const int st = ipow(M, ax);
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int p = e / MD, l = e % MD;
-      const int i = (l / st) % M;
-      const int l0 = l - i * st;
-      const T* src = in + p * MD + l0;
+    for (int e = threadIdx.x; e < 2 * np * NL; e += blockDim.x) {
+      const int half = e / (np * NL), p = (e / NL) % np, q = e % NL;
+      const int l0 = (q / st) * st * M + q % st;  // first element of line q
       const int t = sType[p][ax];
-      T s = T(0);
-#pragma unroll
-      for (int j = 0; j < M; ++j) s = fma(sS[t][j][i], src[j * st], s);
-      out[e] = s;
-    }
-    __syncthreads();
-    T* tmp = in;
-    in = out;
-    out = tmp;
-  }
-  // divide by the eigenvalue sums
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int p = e / MD, l = e % MD;
-    in[e] *= a.dinv[(int64_t)sCombo[p] * MD + l];
-  }
-  __syncthreads();
-  // backward transform: apply S along every axis
-#pragma unroll
-  for (int ax = 0; ax < D; ++ax) {
-    const int st = ipow(M, ax);
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int p = e / MD, l = e % MD;
-      const int i = (l / st) % M;
-      const int l0 = l - i * st;
+      const T* S = &sS[t][0][0];
       const T* src = in + p * MD + l0;
-      const int t = sType[p][ax];
-      T s = T(0);
-#pragma unroll
-      for (int j = 0; j < M; ++j) s = fma(sS[t][i][j], src[j * st], s);
-      out[e] = s;
+      T* dst = out + p * MD + l0;
+      if (pass == D - 1)
+        fdm_line<T, K, true, kFdmScaled>(half, S, t == 0, src, st, dst, st,
+                                         a.dinv + (int64_t)sCombo[p] * MD + l0, st, T(0));
+      else if (pass < D)
+        fdm_line<T, K, true, kFdmStore>(half, S, t == 0, src, st, dst, st, nullptr, 0, T(0));
+      else
+        fdm_line<T, K, false, kFdmStore>(half, S, t == 0, src, st, dst, st, nullptr, 0, T(0));
     }
     __syncthreads();
     T* tmp = in;

@@ -16,7 +16,9 @@
 // Work per patch (m = 2k-1, band nonzeros of the 1D M, L, B rows):
 //   x-split: T_M on the 4k+1 window rows, T_L and T_B on the 2k+1 middle rows
 //   y-combine: m^2 residual values, (5k+6) FMAs each
-//   FDM: 4 m^3 FMAs + m^2 scalings
+//   FDM: 4 m^3 FMAs + m^2 scalings, one output per item: with at most a few
+//   dozen patches per block the folded half-line form of fdm_line.cuh leaves
+//   too few threads per stage in 2D and measured slower
 // Every stage is split into half-lines or single points so that all threads of
 // a warp run the same FP64 instruction stream.
 #pragma once

@@ -16,7 +16,8 @@
 //   y-mix    U_B = M_y T_M (all window z), U_M = M_y T_B + B_y T_M + 2 L_y T_L,
 //            U_L = 2 (L_y T_M + M_y T_L) (middle z), on the patch (y, x);
 //   z        r = b - ascale (M_z U_M + B_z U_B + L_z U_L) on the patch nodes;
-//   FDM      S^T along x, y, z, scaling by 1 / (l_x + l_y + l_z), S along z, y, x.
+//   FDM      S^T along x, y, z, scaling by 1 / (l_x + l_y + l_z), S along z, y, x
+//            (folded form of fdm_line.cuh along the axes where the patch is interior).
 //
 // x is read from global memory (L1/L2) by the x-split; two shared-memory
 // regions hold the intermediates and ping-pong through the FDM.
@@ -258,35 +259,73 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
   }
   __syncthreads();
   // ---- fast diagonalization (region A <-> region B, M^3 values each) ---------
-  // stage s: out[l] = sum_c S_ax[c][a] in[... c ...] (TRANS) or S_ax[a][c]
-  for (int stage = 0; stage < 6; ++stage) {
-    const int ax = stage < 3 ? stage : 5 - stage;  // x, y, z, then z, y, x
-    const bool trans = stage < 3;
-    const int st = ax == 0 ? 1 : (ax == 1 ? M : MM);
-    const T* in = (stage % 2 == 0) ? regA : regB;
-    T* outp = (stage % 2 == 0) ? regB : regA;
-    const int istride = (stage % 2 == 0) ? C::RA : C::RB;
-    const int ostride = (stage % 2 == 0) ? C::RB : C::RA;
-    for (int e = threadIdx.x; e < np * M3; e += blockDim.x) {
-      const int p = e / M3, l = e % M3;
-      const int c_ax = (l / st) % M, l0 = l - c_ax * st;
-      const T* S = sS + sTy[p][ax] * MM;
-      const T* src = in + p * istride + l0;
-      T s = T(0);
+  // stage s along axis x, y, z (S^T; the third scaled by 1 / (l_x + l_y + l_z)),
+  // then z, y, x (S; the last adds pscale * result to x); k >= 3: one half-line
+  // per item, folded along the axes where the patch is interior
+  if constexpr (K == 2) {
+    // m = 3: folding saves little, one output per item keeps more threads busy
+    for (int stage = 0; stage < 6; ++stage) {
+      const int ax = stage < 3 ? stage : 5 - stage;  // x, y, z, then z, y, x
+      const bool trans = stage < 3;
+      const int st = ax == 0 ? 1 : (ax == 1 ? M : MM);
+      const T* in = (stage % 2 == 0) ? regA : regB;
+      T* outp = (stage % 2 == 0) ? regB : regA;
+      const int istride = (stage % 2 == 0) ? C::RA : C::RB;
+      const int ostride = (stage % 2 == 0) ? C::RB : C::RA;
+      for (int e = threadIdx.x; e < np * M3; e += blockDim.x) {
+        const int p = e / M3, l = e % M3;
+        const int c_ax = (l / st) % M, l0 = l - c_ax * st;
+        const T* S = sS + sTy[p][ax] * MM;
+        const T* src = in + p * istride + l0;
+        T s = T(0);
 #pragma unroll
-      for (int c = 0; c < M; ++c)
-        s = fma(trans ? S[c * M + c_ax] : S[c_ax * M + c], src[c * st], s);
-      if (stage == 2) s *= a.dinv[(int64_t)sCombo[p] * M3 + l];
-      if (stage < 5) {
-        outp[p * ostride + l] = s;
-      } else {
-        const int j = l % M, i = (l / M) % M, kz = l / MM;
-        const int gx = K * (sV[p][0] - 1) + j + 1, gy = K * (sV[p][1] - 1) + i + 1,
-                  gz = K * (sV[p][2] - 1) + kz + 1;
-        a.x[(int64_t)(gz - 1) * n2 + (int64_t)(gy - 1) * n + (gx - 1)] += (T)a.pscale * s;
+        for (int c = 0; c < M; ++c)
+          s = fma(trans ? S[c * M + c_ax] : S[c_ax * M + c], src[c * st], s);
+        if (stage == 2) s *= a.dinv[(int64_t)sCombo[p] * M3 + l];
+        if (stage < 5) {
+          outp[p * ostride + l] = s;
+        } else {
+          const int j = l % M, i = (l / M) % M, kz = l / MM;
+          const int gx = K * (sV[p][0] - 1) + j + 1, gy = K * (sV[p][1] - 1) + i + 1,
+                    gz = K * (sV[p][2] - 1) + kz + 1;
+          a.x[(int64_t)(gz - 1) * n2 + (int64_t)(gy - 1) * n + (gx - 1)] += (T)a.pscale * s;
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
+  } else {
+    const T ps = (T)a.pscale;
+    for (int stage = 0; stage < 6; ++stage) {
+      const int ax = stage < 3 ? stage : 5 - stage;  // x, y, z, then z, y, x
+      const int st = ax == 0 ? 1 : (ax == 1 ? M : MM);
+      const T* in = (stage % 2 == 0) ? regA : regB;
+      T* outp = (stage % 2 == 0) ? regB : regA;
+      const int istride = (stage % 2 == 0) ? C::RA : C::RB;
+      const int ostride = (stage % 2 == 0) ? C::RB : C::RA;
+      for (int e = threadIdx.x; e < 2 * np * MM; e += blockDim.x) {
+        const int half = e / (np * MM), p = (e / MM) % np, q = e % MM;
+        // first element of line q (the two other coordinates) in [z][y][x] order
+        const int l0 = ax == 0 ? q * M : (ax == 1 ? (q / M) * MM + q % M : q);
+        const int t = sTy[p][ax];
+        const T* S = sS + t * MM;
+        const T* src = in + p * istride + l0;
+        T* dst = outp + p * ostride + l0;
+        if (stage == 2) {
+          fdm_line<T, K, true, kFdmScaled>(half, S, t == 0, src, st, dst, st,
+                                           a.dinv + (int64_t)sCombo[p] * M3 + l0, st, T(0));
+        } else if (stage < 3) {
+          fdm_line<T, K, true, kFdmStore>(half, S, t == 0, src, st, dst, st, nullptr, 0, T(0));
+        } else if (stage < 5) {
+          fdm_line<T, K, false, kFdmStore>(half, S, t == 0, src, st, dst, st, nullptr, 0, T(0));
+        } else {  // x lines: q = kz M + i
+          const int i = q % M, kz = q / M;
+          const int gy = K * (sV[p][1] - 1) + i + 1, gz = K * (sV[p][2] - 1) + kz + 1;
+          T* xrow = a.x + (int64_t)(gz - 1) * n2 + (int64_t)(gy - 1) * n + K * (sV[p][0] - 1);
+          fdm_line<T, K, false, kFdmAdd>(half, S, t == 0, src, 1, xrow, 1, nullptr, 0, ps);
+        }
+      }
+      __syncthreads();
+    }
   }
 }
 

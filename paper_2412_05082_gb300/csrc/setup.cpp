@@ -333,6 +333,58 @@ bool gen_eig(int n, const double* B, const double* M, double* S, double* lambda)
   return true;
 }
 
+// Generalized eigenpairs of a centrosymmetric pencil (J B J = B, J M J = M with
+// J the exchange matrix, m = 2k - 1): the even and odd subspaces decouple, so
+// the problem is solved in each (orthonormal bases (e_i +- e_{m-1-i}) / sqrt 2
+// and e_{k-1}).  Columns 0..k-1 of S are the even eigenvectors (s_j =
+// s_{m-1-j}), columns k..m-1 the odd ones (s_j = -s_{m-1-j}, s_{k-1} = 0),
+// both exactly, as the folded FDM transform requires.
+bool gen_eig_centro(int m, const double* B, const double* M, double* S, double* lambda) {
+  const int k = (m + 1) / 2, ko = k - 1;
+  const double r = std::sqrt(0.5);
+  // folded basis vectors: even column a (a < k), odd column a (a < k - 1)
+  auto qe = [&](int i, int a) -> double {
+    if (a == k - 1) return i == k - 1 ? 1.0 : 0.0;
+    return (i == a || i == m - 1 - a) ? r : 0.0;
+  };
+  auto qo = [&](int i, int a) -> double { return i == a ? r : (i == m - 1 - a ? -r : 0.0); };
+  auto project = [&](const double* A, int c, bool even, std::vector<double>& out) {
+    out.assign((size_t)c * c, 0.0);
+    for (int a = 0; a < c; ++a)
+      for (int b = 0; b < c; ++b) {
+        double t = 0.0;
+        for (int i = 0; i < m; ++i)
+          for (int j = 0; j < m; ++j)
+            t += (even ? qe(i, a) : qo(i, a)) * A[(size_t)i * m + j] * (even ? qe(j, b) : qo(j, b));
+        out[(size_t)a * c + b] = t;
+      }
+  };
+  std::vector<double> Me, Be, Mo, Bo, Se((size_t)k * k), So((size_t)ko * ko), le(k), lo(ko);
+  project(M, k, true, Me);
+  project(B, k, true, Be);
+  if (!gen_eig(k, Be.data(), Me.data(), Se.data(), le.data())) return false;
+  if (ko > 0) {
+    project(M, ko, false, Mo);
+    project(B, ko, false, Bo);
+    if (!gen_eig(ko, Bo.data(), Mo.data(), So.data(), lo.data())) return false;
+  }
+  for (int i = 0; i < m; ++i) {
+    for (int c = 0; c < k; ++c) {
+      double t = 0.0;
+      for (int a = 0; a < k; ++a) t += qe(i, a) * Se[(size_t)a * k + c];
+      S[(size_t)i * m + c] = t;
+    }
+    for (int c = 0; c < ko; ++c) {
+      double t = 0.0;
+      for (int a = 0; a < ko; ++a) t += qo(i, a) * So[(size_t)a * ko + c];
+      S[(size_t)i * m + k + c] = t;
+    }
+  }
+  for (int c = 0; c < k; ++c) lambda[c] = le[c];
+  for (int c = 0; c < ko; ++c) lambda[k + c] = lo[c];
+  return true;
+}
+
 void build_setup(int k, double gamma, Setup1D& s) {
   if (k < 2 || k > kMaxK) throw std::runtime_error("degree out of range");
   s.k = k;
@@ -391,7 +443,12 @@ void build_setup(int k, double gamma, Setup1D& s) {
       }
     s.fdmS[t].assign(m * m, 0.0);
     s.fdmLam[t].assign(m, 0.0);
-    if (!gen_eig(m, s.patchB[t].data(), s.patchM[t].data(), s.fdmS[t].data(), s.fdmLam[t].data()))
+    // the interior patch pencil is centrosymmetric: even / odd eigenvectors
+    const bool ok = t == 0 ? gen_eig_centro(m, s.patchB[t].data(), s.patchM[t].data(),
+                                            s.fdmS[t].data(), s.fdmLam[t].data())
+                           : gen_eig(m, s.patchB[t].data(), s.patchM[t].data(), s.fdmS[t].data(),
+                                     s.fdmLam[t].data());
+    if (!ok)
       throw std::runtime_error("generalized eigenproblem failed (B_v not definite: gamma too small?)");
   }
   // prolongation: fine nodes of the two fine cells inside a coarse cell

@@ -53,6 +53,9 @@ double lagrange(const std::vector<double>& z, int i, double x, int deriv);
 // Generalized symmetric-definite eigenproblem B s = lambda M s (n x n,
 // row-major): S with S^T M S = I, S^T B S = diag(lambda), lambda ascending.
 bool gen_eig(int n, const double* B, const double* M, double* S, double* lambda);
+// the same for a centrosymmetric pencil, eigenvectors ordered even (columns
+// 0..k-1) then odd (k..m-1), m = 2k - 1
+bool gen_eig_centro(int m, const double* B, const double* M, double* S, double* lambda);
 
 // In-place inverse of a symmetric positive definite n x n matrix (row-major).
 bool spd_inverse(int n, double* A);
