@@ -279,6 +279,18 @@ def breakdown_3d(bh, torch, dev, stream, time_op):
     return out
 
 
+def max_over_ranks(t, dist, device):
+    """The slowest rank's time (every rank gets it); t itself without a
+    process group.  The replicas share no data, so this reduction is the only
+    collective of a multi-GPU run."""
+    if dist is None:
+        return t
+    import torch
+    v = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v)
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle timed as it stands, each step a bounded
     sample of the workload (2D, k = 2..7, N = 8: one MG-GMRES solve each)."""
@@ -403,11 +415,8 @@ def main():
     with Clocks(local_rank) as clk:
         ts = timed(step, args.steps)
     launches = bh.kernel_launches() - launches0
-    t_total = sum(ts)
+    t_total = max_over_ranks(sum(ts), dist, dev)
     if dist:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t)
         dist.barrier()
     dofs_step = sum(workload.paper_dofs(*p) for p in problems)
     value = dofs_step * args.steps * world / t_total
@@ -415,11 +424,7 @@ def main():
     # end to end through the C ABI with host buffers (copies inside the region)
     step_host()
     te = timed(step_host, args.steps)
-    t_e2e = sum(te)
-    if dist:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t)
+    t_e2e = max_over_ranks(sum(te), dist, dev)
     bytes_h2d = sum(8 * c.num_unknowns() for c in ctxs)
 
     result = {

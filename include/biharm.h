@@ -133,6 +133,12 @@ bh_status bh_restrict(bh_ctx* ctx, int level, const double* rf_dev, double* bc_d
  * BH_MIXED_FP32).  In place on x_dev. */
 bh_status bh_vcycle(bh_ctx* ctx, int level, double* x_dev, const double* b_dev);
 
+/* Tile shape of the fused colored-MVS kernels of this context: patches per
+ * thread block (0 = automatic, about two blocks per SM; larger values are
+ * clamped to the kernel's shared-memory budget).  Host only; takes effect on
+ * the next smoothing call.  BH_EINVAL for a negative value. */
+bh_status bh_set_tile(bh_ctx* ctx, int patches_per_block);
+
 /* Solve A_L x = b on the finest level with a Krylov method preconditioned by
  * one V-cycle (Sec. 5.1), x0 = 0.
  * BH_GMRES: until the Givens estimate of the minimized residual

@@ -69,6 +69,7 @@ SIGNATURES = {
     "bh_batch_create": (_I, [_c.POINTER(Params), _I, _P, _c.POINTER(_P)]),
     "bh_batch_destroy": (_I, [_P]),
     "bh_batch_set_tile": (_I, [_P, _I, _I]),
+    "bh_set_tile": (_I, [_P, _I]),
     "bh_batch_vcycle_time": (_I, [_P, _I, _c.POINTER(_D)]),
     "bh_batch_solve": (_I, [_P, _P, _P, _D, _I, _P, _P]),
     "bh_batch_stats": (_I, [_P, _c.POINTER(_c.c_longlong)]),
@@ -241,6 +242,10 @@ class Context:
     def vcycle(self, level, x, b):
         n = self.num_unknowns(level)
         _check(load().bh_vcycle(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b")))
+
+    def set_tile(self, patches_per_block):
+        """Patches per block of the fused MVS kernels (0: automatic)."""
+        _check(load().bh_set_tile(self._h, int(patches_per_block)))
 
     def solve(self, b, x, rtol=1e-8, maxit=200, raise_on_noconv=True):
         n = self.num_unknowns()

@@ -135,7 +135,7 @@ bh_status smooth_t(bh_ctx* c, int l, T* x, const T* b, int steps, bool x_zero) {
       for (int col = 0; col < nc; ++col)
         CK(Ops<T>::mvs_color(TypeOf<T>::tab(c), L.g, x, b, L.verts + L.coff[col],
                              L.coff[col + 1] - L.coff[col], L.ascale, c->p.omega * L.pscale,
-                             c->st));
+                             c->tile, c->st));
     } else if (c->p.smoother == BH_MVS_COLORED) {
       for (int col = 0; col < nc; ++col) {
         const T* r = b;
@@ -759,6 +759,13 @@ bh_status bh_vcycle(bh_ctx* ctx, int level, double* x, const double* b) {
   CKS(vcycle_t<float>(ctx, level, L.x32, L.b32, true));
   CK(vec_f2d(L.r64, L.x32, L.g.nd, ctx->st));
   CK(Ops<double>::add(x, L.r64, L.g.nd, ctx->st));
+  return BH_OK;
+}
+
+bh_status bh_set_tile(bh_ctx* ctx, int patches_per_block) {
+  if (!ctx) return fail(BH_EINVAL, "null context");
+  if (patches_per_block < 0) return fail(BH_EINVAL, "negative tile");
+  ctx->tile = patches_per_block;
   return BH_OK;
 }
 

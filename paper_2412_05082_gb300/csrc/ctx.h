@@ -49,6 +49,7 @@ struct bh_ctx {
   double* hdots = nullptr;  // pinned host
   // CG workspace (allocated on first CG solve): r, z, p, q, z_prev
   double* cgv = nullptr;
+  int tile = 0;  // patches per block of the fused MVS kernels (0: automatic)
   std::vector<void*> dev_allocs;
   // stats
   long long n_apply = 0, n_smooth = 0, n_vcycle = 0, n_solve = 0;

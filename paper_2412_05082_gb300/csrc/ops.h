@@ -51,9 +51,10 @@ struct Ops {
 
   // One color of the colored MVS, fused (2D and 3D, fast diagonalization): for every
   // patch v in verts, x_v += pscale * A~_v,ref^-1 R_v (b - ascale * A_ref x).
+  // pb: patches per block (0: automatic)
   static cudaError_t mvs_color(const void* tab, const LevelGeom& g, T* x, const T* b,
                                const int* verts, int count, double ascale, double pscale,
-                               cudaStream_t st);
+                               int pb, cudaStream_t st);
 
   // x += scale * sum_{v in verts} R_v^T Ainv[combo(v)] R_v r  (dense exact inverse;
   // Ainv holds 4^d slots of m^d x m^d matrices, slot = sum_a type_a 4^a).

@@ -258,7 +258,7 @@ cudaError_t Ops<T>::patch_fdm(const void* tab, const LevelGeom& g, const T* r, T
 template <typename T, int K>
 static cudaError_t mvs_color_k(const void* tabp, const LevelGeom& g, T* x, const T* b,
                                const int* verts, int count, double ascale, double pscale,
-                               cudaStream_t st) {
+                               int pb_req, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   const auto* h = static_cast<const HostTables<T, K>*>(tabp);
   MvsArgs<T> a{};
@@ -273,7 +273,7 @@ static cudaError_t mvs_color_k(const void* tabp, const LevelGeom& g, T* x, const
   a.dinv = h->dinv;
   using C = Mvs2Cfg<T, K>;
   // patches per block: enough blocks for two waves on 152 SMs, at most PB_MAX
-  int pb = (count + 2 * 152 - 1) / (2 * 152);
+  int pb = pb_req > 0 ? pb_req : (count + 2 * 152 - 1) / (2 * 152);
   pb = pb < 1 ? 1 : (pb > C::PB_MAX ? C::PB_MAX : pb);
   a.pb = pb;
   // opt in to the dynamic shared memory once per instantiation (thread-safe static init)
@@ -290,7 +290,7 @@ static cudaError_t mvs_color_k(const void* tabp, const LevelGeom& g, T* x, const
 template <typename T, int K>
 static cudaError_t mvs3_color_k(const void* tabp, const LevelGeom& g, T* x, const T* b,
                                 const int* verts, int count, double ascale, double pscale,
-                                cudaStream_t st) {
+                                int pb_req, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   const auto* h = static_cast<const HostTables<T, K>*>(tabp);
   MvsArgs<T> a{};
@@ -304,7 +304,7 @@ static cudaError_t mvs3_color_k(const void* tabp, const LevelGeom& g, T* x, cons
   a.pscale = pscale;
   a.dinv = h->dinv;
   using C = Mvs3Cfg<T, K>;
-  int pb = (count + 2 * 152 - 1) / (2 * 152);
+  int pb = pb_req > 0 ? pb_req : (count + 2 * 152 - 1) / (2 * 152);
   pb = pb < 1 ? 1 : (pb > C::PB_MAX ? C::PB_MAX : pb);
   a.pb = pb;
   static const cudaError_t attr = cudaFuncSetAttribute(
@@ -319,14 +319,15 @@ static cudaError_t mvs3_color_k(const void* tabp, const LevelGeom& g, T* x, cons
 
 template <typename T>
 cudaError_t Ops<T>::mvs_color(const void* tab, const LevelGeom& g, T* x, const T* b,
-                              const int* verts, int count, double ascale, double pscale,
+                              const int* verts, int count, double ascale, double pscale, int pb,
                               cudaStream_t st) {
   if (g.d == 2) {
-#define BH_CALL(KK) return mvs_color_k<T, KK>(tab, g, x, b, verts, count, ascale, pscale, st)
+#define BH_CALL(KK) return mvs_color_k<T, KK>(tab, g, x, b, verts, count, ascale, pscale, pb, st)
     BH_K_DISPATCH(g.k, BH_CALL)
 #undef BH_CALL
   } else {
-#define BH_CALL(KK) return mvs3_color_k<T, KK>(tab, g, x, b, verts, count, ascale, pscale, st)
+#define BH_CALL(KK) \
+  return mvs3_color_k<T, KK>(tab, g, x, b, verts, count, ascale, pscale, pb, st)
     BH_K_DISPATCH(g.k, BH_CALL)
 #undef BH_CALL
   }
