@@ -134,8 +134,9 @@ bh_status bh_restrict(bh_ctx* ctx, int level, const double* rf_dev, double* bc_d
 bh_status bh_vcycle(bh_ctx* ctx, int level, double* x_dev, const double* b_dev);
 
 /* Tile shape of the fused colored-MVS kernels of this context: patches per
- * thread block (0 = automatic, about two blocks per SM; larger values are
- * clamped to the kernel's shared-memory budget).  Host only; takes effect on
+ * thread block (0 = automatic: about two blocks per SM, for FP64 capped at a
+ * measured per-degree optimum; larger values are clamped to the kernel's
+ * shared-memory budget).  Host only; takes effect on
  * the next smoothing call.  BH_EINVAL for a negative value. */
 bh_status bh_set_tile(bh_ctx* ctx, int patches_per_block);
 

@@ -255,6 +255,21 @@ cudaError_t Ops<T>::patch_fdm(const void* tab, const LevelGeom& g, const T* r, T
   return cudaErrorInvalidValue;
 }
 
+// Patches per block of the FP64 fused MVS kernels at which one smoothing step
+// at the paper's sizes (2D: 512^2 cells for k <= 4, 256^2 above; 3D: 128^3 for
+// k = 2) ran fastest on GB300; the automatic choice is
+// min(ceil(count / (2 * 152)), this, the shared-memory limit), so levels with
+// few patches still spread over the SMs.  FP32 keeps the first two terms.
+constexpr int kMvs2TileF64[8] = {0, 0, 24, 12, 12, 8, 8, 4};
+constexpr int kMvs3TileF64[8] = {0, 0, 12, 16, 16, 16, 16, 16};
+
+template <typename T>
+inline int auto_tile(int count, int pref) {
+  int pb = (count + 2 * 152 - 1) / (2 * 152);
+  if (sizeof(T) == 8 && pb > pref) pb = pref;
+  return pb;
+}
+
 template <typename T, int K>
 static cudaError_t mvs_color_k(const void* tabp, const LevelGeom& g, T* x, const T* b,
                                const int* verts, int count, double ascale, double pscale,
@@ -273,7 +288,7 @@ static cudaError_t mvs_color_k(const void* tabp, const LevelGeom& g, T* x, const
   a.dinv = h->dinv;
   using C = Mvs2Cfg<T, K>;
   // patches per block: enough blocks for two waves on 152 SMs, at most PB_MAX
-  int pb = pb_req > 0 ? pb_req : (count + 2 * 152 - 1) / (2 * 152);
+  int pb = pb_req > 0 ? pb_req : auto_tile<T>(count, kMvs2TileF64[K]);
   pb = pb < 1 ? 1 : (pb > C::PB_MAX ? C::PB_MAX : pb);
   a.pb = pb;
   // opt in to the dynamic shared memory once per instantiation (thread-safe static init)
@@ -304,7 +319,7 @@ static cudaError_t mvs3_color_k(const void* tabp, const LevelGeom& g, T* x, cons
   a.pscale = pscale;
   a.dinv = h->dinv;
   using C = Mvs3Cfg<T, K>;
-  int pb = pb_req > 0 ? pb_req : (count + 2 * 152 - 1) / (2 * 152);
+  int pb = pb_req > 0 ? pb_req : auto_tile<T>(count, kMvs3TileF64[K]);
   pb = pb < 1 ? 1 : (pb > C::PB_MAX ? C::PB_MAX : pb);
   a.pb = pb;
   static const cudaError_t attr = cudaFuncSetAttribute(
