@@ -220,7 +220,7 @@ def measure_serving(bh, nreq):
     out = {"workload": "first %d requests of the Poisson stream (200 req/s, seed 2024), 2D and "
                        "3D, k = 2..7, 1e4-2e7 DoFs, uniform[-1,1] RHS, to 1e-8 (true residual)"
                        % nreq, "dofs": dofs}
-    for slots, mixed in ((8, 4), (1, 0)):
+    for slots, mixed in ((8, 7), (1, 0)):
         xs = [np.zeros_like(b) for b in rhs]
         with bh.Server(slots=slots, mixed_max_degree=mixed) as srv:
             start = time.perf_counter()
@@ -234,7 +234,7 @@ def measure_serving(bh, nreq):
             st = srv.stats()
         lat = np.array([r["latency_s"] for r in res])
         key = "served" if slots > 1 else "plain_fp64_one_slot"
-        out[key] = {"slots": slots, "precision": "FP32 V-cycle for k<=4, FP64 above" if mixed
+        out[key] = {"slots": slots, "precision": "FP32 V-cycle with FP64 defects" if mixed
                     else "FP64", "value": dofs / wall, "unit": UNIT, "wall_s": wall,
                     "p50_latency_s": float(np.percentile(lat, 50)),
                     "p99_latency_s": float(np.percentile(lat, 99)),
@@ -247,8 +247,9 @@ def measure_serving(bh, nreq):
 def breakdown_3d(bh, torch, dev, stream, time_op):
     """The 3D sweep (Q2, Q3 on 128^3, Q4-Q7 on 64^3 cells): apply, one colored
     MVS step (inexact; exact local solvers for k <= 4, whose dense inverses at
-    higher k take minutes to set up), the FP64 MG-GMRES solve and, for k <= 4,
-    the FP32 V-cycle inside flexible GMRES."""
+    higher k take minutes to set up), the FP64 MG-GMRES solve, the FP32
+    V-cycle inside flexible GMRES for k <= 4 and the FP32 V-cycle with FP64
+    defects for every k."""
     out = {}
     for d, k, N in workload.SWEEP_3D:
         L = workload.level_of(N)
@@ -267,12 +268,18 @@ def breakdown_3d(bh, torch, dev, stream, time_op):
         if k <= 4:
             with bh.Context(bh.default_params(d, k, L, local_solver=bh.EXACT), stream) as c2:
                 row["mvs_exact_step"] = dofs / time_op(lambda: c2.smooth(L, x, b, 1), 3)
-            with bh.Context(bh.default_params(d, k, L, precision=bh.MIXED_FP32,
+        # FP32 V-cycles inside flexible GMRES on the true residual: the paper's
+        # (Sec. 5.2, Q2-Q4) and the one with FP64 defects (every degree)
+        for prec, name, kmax in ((bh.MIXED_FP32, "mixed_right", 4),
+                                 (bh.MIXED_FP32_R64, "mixed_r64_right", 7)):
+            if k > kmax:
+                continue
+            with bh.Context(bh.default_params(d, k, L, precision=prec,
                                               gmres_side=bh.RIGHT), stream) as c2:
                 itm = c2.solve(b, x, 1e-8, 100, raise_on_noconv=False)
-                row["solve_mixed_right"] = dofs / time_op(
+                row["solve_" + name] = dofs / time_op(
                     lambda: c2.solve(b, x, 1e-8, 100, raise_on_noconv=False), 1)
-                row["mixed_right_iters"] = itm[0]
+                row[name + "_iters"], row[name + "_relres"] = itm[0], itm[1]
         del b, x, y
         torch.cuda.empty_cache()
         out["k%d" % k] = row
@@ -511,14 +518,19 @@ def main():
                 itr = c2.solve(b, x, 1e-8, 200, raise_on_noconv=False)
                 row["solve_fp64_right"] = dofs / time_op(
                     lambda: c2.solve(b, x, 1e-8, 200, raise_on_noconv=False), 3)
-                row["fp64_right_iters"] = itr[0]
-            if k <= 4:
-                with bh.Context(bh.default_params(d, k, L, precision=bh.MIXED_FP32,
+                row["fp64_right_iters"], row["fp64_right_relres"] = itr[0], itr[1]
+            # the FP32 V-cycle (Sec. 5.2, Q2-Q4) and the FP32 V-cycle with FP64
+            # defects (every degree), both in flexible GMRES
+            for prec, name, kmax in ((bh.MIXED_FP32, "mixed_right", 4),
+                                     (bh.MIXED_FP32_R64, "mixed_r64_right", 7)):
+                if k > kmax:
+                    continue
+                with bh.Context(bh.default_params(d, k, L, precision=prec,
                                                   gmres_side=bh.RIGHT), stream) as c2:
                     itm = c2.solve(b, x, 1e-8, 200, raise_on_noconv=False)
-                    row["solve_mixed_right"] = dofs / time_op(
+                    row["solve_" + name] = dofs / time_op(
                         lambda: c2.solve(b, x, 1e-8, 200, raise_on_noconv=False), 3)
-                    row["mixed_right_iters"] = itm[0]
+                    row[name + "_iters"], row[name + "_relres"] = itm[0], itm[1]
             # the additive smoother's protocol: two pre- and post-steps, CG
             with bh.Context(bh.default_params(d, k, L, smoother=bh.AVS_ATOMIC, pre_steps=2,
                                               post_steps=2, krylov=bh.CG), stream) as c2:

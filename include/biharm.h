@@ -51,8 +51,14 @@ enum { BH_AVS_ATOMIC = 0, BH_AVS_COLORED = 1, BH_MVS_COLORED = 2 };
 /* local solver: fast diagonalization of the separable A~_v
  * (Eq. (localsolverbila), Sec. 4.1) or the exact inverse of A_v (Sec. 3). */
 enum { BH_FDM = 0, BH_EXACT = 1 };
-/* precision of the V-cycle: FP64, or FP32 inside FP64 GMRES (Sec. 5.2). */
-enum { BH_FP64 = 0, BH_MIXED_FP32 = 1 };
+/* precision of the V-cycle: FP64, or FP32 inside FP64 GMRES (Sec. 5.2).
+ * BH_MIXED_FP32_R64 keeps the FP32 smoothing, transfers and storage of
+ * BH_MIXED_FP32 but evaluates the defect b_l - A_l x before each restriction
+ * in FP64 arithmetic (from the FP32 iterate) and restricts it in FP64: the
+ * FP32 rounding error of A x is amplified by the coarse-grid correction like
+ * the condition number of A_l, which stalls the plain FP32 V-cycle on fine
+ * meshes at high degree (2D k >= 5 on 256^2 cells).  Not in the paper. */
+enum { BH_FP64 = 0, BH_MIXED_FP32 = 1, BH_MIXED_FP32_R64 = 2 };
 /* GMRES preconditioning side (Sec. 5.1 leaves it open).  BH_LEFT stops on the
  * reduction of the preconditioned residual M^-1 (b - A x), the convention whose
  * iteration counts match the paper's tables; BH_RIGHT stops on the true
@@ -80,7 +86,8 @@ typedef struct {
   int post_steps;
   double omega;      /* damping; <= 0: Sec. 5.1 defaults (AVS 1/4 in 2D, 0.1 in 3D
                         (1/8 exact); MVS 1 in 2D, 0.7 in 3D) */
-  int precision;     /* BH_FP64 | BH_MIXED_FP32 (needs gmres_side = BH_RIGHT) */
+  int precision;     /* BH_FP64 | BH_MIXED_FP32 | BH_MIXED_FP32_R64 (mixed forms need
+                        gmres_side = BH_RIGHT, or krylov = BH_CG) */
   int gmres_restart; /* restart length m (default 50) */
   int gmres_side;    /* BH_LEFT (default) | BH_RIGHT */
   int coarse;        /* BH_COARSE_EXACT (default) | BH_COARSE_SMOOTH */
@@ -130,7 +137,8 @@ bh_status bh_restrict(bh_ctx* ctx, int level, const double* rf_dev, double* bc_d
 
 /* x <- MG_l(x, b): one V-cycle of Algorithm 1 from level l down to the coarse
  * level 1, in the context's precision (FP32 inside, FP64 in and out, for
- * BH_MIXED_FP32).  In place on x_dev. */
+ * the mixed forms: x += MG_l(0, b - A x) with the FP32 V-cycle).  In place on
+ * x_dev. */
 bh_status bh_vcycle(bh_ctx* ctx, int level, double* x_dev, const double* b_dev);
 
 /* Tile shape of the fused colored-MVS kernels of this context: patches per
@@ -147,8 +155,8 @@ bh_status bh_set_tile(bh_ctx* ctx, int patches_per_block);
  * to its initial value, or maxit iterations.  Right preconditioning keeps the
  * preconditioned directions (flexible form), as the FP32 V-cycle requires.
  * BH_CG: preconditioned conjugate gradients until the recursively updated
- * residual ||r_j|| <= rtol ||b||, or maxit iterations; with BH_MIXED_FP32 the
- * Polak-Ribiere coefficient (flexible CG) is used.  BH_ENOCONV also if p.Ap
+ * residual ||r_j|| <= rtol ||b||, or maxit iterations; with a mixed precision
+ * the Polak-Ribiere coefficient (flexible CG) is used.  BH_ENOCONV also if p.Ap
  * <= 0 (the preconditioner is not positive definite).
  * On return (synchronous) *iters holds the iteration count and *relres the
  * true ||b - A x|| / ||b|| in FP64.  BH_ENOCONV if rtol was not reached (x
@@ -241,16 +249,17 @@ bh_status bh_batch_stats(const bh_batch* batch, long long* launches);
  * hierarchy is admitted when the footprint estimate of a new one fits the
  * memory budget, after evicting idle hierarchies least recently used first;
  * otherwise it waits for running solves to release memory.  A request starts
- * as soon as a slot and its memory are free.  Precision: the FP32 V-cycle in
- * flexible FP64 GMRES for degrees <= mixed_max_degree, FP64 otherwise; right
- * preconditioning (true residual).  A request's result does not depend on the
+ * as soon as a slot and its memory are free.  Precision: the FP32 V-cycle
+ * with FP64 defects (BH_MIXED_FP32_R64) in flexible FP64 GMRES for degrees
+ * <= mixed_max_degree, FP64 otherwise; right preconditioning (true residual).  A request's result does not depend on the
  * other requests in flight. */
 typedef struct bh_server bh_server;
 
 typedef struct {
   int slots;                /* concurrent solves (worker threads), 1..64 */
   double mem_budget_bytes;  /* device memory the resident hierarchies may use */
-  int mixed_max_degree;     /* FP32 V-cycle for k <= this, FP64 above (default 4) */
+  int mixed_max_degree;     /* FP32 V-cycle (FP64 defects) for k <= this, FP64 above
+                               (default 7: every degree) */
   double rtol;              /* GMRES relative tolerance (default 1e-8) */
   int maxit;                /* GMRES iteration limit (default 200) */
   int gmres_restart;        /* restart length (default 30) */

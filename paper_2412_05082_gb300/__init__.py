@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libbiharm.so")
 BH_OK, BH_EINVAL, BH_ENOMEM, BH_ECUDA, BH_ENOCONV, BH_ETIMEOUT, BH_EBUSY = 0, -1, -2, -3, -4, -5, -6
 AVS_ATOMIC, AVS_COLORED, MVS_COLORED = 0, 1, 2
 FDM, EXACT = 0, 1
-FP64, MIXED_FP32 = 0, 1
+FP64, MIXED_FP32, MIXED_FP32_R64 = 0, 1, 2
 RIGHT, LEFT = 0, 1
 COARSE_EXACT, COARSE_SMOOTH = 0, 1
 GMRES, CG = 0, 1

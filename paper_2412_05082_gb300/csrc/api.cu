@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "biharm.h"
@@ -78,7 +79,9 @@ int color_of(const int* v, int d) {
   return 2 * par + (rb & 1);
 }
 
-bool mixed(const bh_ctx* c) { return c->p.precision == BH_MIXED_FP32; }
+bool mixed(const bh_ctx* c) { return c->p.precision != BH_FP64; }
+// FP32 V-cycle whose defects before each restriction are evaluated in FP64
+bool defect64(const bh_ctx* c) { return c->p.precision == BH_MIXED_FP32_R64; }
 
 // typed accessors for the V-cycle template
 template <typename T> struct TypeOf;
@@ -162,6 +165,26 @@ bh_status smooth_t(bh_ctx* c, int l, T* x, const T* b, int steps, bool x_zero) {
   return BH_OK;
 }
 
+// BH_MIXED_FP32_R64: the defect b_l - A_l x of the FP32 V-cycle, evaluated in
+// FP64 arithmetic from the FP32 iterate (exactly representable in FP64) and the
+// FP64 right-hand side L.db64, restricted in FP64 into Lc.db64 and rounded into
+// Lc.b32.  In FP32 arithmetic the cancellation in A x leaves a rounding error
+// of about eps_32 ||A|| ||x||, whose smooth part the coarse-grid correction
+// amplifies like the condition number of A_l.
+bh_status restrict_defect64(bh_ctx* c, int l, const float* x, bool x_zero) {
+  Level& L = c->lv[l];
+  Level& Lc = c->lv[l - 1];
+  const double* r = L.db64;
+  if (!(x_zero && c->p.pre_steps == 0)) {
+    CK(vec_f2d(L.dx64, x, L.g.nd, c->st));
+    CKS(residual_t<double>(c, l, L.dx64, L.db64, L.r64));
+    r = L.r64;
+  }
+  CK(Ops<double>::restrict_(c->tab64, L.g, r, Lc.db64, c->xs64[0], c->xs64[1], c->st));
+  CK(vec_d2f(Lc.b32, Lc.db64, Lc.g.nd, c->st));
+  return BH_OK;
+}
+
 template <typename T>
 bh_status coarse_t(bh_ctx* c, T* x, const T* b, bool x_zero) {
   Level& L = c->lv[1];
@@ -186,12 +209,25 @@ bh_status vcycle_t(bh_ctx* c, int l, T* x, const T* b, bool x_zero) {
   Level& Lc = c->lv[l - 1];
   T* R = TypeOf<T>::r(L);
   CKS(smooth_t<T>(c, l, x, b, c->p.pre_steps, x_zero));
-  if (x_zero && c->p.pre_steps == 0)
-    CK(cudaMemcpyAsync(R, b, L.g.nd * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
-  else
-    CKS(residual_t<T>(c, l, x, b, R));
-  CK(Ops<T>::restrict_(TypeOf<T>::tab(c), L.g, R, TypeOf<T>::b(Lc), TypeOf<T>::xs(c, 0),
-                       TypeOf<T>::xs(c, 1), c->st));
+  if constexpr (std::is_same<T, float>::value) {
+    if (defect64(c)) {
+      CKS(restrict_defect64(c, l, x, x_zero));
+    } else {
+      if (x_zero && c->p.pre_steps == 0)
+        CK(cudaMemcpyAsync(R, b, L.g.nd * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
+      else
+        CKS(residual_t<T>(c, l, x, b, R));
+      CK(Ops<T>::restrict_(TypeOf<T>::tab(c), L.g, R, TypeOf<T>::b(Lc), TypeOf<T>::xs(c, 0),
+                           TypeOf<T>::xs(c, 1), c->st));
+    }
+  } else {
+    if (x_zero && c->p.pre_steps == 0)
+      CK(cudaMemcpyAsync(R, b, L.g.nd * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
+    else
+      CKS(residual_t<T>(c, l, x, b, R));
+    CK(Ops<T>::restrict_(TypeOf<T>::tab(c), L.g, R, TypeOf<T>::b(Lc), TypeOf<T>::xs(c, 0),
+                         TypeOf<T>::xs(c, 1), c->st));
+  }
   CK(cudaMemsetAsync(TypeOf<T>::x(Lc), 0, Lc.g.nd * sizeof(T), c->st));
   CKS(vcycle_t<T>(c, l - 1, TypeOf<T>::x(Lc), TypeOf<T>::b(Lc), true));
   CK(Ops<T>::prolongate_add(TypeOf<T>::tab(c), L.g, TypeOf<T>::x(Lc), x, TypeOf<T>::xs(c, 0),
@@ -209,6 +245,8 @@ bh_status precondition(bh_ctx* c, const double* v, double* z) {
     return vcycle_t<double>(c, L, z, v, true);
   }
   CK(vec_d2f(F.b32, v, F.g.nd, c->st));
+  if (defect64(c))
+    CK(cudaMemcpyAsync(F.db64, v, F.g.nd * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   CK(cudaMemsetAsync(F.x32, 0, F.g.nd * sizeof(float), c->st));
   CKS(vcycle_t<float>(c, L, F.x32, F.b32, true));
   CK(vec_f2d(z, F.x32, F.g.nd, c->st));
@@ -536,7 +574,7 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
   if (p.level < 1 || p.level > 14) return fail(BH_EINVAL, "level must be in 1..14");
   if (p.smoother < 0 || p.smoother > 2) return fail(BH_EINVAL, "unknown smoother");
   if (p.local_solver < 0 || p.local_solver > 1) return fail(BH_EINVAL, "unknown local solver");
-  if (p.precision < 0 || p.precision > 1) return fail(BH_EINVAL, "unknown precision");
+  if (p.precision < 0 || p.precision > 2) return fail(BH_EINVAL, "unknown precision");
   if (p.pre_steps < 0 || p.post_steps < 0) return fail(BH_EINVAL, "negative smoothing steps");
   if (p.gmres_side < 0 || p.gmres_side > 1) return fail(BH_EINVAL, "unknown GMRES side");
   if (p.coarse < 0 || p.coarse > 1) return fail(BH_EINVAL, "unknown coarse solver");
@@ -545,7 +583,7 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
     return fail(BH_EINVAL,
                 "CG needs a symmetric preconditioner: the V-cycle with the additive smoother "
                 "(the multiplicative one goes with GMRES)");
-  if (p.krylov == BH_GMRES && p.precision == BH_MIXED_FP32 && p.gmres_side == BH_LEFT)
+  if (p.krylov == BH_GMRES && p.precision != BH_FP64 && p.gmres_side == BH_LEFT)
     return fail(BH_EINVAL,
                 "the FP32 V-cycle is not a fixed linear operator (its rounding varies): mixed "
                 "precision needs the flexible right-preconditioned GMRES, gmres_side = BH_RIGHT");
@@ -581,7 +619,7 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
     delete c;
     return fail(BH_EINVAL, std::string("setup failed: ") + e.what());
   }
-  const bool mx = p.precision == BH_MIXED_FP32;
+  const bool mx = p.precision != BH_FP64;
   c->tab64 = Ops<double>::make_tables(c->s, d);
   if (!c->tab64) return bail(fail(BH_ENOMEM, "device tables"));
   if (mx) {
@@ -604,6 +642,9 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
       return bail(status);
     if (mx && ((status = dmalloc(c, &L.x32, nd)) || (status = dmalloc(c, &L.b32, nd)) ||
                (status = dmalloc(c, &L.r32, nd))))
+      return bail(status);
+    if (p.precision == BH_MIXED_FP32_R64 &&
+        ((status = dmalloc(c, &L.db64, nd)) || (status = dmalloc(c, &L.dx64, nd))))
       return bail(status);
     // vertex patches sorted by color (Sec. 3), lexicographic inside a color
     const int Nm = L.g.N - 1;
@@ -755,6 +796,9 @@ bh_status bh_vcycle(bh_ctx* ctx, int level, double* x, const double* b) {
   Level& L = ctx->lv[level];
   CKS(residual_t<double>(ctx, level, x, b, L.r64));
   CK(vec_d2f(L.b32, L.r64, L.g.nd, ctx->st));
+  if (defect64(ctx))
+    CK(cudaMemcpyAsync(L.db64, L.r64, L.g.nd * sizeof(double), cudaMemcpyDeviceToDevice,
+                       ctx->st));
   CK(cudaMemsetAsync(L.x32, 0, L.g.nd * sizeof(float), ctx->st));
   CKS(vcycle_t<float>(ctx, level, L.x32, L.b32, true));
   CK(vec_f2d(L.r64, L.x32, L.g.nd, ctx->st));

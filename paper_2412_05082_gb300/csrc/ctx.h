@@ -17,6 +17,9 @@ struct Level {
   double pscale = 0;  // A_v^-1 = pscale * A_ref^-1 (h^(4-d))
   double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
   float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+  // BH_MIXED_FP32_R64: FP64 right-hand side of the FP32 V-cycle and FP64 copy
+  // of its iterate (kept apart from x64 / b64, which bh_solve_host stages in)
+  double *db64 = nullptr, *dx64 = nullptr;
   int* verts = nullptr;  // vertex ids sorted by color
   int coff[17] = {0};    // color offsets into verts
 };

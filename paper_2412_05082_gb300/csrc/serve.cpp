@@ -15,9 +15,9 @@
 //  - Continuous batching: a request starts as soon as a slot and its memory
 //    are free -- requests that arrive while others run join immediately, not
 //    at a batch boundary.
-//  - Precision: the FP32 V-cycle inside flexible FP64 GMRES for degrees up to
-//    mixed_max_degree, FP64 otherwise; GMRES is right-preconditioned (true
-//    residual) for every request.
+//  - Precision: the FP32 V-cycle with FP64 defects (BH_MIXED_FP32_R64) inside
+//    flexible FP64 GMRES for degrees up to mixed_max_degree, FP64 otherwise;
+//    GMRES is right-preconditioned (true residual) for every request.
 //  - Latency of a request = completion time - submission time.
 #include <cuda_runtime.h>
 
@@ -77,7 +77,8 @@ double footprint(int d, int k, int L, int precision, int restart) {
   // every level: x, b, r (+ FP32 copies); finest: sweep scratch and two
   // transfer vectors (+ FP32); GMRES basis V (m+1), Z (m), w, t; patch lists
   double total = 0, nL = 0;
-  const double vb = precision == BH_MIXED_FP32 ? 12.0 : 8.0;
+  // FP64 x, b, r; + FP32 x, b, r (mixed); + FP64 defect and iterate copy (R64)
+  const double vb = precision == BH_FP64 ? 8.0 : (precision == BH_MIXED_FP32 ? 12.0 : 17.33);
   for (int l = 1; l <= L; ++l) {
     const double n = std::pow((double)k * (1 << l) - 1.0, d);
     total += 3 * vb * n + 4.0 * n / std::pow(k, d);
@@ -184,7 +185,7 @@ void worker(bh_server* s) {
     if (s->queue.empty() && s->stop) return;
     Request* r = s->queue.front();
     s->queue.pop_front();
-    const int precision = (s->cfg.mixed_max_degree >= r->degree) ? BH_MIXED_FP32 : BH_FP64;
+    const int precision = (s->cfg.mixed_max_degree >= r->degree) ? BH_MIXED_FP32_R64 : BH_FP64;
     bh_status st = BH_OK;
     Pooled* p = acquire(s, lk, *r, precision, &st);
     if (!p) {
@@ -235,7 +236,7 @@ bh_status bh_server_default_config(bh_server_config* cfg) {
     cudaGetLastError();
     c.mem_budget_bytes = 0.0;
   }
-  c.mixed_max_degree = 4;
+  c.mixed_max_degree = 7;
   c.rtol = 1e-8;
   c.maxit = 200;
   c.gmres_restart = 30;

@@ -111,6 +111,7 @@ SMOOTH_CASES = [
     (3, 2, 4, "mvs", "exact"), (2, 3, 2, "mvs", "inexact"), (3, 4, 2, "avs", "inexact"),
     (3, 4, 4, "mvs", "inexact"), (3, 5, 4, "mvs", "inexact"), (3, 7, 2, "mvs", "inexact"),
     (3, 6, 2, "mvs", "inexact"), (3, 3, 8, "mvs", "inexact"),
+    (2, 3, 16, "mvs", "inexact"), (2, 5, 8, "mvs", "inexact"), (2, 7, 8, "mvs", "inexact"),
 ]
 
 
@@ -130,6 +131,27 @@ def test_one_smoothing_step(bh, d, k, N, kind, ls):
             X = cuda(x)
             ctx.smooth(L, X, cuda(b), 1)
             assert relerr(host(X) - x, ref - x) <= 1e-10, sm
+
+
+@pytest.mark.parametrize("k,tile", [(2, 5), (4, 1), (4, 7), (4, 12), (6, 3)])
+def test_mvs_step_for_every_tile_shape(bh, k, tile):
+    """One colored MVS step with a given number of patches per thread block:
+    tiles of interior patches take the folded, compile-time-coefficient path,
+    tiles touching the boundary the general one, and a ragged last tile mixes
+    both kinds of patch."""
+    d, N = 2, 16
+    L = workload.level_of(N)
+    A = oracle_A(d, k, N)
+    loc = oracle_local(d, k, N, "inexact")
+    n = A.shape[0]
+    b = workload.rhs_uniform(n, seed=8)
+    x = workload.vector_uniform(n, seed=9)
+    ref = smoothers.smooth("mvs", A, loc, b, x, 1.0, 1)
+    with make_ctx(bh, d, k, L) as ctx:
+        ctx.set_tile(tile)
+        X = cuda(x)
+        ctx.smooth(L, X, cuda(b), 1)
+        assert relerr(host(X) - x, ref - x) <= 1e-10
 
 
 def test_colored_avs_is_deterministic_and_equals_atomic(bh):
@@ -178,24 +200,49 @@ def test_solve_matches_oracle(bh, d, k, L, side):
     assert relerr(host(X), xr) <= 1e-6
 
 
-@pytest.mark.parametrize("d,k,L", [(2, 2, 5), (2, 3, 5), (2, 4, 4), (3, 2, 3), (3, 3, 3)])
-def test_mixed_precision_solve(bh, d, k, L):
+@pytest.mark.parametrize("d,k,L,mode", [(2, 2, 5, "fp32"), (2, 3, 5, "fp32"), (2, 4, 4, "fp32"),
+                                         (3, 2, 3, "fp32"), (3, 3, 3, "fp32"),
+                                         (2, 2, 5, "r64"), (2, 4, 4, "r64"), (2, 6, 3, "r64"),
+                                         (2, 7, 3, "r64"), (3, 3, 3, "r64"), (3, 5, 2, "r64")])
+def test_mixed_precision_solve(bh, d, k, L, mode):
     """FP32 V-cycle inside flexible FP64 GMRES (Sec. 5.2, shown there for
-    Q2-Q4): the same 1e-8 true residual, at most one more iteration than FP64,
-    and the same solution (both within 1e-6 of the dense solve)."""
+    Q2-Q4), and the variant with FP64 defects before each restriction: the
+    same 1e-8 true residual, at most one more iteration than FP64, and the
+    same solution (both within 1e-6 of the dense solve)."""
     n = (k * 2 ** L - 1) ** d
     b = workload.rhs_uniform(n, 21)
     exact = np.linalg.solve(oracle_A(d, k, 2 ** L).toarray(), b)
+    prec = bh.MIXED_FP32 if mode == "fp32" else bh.MIXED_FP32_R64
     res = {}
-    for prec in (bh.FP64, bh.MIXED_FP32):
-        with make_ctx(bh, d, k, L, precision=prec, gmres_side=bh.RIGHT) as ctx:
+    for pr in (bh.FP64, prec):
+        with make_ctx(bh, d, k, L, precision=pr, gmres_side=bh.RIGHT) as ctx:
             X = torch.empty(n, dtype=torch.float64, device="cuda")
-            res[prec] = ctx.solve(cuda(b), X, 1e-8, 100) + (host(X),)
+            res[pr] = ctx.solve(cuda(b), X, 1e-8, 100) + (host(X),)
     it64, rr64, x64 = res[bh.FP64]
-    it32, rr32, x32 = res[bh.MIXED_FP32]
+    it32, rr32, x32 = res[prec]
     assert rr32 <= 1.0001e-8 and rr64 <= 1.0001e-8
     assert it32 <= it64 + 1, (it32, it64)
     assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
+
+
+@pytest.mark.parametrize("k,L", [(6, 8), (7, 7)])
+def test_fp64_defects_keep_the_fp32_vcycle_converging_on_fine_meshes(bh, k, L):
+    """2D, high degree, fine mesh (2.4 M and 0.8 M unknowns): with FP64
+    defects before each restriction the FP32 V-cycle needs at most two more
+    GMRES iterations than the FP64 one and reaches the same true residual
+    floor (the plain FP32 V-cycle needs 150 and 33 iterations here)."""
+    d = 2
+    n = (k * 2 ** L - 1) ** d
+    b = cuda(workload.rhs_uniform(n, k))
+    res = {}
+    for pr in (bh.FP64, bh.MIXED_FP32_R64):
+        with make_ctx(bh, d, k, L, precision=pr, gmres_side=bh.RIGHT) as ctx:
+            X = torch.empty(n, dtype=torch.float64, device="cuda")
+            res[pr] = ctx.solve(b, X, 1e-8, 100)
+    it64, rr64 = res[bh.FP64]
+    itr, rrr = res[bh.MIXED_FP32_R64]
+    assert itr <= it64 + 2, (itr, it64)
+    assert rrr <= 2.0 * max(rr64, 1e-8), (rrr, rr64)
 
 
 @pytest.mark.parametrize("d,k,L,sm,ls", [(2, 2, 4, "atomic", "inexact"), (2, 3, 4, "colored", "exact"),
@@ -217,40 +264,45 @@ def test_cg_solve_matches_oracle(bh, d, k, L, sm, ls):
     assert relerr(host(X), xr) <= 1e-6
 
 
-@pytest.mark.parametrize("d,k,L", [(2, 3, 4), (3, 2, 3)])
-def test_mixed_precision_cg(bh, d, k, L):
+@pytest.mark.parametrize("d,k,L,mode", [(2, 3, 4, "fp32"), (3, 2, 3, "fp32"), (2, 5, 3, "r64")])
+def test_mixed_precision_cg(bh, d, k, L, mode):
     """FP32 V-cycle inside flexible (Polak-Ribiere) FP64 CG: the same 1e-8
     reduction, at most one more iteration than FP64 CG, both within 1e-6 of
     the dense solve."""
     n = (k * 2 ** L - 1) ** d
     b = workload.rhs_uniform(n, 31)
     exact = np.linalg.solve(oracle_A(d, k, 2 ** L).toarray(), b)
+    prec = bh.MIXED_FP32 if mode == "fp32" else bh.MIXED_FP32_R64
     res = {}
-    for prec in (bh.FP64, bh.MIXED_FP32):
+    for pr in (bh.FP64, prec):
         with make_ctx(bh, d, k, L, smoother=bh.AVS_ATOMIC, pre_steps=2, post_steps=2,
-                      krylov=bh.CG, precision=prec) as ctx:
+                      krylov=bh.CG, precision=pr) as ctx:
             X = torch.empty(n, dtype=torch.float64, device="cuda")
-            res[prec] = ctx.solve(cuda(b), X, 1e-8, 300) + (host(X),)
+            res[pr] = ctx.solve(cuda(b), X, 1e-8, 300) + (host(X),)
     it64, rr64, x64 = res[bh.FP64]
-    it32, rr32, x32 = res[bh.MIXED_FP32]
+    it32, rr32, x32 = res[prec]
     assert rr32 <= 1.5e-8 and rr64 <= 1.5e-8
     assert it32 <= it64 + 1, (it32, it64)
     assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
 
 
-def test_mixed_precision_requires_flexible_gmres(bh):
+@pytest.mark.parametrize("mode", ["fp32", "r64"])
+def test_mixed_precision_requires_flexible_gmres(bh, mode):
+    prec = bh.MIXED_FP32 if mode == "fp32" else bh.MIXED_FP32_R64
     with pytest.raises(bh.BiharmError) as e:
-        make_ctx(bh, 2, 2, 3, precision=bh.MIXED_FP32, gmres_side=bh.LEFT)
+        make_ctx(bh, 2, 2, 3, precision=prec, gmres_side=bh.LEFT)
     assert "flexible" in str(e.value)
 
 
-def test_mixed_vcycle_error_against_fp64_oracle(bh):
+@pytest.mark.parametrize("mode", ["fp32", "r64"])
+def test_mixed_vcycle_error_against_fp64_oracle(bh, mode):
     d, k, L = 2, 4, 4
     H = mg.Hierarchy(d, k, L)
     n = H.A[L].shape[0]
     b = workload.rhs_uniform(n, 31)
     ref = H.vcycle(L, np.zeros(n), b)
-    with make_ctx(bh, d, k, L, precision=bh.MIXED_FP32, gmres_side=bh.RIGHT) as ctx:
+    prec = bh.MIXED_FP32 if mode == "fp32" else bh.MIXED_FP32_R64
+    with make_ctx(bh, d, k, L, precision=prec, gmres_side=bh.RIGHT) as ctx:
         X = torch.zeros(n, dtype=torch.float64, device="cuda")
         ctx.vcycle(L, X, cuda(b))
         err = relerr(host(X), ref)
