@@ -75,6 +75,14 @@ def mvs2_fma_per_patch(k):
     return w * sm + wm * sm + wm * sb + m * (sb + 2 * sm) + 4 * m ** 3 + m * m
 
 
+def mvs2_fp64_ops_interior(k):
+    """FP64 operations the fused 2D MVS kernel executes on a patch away from
+    the boundary: the same band contractions, with the four FDM contractions
+    in the folded form (per line 2k^2 + k - 2 forward, 2k^2 - 1 backward)."""
+    m = 2 * k - 1
+    return mvs2_fma_per_patch(k) - 4 * m ** 3 + 2 * m * (4 * k * k + k - 3)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
 
@@ -268,8 +276,17 @@ def breakdown_3d(bh, torch, dev, stream, time_op):
         if k <= 4:
             with bh.Context(bh.default_params(d, k, L, local_solver=bh.EXACT), stream) as c2:
                 row["mvs_exact_step"] = dofs / time_op(lambda: c2.smooth(L, x, b, 1), 3)
-        # FP32 V-cycles inside flexible GMRES on the true residual: the paper's
-        # (Sec. 5.2, Q2-Q4) and the one with FP64 defects (every degree)
+        # flexible GMRES on the true residual: the FP64 V-cycle (one timed
+        # solve, the first on its context), the FP32 V-cycle of Sec. 5.2 (Q2-Q4)
+        # and the FP32 V-cycle with FP64 defects (every degree)
+        with bh.Context(bh.default_params(d, k, L, gmres_side=bh.RIGHT), stream) as c2:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            itr = c2.solve(b, x, 1e-8, 100, raise_on_noconv=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row["solve_fp64_right"] = dofs / (e0.elapsed_time(e1) / 1e3)
+            row["fp64_right_iters"], row["fp64_right_relres"] = itr[0], itr[1]
         for prec, name, kmax in ((bh.MIXED_FP32, "mixed_right", 4),
                                  (bh.MIXED_FP32_R64, "mixed_r64_right", 7)):
             if k > kmax:
@@ -483,6 +500,15 @@ def main():
         "fma_per_patch": mvs2_fma_per_patch(k), "patches_per_launch": patches / 8,
         "launch_ms": t_step / 8 * 1e3,
     }
+    # the FP64 FMA rate this GPU reaches on register-only FMA chains (library
+    # probe), and the rate of the FP64 operations the kernel executes (interior
+    # patches, 99 % of them at this size, take the folded FDM)
+    probe = bh.fp64_fma_rate(stream)
+    executed = 2 * mvs2_fp64_ops_interior(k) * patches / 8 / (t_step / 8) / 1e12
+    result["roofline"].update({
+        "fp64_fma_probe_tflops": probe, "frac_of_probe": achieved / probe,
+        "executed_ops_per_interior_patch": mvs2_fp64_ops_interior(k),
+        "executed_tflops": executed, "executed_frac_of_probe": executed / probe})
     n4 = ctx.num_unknowns()
     r4 = torch.empty(n4, dtype=torch.float64, device=dev)
     t_res = time_op(lambda: ctx.residual(L, xs[i4], rhs[i4], r4), 20)
@@ -519,6 +545,7 @@ def main():
                 row["solve_fp64_right"] = dofs / time_op(
                     lambda: c2.solve(b, x, 1e-8, 200, raise_on_noconv=False), 3)
                 row["fp64_right_iters"], row["fp64_right_relres"] = itr[0], itr[1]
+                x_right = x.clone()
             # the FP32 V-cycle (Sec. 5.2, Q2-Q4) and the FP32 V-cycle with FP64
             # defects (every degree), both in flexible GMRES
             for prec, name, kmax in ((bh.MIXED_FP32, "mixed_right", 4),
@@ -528,6 +555,9 @@ def main():
                 with bh.Context(bh.default_params(d, k, L, precision=prec,
                                                   gmres_side=bh.RIGHT), stream) as c2:
                     itm = c2.solve(b, x, 1e-8, 200, raise_on_noconv=False)
+                    # relative difference of the solution from the FP64 V-cycle's
+                    row[name + "_vs_fp64"] = float((x - x_right).abs().max() /
+                                                   x_right.abs().max())
                     row["solve_" + name] = dofs / time_op(
                         lambda: c2.solve(b, x, 1e-8, 200, raise_on_noconv=False), 3)
                     row[name + "_iters"], row[name + "_relres"] = itm[0], itm[1]

@@ -127,6 +127,14 @@ bh_status bh_residual(bh_ctx* ctx, int level, const double* x_dev, const double*
  * colored MVS, Sec. 3) with its local solver and damping, in place on x_dev. */
 bh_status bh_smooth(bh_ctx* ctx, int level, double* x_dev, const double* b_dev, int steps);
 
+/* Colors first_color .. end_color-1 of one step of the colored multiplicative
+ * smoother (Sec. 3, 8 colors in 2D, 16 in 3D, processed in increasing order):
+ * for each color, x_v += omega A_v^-1 R_v (b - A_l x) on all its patches at
+ * once.  bh_smooth with one step equals the range 0 .. ncolors.  In place on
+ * x_dev.  BH_EINVAL for another smoother or a range outside 0..ncolors. */
+bh_status bh_smooth_colors(bh_ctx* ctx, int level, double* x_dev, const double* b_dev,
+                           int first_color, int end_color);
+
 /* xf += I_{l-1}^up xc: the embedding V_{l-1} -> V_l (Sec. 3).  level is the
  * fine level (>= 2); xc_dev has n(level-1) values, xf_dev n(level). */
 bh_status bh_prolongate_add(bh_ctx* ctx, int level, const double* xc_dev, double* xf_dev);
@@ -184,6 +192,14 @@ const char* bh_last_error(void);
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts).  Host only; never fails. */
 long long bh_kernel_launches(void);
+
+/* Measured FP64 fused-multiply-add rate of the current device in TFLOP/s:
+ * 4 blocks per SM of 128 threads, each running four independent chains of
+ * dependent FMAs on registers, timed with CUDA events on `stream` (a
+ * cudaStream_t; NULL = legacy default stream).  A reference for the FP64
+ * kernels' roofline (the paper has no counterpart).  Allocates and frees a
+ * small device buffer; synchronous.  BH_ECUDA without a device. */
+bh_status bh_fp64_fma_rate(void* stream, double* tflops);
 
 /* Host-only 1D setup in FP64 on a line of `cells` cells of size 1 (the level
  * scaling is applied by the caller): which = 0, 1, 2 returns the mass M,

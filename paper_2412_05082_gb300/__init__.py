@@ -54,6 +54,7 @@ SIGNATURES = {
     "bh_apply_A": (_I, [_P, _I, _P, _P]),
     "bh_residual": (_I, [_P, _I, _P, _P, _P]),
     "bh_smooth": (_I, [_P, _I, _P, _P, _I]),
+    "bh_smooth_colors": (_I, [_P, _I, _P, _P, _I, _I]),
     "bh_prolongate_add": (_I, [_P, _I, _P, _P]),
     "bh_restrict": (_I, [_P, _I, _P, _P]),
     "bh_vcycle": (_I, [_P, _I, _P, _P]),
@@ -63,6 +64,7 @@ SIGNATURES = {
     "bh_stats": (_I, [_P, _c.c_char_p, _c.c_size_t]),
     "bh_last_error": (_c.c_char_p, []),
     "bh_kernel_launches": (_c.c_longlong, []),
+    "bh_fp64_fma_rate": (_I, [_P, _c.POINTER(_D)]),
     "bh_setup_1d": (_I, [_I, _D, _I, _I, _P]),
     "bh_setup_fdm": (_I, [_I, _D, _I, _P, _P]),
     "bh_apply_A_noalloc": (_I, [_I, _I, _I, _D, _P, _P, _P]),
@@ -133,6 +135,14 @@ def default_params(dim, degree, level, **overrides):
 
 def kernel_launches():
     return int(load().bh_kernel_launches())
+
+
+def fp64_fma_rate(stream=None):
+    """Measured FP64 FMA throughput of the current device (TFLOP/s)."""
+    out = ctypes.c_double()
+    st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    _check(load().bh_fp64_fma_rate(st, ctypes.byref(out)))
+    return out.value
 
 
 def last_error():
@@ -229,6 +239,12 @@ class Context:
     def smooth(self, level, x, b, steps=1):
         n = self.num_unknowns(level)
         _check(load().bh_smooth(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b"), steps))
+
+    def smooth_colors(self, level, x, b, first_color, end_color):
+        """Colors first_color .. end_color-1 of one colored MVS step."""
+        n = self.num_unknowns(level)
+        _check(load().bh_smooth_colors(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b"),
+                                       first_color, end_color))
 
     def prolongate_add(self, level, xc, xf):
         _check(load().bh_prolongate_add(self.handle, level,

@@ -125,6 +125,30 @@ bh_status patches_t(bh_ctx* c, int l, const T* r, T* x, int lo, int hi, bool ato
   return BH_OK;
 }
 
+// colors c0 .. c1-1 of one colored MVS step on level l; zero: x holds zeros on
+// entry (the first color skips its residual)
+template <typename T>
+bh_status mvs_colors_t(bh_ctx* c, int l, T* x, const T* b, int c0, int c1, bool zero) {
+  Level& L = c->lv[l];
+  T* R = TypeOf<T>::r(L);
+  for (int col = c0; col < c1; ++col) {
+    if (c->p.local_solver == BH_FDM) {
+      // fused kernel: local residual, fast diagonalization and update per patch
+      CK(Ops<T>::mvs_color(TypeOf<T>::tab(c), L.g, x, b, L.verts + L.coff[col],
+                           L.coff[col + 1] - L.coff[col], L.ascale, c->p.omega * L.pscale,
+                           c->tile, c->st));
+    } else {
+      const T* r = b;
+      if (!(zero && col == c0)) {
+        CKS(residual_t<T>(c, l, x, b, R));
+        r = R;
+      }
+      CKS(patches_t<T>(c, l, r, x, L.coff[col], L.coff[col + 1], false));
+    }
+  }
+  return BH_OK;
+}
+
 // steps smoothing steps on level l; x_zero: x holds zeros on entry (skips a residual)
 template <typename T>
 bh_status smooth_t(bh_ctx* c, int l, T* x, const T* b, int steps, bool x_zero) {
@@ -133,21 +157,8 @@ bh_status smooth_t(bh_ctx* c, int l, T* x, const T* b, int steps, bool x_zero) {
   const int d = c->p.dim, nc = c->ncolors();
   for (int s = 0; s < steps; ++s) {
     const bool zero = x_zero && s == 0;
-    if (c->p.smoother == BH_MVS_COLORED && c->p.local_solver == BH_FDM) {
-      // fused kernel: local residual, fast diagonalization and update per patch
-      for (int col = 0; col < nc; ++col)
-        CK(Ops<T>::mvs_color(TypeOf<T>::tab(c), L.g, x, b, L.verts + L.coff[col],
-                             L.coff[col + 1] - L.coff[col], L.ascale, c->p.omega * L.pscale,
-                             c->tile, c->st));
-    } else if (c->p.smoother == BH_MVS_COLORED) {
-      for (int col = 0; col < nc; ++col) {
-        const T* r = b;
-        if (!(zero && col == 0)) {
-          CKS(residual_t<T>(c, l, x, b, R));
-          r = R;
-        }
-        CKS(patches_t<T>(c, l, r, x, L.coff[col], L.coff[col + 1], false));
-      }
+    if (c->p.smoother == BH_MVS_COLORED) {
+      CKS(mvs_colors_t<T>(c, l, x, b, 0, nc, zero));
     } else {
       const T* r = b;
       if (!zero) {
@@ -767,6 +778,17 @@ bh_status bh_smooth(bh_ctx* ctx, int level, double* x, const double* b, int step
   CKS(smooth_t<double>(ctx, level, x, b, steps, false));
   ctx->n_smooth += steps;
   return BH_OK;
+}
+
+bh_status bh_smooth_colors(bh_ctx* ctx, int level, double* x, const double* b, int first_color,
+                           int end_color) {
+  CKS(check_level(ctx, level));
+  if (!x || !b || x == b) return fail(BH_EINVAL, "bad arguments");
+  if (ctx->p.smoother != BH_MVS_COLORED)
+    return fail(BH_EINVAL, "color ranges belong to the colored multiplicative smoother");
+  if (first_color < 0 || end_color > ctx->ncolors() || first_color > end_color)
+    return fail(BH_EINVAL, "color range outside 0.." + std::to_string(ctx->ncolors()));
+  return mvs_colors_t<double>(ctx, level, x, b, first_color, end_color, false);
 }
 
 bh_status bh_prolongate_add(bh_ctx* ctx, int level, const double* xc, double* xf) {

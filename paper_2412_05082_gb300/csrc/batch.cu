@@ -123,6 +123,13 @@ struct Tile {
   int count;
 };
 
+// Degrees whose interior tiles take the folded path inside the batched
+// kernel.  Its register count is the maximum over the degrees it dispatches:
+// with the folded path up to k = 4 it stays at 64 per thread and the 2D sweep's
+// batched solve ran 1 % faster than without it; up to k = 5 or 7 it needs
+// 80-128 registers and ran 3-17 % slower (measured on GB300).
+constexpr int kBatchInteriorMaxK = 4;
+
 __global__ void __launch_bounds__(256) mvs2_batch_kernel(Meta m, const MvsArgs<T>* args,
                                                          const int* pid, const Tile* tiles,
                                                          int ntiles) {
@@ -132,10 +139,13 @@ __global__ void __launch_bounds__(256) mvs2_batch_kernel(Meta m, const MvsArgs<T
     const Tile tl = tiles[t];
     const int p = pid[tl.s];
     if (!m.active[p]) continue;
-#define BH_CALL(KK)                                                            \
-  {                                                                            \
-    const auto* tb = static_cast<const Tables<T, KK>*>(m.tabs[p]);             \
-    mvs2_tile<T, KK>(tb->op, tb->fdm, args[tl.s], tl.first, tl.count, smem_raw); \
+#define BH_CALL(KK)                                                                     \
+  {                                                                                     \
+    const auto* tb = static_cast<const Tables<T, KK>*>(m.tabs[p]);                      \
+    if (KK <= kBatchInteriorMaxK && mvs2_tile_is_interior(args[tl.s], tl.first, tl.count)) \
+      mvs2_tile_interior<T, KK>(tb->op, tb->fdm, args[tl.s], tl.first, tl.count, smem_raw); \
+    else                                                                                \
+      mvs2_tile<T, KK>(tb->op, tb->fdm, args[tl.s], tl.first, tl.count, smem_raw);       \
   }
     BH_KSWITCH(m.k[p], BH_CALL)
 #undef BH_CALL

@@ -16,9 +16,8 @@
 // Work per patch (m = 2k-1, band nonzeros of the 1D M, L, B rows):
 //   x-split: T_M on the 4k+1 window rows, T_L and T_B on the 2k+1 middle rows
 //   y-combine: m^2 residual values, (5k+6) FMAs each
-//   FDM: 4 m^3 FMAs + m^2 scalings, one output per item: with at most a few
-//   dozen patches per block the folded half-line form of fdm_line.cuh leaves
-//   too few threads per stage in 2D and measured slower
+//   FDM: 4 m^3 FMAs + m^2 scalings (tiles touching the boundary), or the
+//   folded form, 4 m (2k^2 + k - 2) operations (interior tiles)
 // Every stage is split into half-lines or single points so that all threads of
 // a warp run the same FP64 instruction stream.
 #pragma once
@@ -278,12 +277,329 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
   }
 }
 
+// ---- interior tiles --------------------------------------------------------
+// A tile whose patches all lie away from the boundary (2 <= v_a <= N-2) meets
+// only the canonical row classes q = j mod K and the interior patch type in
+// both directions.  Its coefficients are then read from shared memory at
+// compile-time offsets (one broadcast load each), and every thread first
+// loads the window values of its half-line into registers, so that each FP64
+// FMA needs one shared-memory load instead of two.  The interior 1D
+// pencil is centrosymmetric, so the FDM lines take the folded form (even and
+// odd eigenvectors, 2K^2 + K - 2 operations per line instead of (2K-1)^2).
+
+// T_M along a window row: o[j - 1] = (M x)(j) for the half's positions j.  The
+// window values live in registers, so each output is stored as soon as it is
+// formed.
+template <typename T, int K, int HALF>
+__device__ __forceinline__ void xsplit_m_canon(const OpTab<T, K>& op, const T* xr, T* o) {
+  constexpr int J0 = Half<K, HALF>::J0, J1 = Half<K, HALF>::J1;
+  constexpr int A = HALF == 0 ? 0 : K, Z = 2 * K;  // nodes read: xr[A .. Z]
+  T w[Z - A + 1];
+#pragma unroll
+  for (int u = 0; u <= Z - A; ++u) w[u] = xr[A + u];
+#pragma unroll
+  for (int j = J0; j <= J1; ++j) {
+    const int q = j % K;
+    T s = T(0);
+#pragma unroll
+    for (int t = band_lo(0, q, K); t <= band_hi(0, q, K); ++t)
+      s = fma(op.M[q][t + 2 * K], w[j + t - A], s);
+    o[j - 1] = s;
+  }
+}
+
+// T_L and T_B along a middle window row
+template <typename T, int K, int HALF>
+__device__ __forceinline__ void xsplit_lb_canon(const OpTab<T, K>& op, const T* xr, T* ol,
+                                                T* ob) {
+  constexpr int J0 = Half<K, HALF>::J0, J1 = Half<K, HALF>::J1;
+  constexpr int A = HALF == 0 ? -K : 0, Z = 3 * K;  // nodes read: xr[A .. Z]
+  T w[Z - A + 1];
+#pragma unroll
+  for (int u = 0; u <= Z - A; ++u) w[u] = xr[A + u];
+#pragma unroll
+  for (int j = J0; j <= J1; ++j) {
+    const int q = j % K;
+    T sl = T(0), sb = T(0);
+#pragma unroll
+    for (int t = band_lo(1, q, K); t <= band_hi(1, q, K); ++t)
+      sl = fma(op.L[q][t + 2 * K], w[j + t - A], sl);
+#pragma unroll
+    for (int t = band_lo(2, q, K); t <= band_hi(2, q, K); ++t)
+      sb = fma(op.B[q][t + 2 * K], w[j + t - A], sb);
+    ol[j - 1] = sl;
+    ob[j - 1] = sb;
+  }
+}
+
+// residual on a half-column: r_i = b_i - ascale (B T_M + 2 L T_L + M T_B)_i
+// (pointers as in ycombine_half), accumulated operator by operator
+template <typename T, int K, int HALF>
+__device__ __forceinline__ void ycombine_canon(const OpTab<T, K>& op, const T* cm, const T* cl,
+                                               const T* cb, const T* bcol, int64_t n, T asc,
+                                               T* rcol) {
+  constexpr int M = 2 * K - 1;
+  constexpr int I0 = Half<K, HALF>::J0, I1 = Half<K, HALF>::J1, NI = I1 - I0 + 1;
+  T acc[NI];
+  {  // B on T_M: rows i + t in [A, 3K]
+    constexpr int A = HALF == 0 ? -K : 0, Z = 3 * K;
+    T w[Z - A + 1];
+#pragma unroll
+    for (int u = 0; u <= Z - A; ++u) w[u] = cm[(A + u) * M];
+#pragma unroll
+    for (int i = I0; i <= I1; ++i) {
+      const int q = i % K;
+      T s = T(0);
+#pragma unroll
+      for (int t = band_lo(2, q, K); t <= band_hi(2, q, K); ++t)
+        s = fma(op.B[q][t + 2 * K], w[i + t - A], s);
+      acc[i - I0] = s;
+    }
+  }
+  {  // 2 L on T_L: rows i + t in [A, 2K]
+    constexpr int A = HALF == 0 ? 0 : K, Z = 2 * K;
+    T w[Z - A + 1];
+#pragma unroll
+    for (int u = 0; u <= Z - A; ++u) w[u] = cl[(A + u) * M];
+#pragma unroll
+    for (int i = I0; i <= I1; ++i) {
+      const int q = i % K;
+      T s = T(0);
+#pragma unroll
+      for (int t = band_lo(1, q, K); t <= band_hi(1, q, K); ++t)
+        s = fma(op.L[q][t + 2 * K], w[i + t - A], s);
+      acc[i - I0] = fma(T(2), s, acc[i - I0]);
+    }
+  }
+  {  // M on T_B
+    constexpr int A = HALF == 0 ? 0 : K, Z = 2 * K;
+    T w[Z - A + 1];
+#pragma unroll
+    for (int u = 0; u <= Z - A; ++u) w[u] = cb[(A + u) * M];
+#pragma unroll
+    for (int i = I0; i <= I1; ++i) {
+      const int q = i % K;
+#pragma unroll
+      for (int t = band_lo(0, q, K); t <= band_hi(0, q, K); ++t)
+        acc[i - I0] = fma(op.M[q][t + 2 * K], w[i + t - A], acc[i - I0]);
+    }
+  }
+#pragma unroll
+  for (int i = I0; i <= I1; ++i)
+    rcol[(i - 1) * M] = bcol[(int64_t)(i - 1) * n] - asc * acc[i - I0];
+}
+
+// Folded FDM line of the interior type: forward (S^T v)_c for the half's
+// eigenvectors c (half 0: the K even ones, half 1: the K-1 odd ones);
+// put(c, value) receives each output.
+template <typename T, int K, int HALF, typename Put>
+__device__ __forceinline__ void fdm_fwd_canon(const FdmTab<T, K>& fdm, const T* src, int is,
+                                              Put put) {
+  constexpr int M = 2 * K - 1;
+  if (HALF == 0) {
+    T f[K];
+#pragma unroll
+    for (int j = 0; j < K - 1; ++j) f[j] = src[j * is] + src[(M - 1 - j) * is];
+    f[K - 1] = src[(K - 1) * is];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < K; ++j) s = fma(fdm.S[0][j][c], f[j], s);
+      put(c, s);
+    }
+  } else {
+    T f[K - 1];
+#pragma unroll
+    for (int j = 0; j < K - 1; ++j) f[j] = src[j * is] - src[(M - 1 - j) * is];
+#pragma unroll
+    for (int c = K; c < M; ++c) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < K - 1; ++j) s = fma(fdm.S[0][j][c], f[j], s);
+      put(c, s);
+    }
+  }
+}
+
+// backward (S g)_i for the half's position pairs (i, M-1-i): half 0 takes
+// i < K/2, half 1 the rest (with the middle position K-1)
+template <typename T, int K, int HALF, typename Put>
+__device__ __forceinline__ void fdm_bwd_canon(const FdmTab<T, K>& fdm, const T* src, int is,
+                                              Put put) {
+  constexpr int M = 2 * K - 1;
+  constexpr int I0 = HALF == 0 ? 0 : K / 2, I1 = HALF == 0 ? K / 2 : K;
+  T g[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) g[c] = src[c * is];
+#pragma unroll
+  for (int i = I0; i < I1; ++i) {
+    T e = T(0);
+#pragma unroll
+    for (int c = 0; c < K; ++c) e = fma(fdm.S[0][i][c], g[c], e);
+    if (i < K - 1) {
+      T o = T(0);
+#pragma unroll
+      for (int c = K; c < M; ++c) o = fma(fdm.S[0][i][c], g[c], o);
+      put(i, e + o);
+      put(M - 1 - i, e - o);
+    } else {
+      put(i, e);
+    }
+  }
+}
+
+// all patches of the tile interior: same stages as mvs2_tile
+template <typename T, int K>
+__device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
+                                                   const FdmTab<T, K>& fdm, const MvsArgs<T>& a,
+                                                   int first, int np, unsigned char* smem_raw) {
+  using C = Mvs2Cfg<T, K>;
+  constexpr int M = C::M, W = C::W, WM = C::WM, MM = M * M;
+  const int pb = a.pb;
+  T* sX = reinterpret_cast<T*>(smem_raw) + C::TABLES;  // same layout as mvs2_tile
+  T* sTM = sX + pb * W * W;
+  T* sTL = sTM + pb * W * M;
+  T* sTB = sTL + pb * WM * M;
+  T* sR = sTB + pb * WM * M;
+  T* sF = sR + pb * MM;
+  __shared__ int sVi[32][2];
+  const int N = a.N, n = a.n;
+  // operator and eigenvector tables staged in shared memory (layout of OpTab
+  // and FdmTab), read at compile-time offsets
+  {
+    T* sT = reinterpret_cast<T*>(smem_raw);
+    constexpr int NOP = 3 * C::NC * C::BW;
+    for (int e = threadIdx.x; e < NOP; e += blockDim.x) sT[e] = (&op.M[0][0])[e];
+    for (int e = threadIdx.x; e < 4 * MM; e += blockDim.x) sT[NOP + e] = (&fdm.S[0][0][0])[e];
+  }
+  const OpTab<T, K>& op_s = *reinterpret_cast<const OpTab<T, K>*>(smem_raw);
+  const FdmTab<T, K>& fdm_s =
+      *reinterpret_cast<const FdmTab<T, K>*>(smem_raw + sizeof(T) * 3 * C::NC * C::BW);
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const int vid = a.verts[first + p];
+    sVi[p][0] = vid % (N - 1) + 1;
+    sVi[p][1] = vid / (N - 1) + 1;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < np * W * W; e += blockDim.x) {
+    const int p = e / (W * W), wy = (e / W) % W, wx = e % W;
+    const int gx = K * (sVi[p][0] - 2) + wx, gy = K * (sVi[p][1] - 2) + wy;
+    sX[e] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? a.x[(int64_t)(gy - 1) * n + (gx - 1)]
+                                                       : T(0);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * np * W; e += blockDim.x) {
+    const int half = e / (np * W), p = (e / W) % np, wy = e % W;
+    const T* xr = sX + (p * W + wy) * W + K;
+    T* tm = sTM + (p * W + wy) * M;
+    if (half == 0)
+      xsplit_m_canon<T, K, 0>(op_s, xr, tm);
+    else
+      xsplit_m_canon<T, K, 1>(op_s, xr, tm);
+  }
+  for (int e = threadIdx.x; e < 2 * np * WM; e += blockDim.x) {
+    const int half = e / (np * WM), p = (e / WM) % np, r = e % WM;
+    const T* xr = sX + (p * W + K + r) * W + K;
+    T* tl = sTL + (p * WM + r) * M;
+    T* tb = sTB + (p * WM + r) * M;
+    if (half == 0)
+      xsplit_lb_canon<T, K, 0>(op_s, xr, tl, tb);
+    else
+      xsplit_lb_canon<T, K, 1>(op_s, xr, tl, tb);
+  }
+  __syncthreads();
+  const T asc = (T)a.ascale;
+  for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
+    const int half = e / (np * M), p = (e / M) % np, j = e % M;
+    const T* cm = sTM + (p * W + K) * M + j;
+    const T* cl = sTL + (p * WM) * M + j;
+    const T* cb = sTB + (p * WM) * M + j;
+    const int g0 = K * (sVi[p][1] - 1);
+    const int gx = K * (sVi[p][0] - 1) + j + 1;
+    const T* bcol = a.b + (int64_t)g0 * n + (gx - 1);
+    T* rcol = sR + p * MM + j;
+    if (half == 0)
+      ycombine_canon<T, K, 0>(op_s, cm, cl, cb, bcol, n, asc, rcol);
+    else
+      ycombine_canon<T, K, 1>(op_s, cm, cl, cb, bcol, n, asc, rcol);
+  }
+  __syncthreads();
+  // F = R S (rows)
+  for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
+    const int half = e / (np * M), p = (e / M) % np, i = e % M;
+    const T* src = sR + p * MM + i * M;
+    T* dst = sF + p * MM + i * M;
+    auto put = [&](int c, T v) { dst[c] = v; };
+    if (half == 0)
+      fdm_fwd_canon<T, K, 0>(fdm_s, src, 1, put);
+    else
+      fdm_fwd_canon<T, K, 1>(fdm_s, src, 1, put);
+  }
+  __syncthreads();
+  // G = D^-1 S^T F (columns), into sR
+  for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
+    const int half = e / (np * M), p = (e / M) % np, c0 = e % M;
+    const T* src = sF + p * MM + c0;
+    T* dst = sR + p * MM + c0;
+    const T* dv = a.dinv + c0;  // type combination 0 (interior x interior)
+    auto put = [&](int c1, T v) { dst[c1 * M] = v * dv[c1 * M]; };
+    if (half == 0)
+      fdm_fwd_canon<T, K, 0>(fdm_s, src, M, put);
+    else
+      fdm_fwd_canon<T, K, 1>(fdm_s, src, M, put);
+  }
+  __syncthreads();
+  // F = S G (columns)
+  for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
+    const int half = e / (np * M), p = (e / M) % np, c0 = e % M;
+    const T* src = sR + p * MM + c0;
+    T* dst = sF + p * MM + c0;
+    auto put = [&](int i, T v) { dst[i * M] = v; };
+    if (half == 0)
+      fdm_bwd_canon<T, K, 0>(fdm_s, src, M, put);
+    else
+      fdm_bwd_canon<T, K, 1>(fdm_s, src, M, put);
+  }
+  __syncthreads();
+  // x_v += pscale F S^T (rows)
+  const T ps = (T)a.pscale;
+  for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
+    const int half = e / (np * M), p = (e / M) % np, i = e % M;
+    const T* src = sF + p * MM + i * M;
+    const int gy = K * (sVi[p][1] - 1) + i + 1, gx0 = K * (sVi[p][0] - 1) + 1;
+    T* xrow = a.x + (int64_t)(gy - 1) * n + (gx0 - 1);
+    auto put = [&](int j, T v) { xrow[j] += ps * v; };
+    if (half == 0)
+      fdm_bwd_canon<T, K, 0>(fdm_s, src, 1, put);
+    else
+      fdm_bwd_canon<T, K, 1>(fdm_s, src, 1, put);
+  }
+}
+
+// true on every thread iff all np patches of the tile lie away from the boundary
+template <typename T>
+__device__ __forceinline__ bool mvs2_tile_is_interior(const MvsArgs<T>& a, int first, int np) {
+  int ok = 1;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const int vid = a.verts[first + p];
+    const int v0 = vid % (a.N - 1) + 1, v1 = vid / (a.N - 1) + 1;
+    ok &= (v0 >= 2 && v0 <= a.N - 2 && v1 >= 2 && v1 <= a.N - 2) ? 1 : 0;
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
 template <typename T, int K>
 __global__ void __launch_bounds__(256) mvs2_color_kernel(const __grid_constant__ MvsTab<T, K> tab,
                                                          const MvsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int first = blockIdx.x * a.pb;
-  mvs2_tile<T, K>(tab.op, tab.fdm, a, first, min(a.pb, a.count - first), smem_raw);
+  const int np = min(a.pb, a.count - first);
+  if (np <= 0) return;
+  if (mvs2_tile_is_interior(a, first, np))
+    mvs2_tile_interior<T, K>(tab.op, tab.fdm, a, first, np, smem_raw);
+  else
+    mvs2_tile<T, K>(tab.op, tab.fdm, a, first, np, smem_raw);
 }
 
 }  // namespace bh

@@ -260,7 +260,7 @@ cudaError_t Ops<T>::patch_fdm(const void* tab, const LevelGeom& g, const T* r, T
 // k = 2) ran fastest on GB300; the automatic choice is
 // min(ceil(count / (2 * 152)), this, the shared-memory limit), so levels with
 // few patches still spread over the SMs.  FP32 keeps the first two terms.
-constexpr int kMvs2TileF64[8] = {0, 0, 24, 12, 12, 8, 8, 4};
+constexpr int kMvs2TileF64[8] = {0, 0, 32, 18, 12, 8, 8, 4};
 constexpr int kMvs3TileF64[8] = {0, 0, 12, 16, 16, 16, 16, 16};
 
 template <typename T>
