@@ -182,8 +182,9 @@ bh_status bh_solve_host(bh_ctx* ctx, const double* b_host, double* x_host, doubl
  * (BH_RHS_PAPER_SINE, Sec. 5.1), on level l. */
 bh_status bh_rhs(bh_ctx* ctx, int level, int kind, double* b_dev);
 
-/* Counters and CUDA-event timings of the context as a JSON object written to
- * buf (NUL-terminated, truncated to len).  Host only. */
+/* Counters of the context and the CUDA-event device time of its last
+ * bh_solve / bh_solve_host ("last_solve_ms") as a JSON object written to buf
+ * (NUL-terminated, truncated to len).  Host only. */
 bh_status bh_stats(const bh_ctx* ctx, char* buf, size_t len);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -277,6 +277,8 @@ void destroy_ctx(bh_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   for (void* p : c->dev_allocs) cudaFree(p);
   if (c->hdots) cudaFreeHost(c->hdots);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
   if (c->tab64) Ops<double>::free_tables(c->tab64, c->p.degree);
   if (c->tab32) Ops<float>::free_tables(c->tab32, c->p.degree);
   delete c;
@@ -519,6 +521,25 @@ bh_status solve_dev(bh_ctx* c, const double* b, double* x, double rtol, int maxi
   if (!(est <= rtol * ref)) return fail(BH_ENOCONV, "GMRES stopped after " + std::to_string(it) +
                                                         " iterations above the tolerance");
   return BH_OK;
+}
+
+// solve_dev bracketed by CUDA events on the context's stream: the device time
+// of the last solve, for bh_stats
+bh_status timed_solve(bh_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters,
+                      double* relres) {
+  if (!c->ev[0]) {
+    if (cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess)
+      return fail(BH_ECUDA, "event creation failed");
+  }
+  CK(cudaEventRecord(c->ev[0], c->st));
+  const bh_status s = solve_dev(c, b, x, rtol, maxit, iters, relres);
+  if (s != BH_OK && s != BH_ENOCONV) return s;
+  CK(cudaEventRecord(c->ev[1], c->st));
+  CK(cudaEventSynchronize(c->ev[1]));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+  c->last_solve_ms = ms;
+  return s;
 }
 
 // 1D load vectors int s^(deriv)(x) phi_g(x) dx over the N cells of a level
@@ -839,7 +860,7 @@ bh_status bh_solve(bh_ctx* ctx, const double* b, double* x, double rtol, int max
                    double* relres) {
   if (!ctx || !b || !x || b == x || !iters || !relres || !(rtol > 0.0) || maxit < 1)
     return fail(BH_EINVAL, "bad arguments");
-  return solve_dev(ctx, b, x, rtol, maxit, iters, relres);
+  return timed_solve(ctx, b, x, rtol, maxit, iters, relres);
 }
 
 bh_status bh_solve_host(bh_ctx* ctx, const double* b_host, double* x_host, double rtol,
@@ -848,7 +869,7 @@ bh_status bh_solve_host(bh_ctx* ctx, const double* b_host, double* x_host, doubl
   Level& F = ctx->lv[ctx->p.level];
   const size_t bytes = F.g.nd * sizeof(double);
   CK(cudaMemcpyAsync(F.b64, b_host, bytes, cudaMemcpyHostToDevice, ctx->st));
-  bh_status s = solve_dev(ctx, F.b64, F.x64, rtol, maxit, iters, relres);
+  bh_status s = timed_solve(ctx, F.b64, F.x64, rtol, maxit, iters, relres);
   if (s != BH_OK && s != BH_ENOCONV) return s;
   CK(cudaMemcpyAsync(x_host, F.x64, bytes, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -915,11 +936,12 @@ bh_status bh_stats(const bh_ctx* ctx, char* buf, size_t len) {
                 "{\"dim\": %d, \"degree\": %d, \"level\": %d, \"gamma\": %.17g, \"omega\": %.17g, "
                 "\"smoother\": %d, \"local_solver\": %d, \"precision\": %d, \"applies\": %lld, "
                 "\"smooth_steps\": %lld, \"vcycles\": %lld, \"solves\": %lld, "
-                "\"last_iters\": %d, \"last_relres\": %.17g, \"kernel_launches\": %lld}",
+                "\"last_iters\": %d, \"last_relres\": %.17g, \"last_solve_ms\": %.6g, "
+                "\"kernel_launches\": %lld}",
                 ctx->p.dim, ctx->p.degree, ctx->p.level, ctx->p.gamma, ctx->p.omega,
                 ctx->p.smoother, ctx->p.local_solver, ctx->p.precision, ctx->n_apply,
                 ctx->n_smooth, ctx->n_vcycle, ctx->n_solve, ctx->last_iters, ctx->last_relres,
-                (long long)g_kernel_launches.load());
+                ctx->last_solve_ms, (long long)g_kernel_launches.load());
   return BH_OK;
 }
 

@@ -40,6 +40,9 @@ struct Mvs3Cfg {
   static constexpr int BUDGET = 220 * 1024;
   static constexpr int FIT = (BUDGET / (int)sizeof(T) - TABLES) / PER;
   static constexpr int PB_MAX = FIT < 1 ? 1 : (FIT > 16 ? 16 : FIT);
+  // threads per block: FP32 at high degree holds one to three patches of large
+  // intermediates per SM, so the block brings more threads to each stage
+  static constexpr int THREADS = (sizeof(T) == 4 && K >= 6) ? 512 : 256;
   static size_t smem_bytes(int pb) { return sizeof(T) * (size_t)(TABLES + pb * PER) + 64; }
 };
 
@@ -330,8 +333,8 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(256) mvs3_color_kernel(const __grid_constant__ MvsTab<T, K> tab,
-                                                         const MvsArgs<T> a) {
+__global__ void __launch_bounds__(Mvs3Cfg<T, K>::THREADS)
+    mvs3_color_kernel(const __grid_constant__ MvsTab<T, K> tab, const MvsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int first = blockIdx.x * a.pb;
   mvs3_tile<T, K>(tab.op, tab.fdm, a, first, min(a.pb, a.count - first), smem_raw);

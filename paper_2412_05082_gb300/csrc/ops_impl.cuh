@@ -255,18 +255,23 @@ cudaError_t Ops<T>::patch_fdm(const void* tab, const LevelGeom& g, const T* r, T
   return cudaErrorInvalidValue;
 }
 
-// Patches per block of the FP64 fused MVS kernels at which one smoothing step
-// at the paper's sizes (2D: 512^2 cells for k <= 4, 256^2 above; 3D: 128^3 for
-// k = 2) ran fastest on GB300; the automatic choice is
-// min(ceil(count / (2 * 152)), this, the shared-memory limit), so levels with
-// few patches still spread over the SMs.  FP32 keeps the first two terms.
+// Patches per block of the fused MVS kernels at which one smoothing step (FP64)
+// or one V-cycle (FP32) at the paper's sizes (2D: 512^2 cells for k <= 4, 256^2
+// above; 3D: 128^3 for k <= 3, 64^3 above) ran fastest on GB300; the automatic
+// choice is min(ceil(count / (2 * 152)), this, the shared-memory limit), so
+// levels with few patches still spread over the SMs (0: no cap).  In FP32 the
+// 3D kernel's shared memory, not its FMAs, sets the pace: smaller tiles leave
+// room for more blocks per SM.
 constexpr int kMvs2TileF64[8] = {0, 0, 32, 18, 12, 8, 8, 4};
 constexpr int kMvs3TileF64[8] = {0, 0, 12, 16, 16, 16, 16, 16};
+constexpr int kMvs2TileF32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+constexpr int kMvs3TileF32[8] = {0, 0, 12, 8, 4, 3, 0, 0};
 
 template <typename T>
-inline int auto_tile(int count, int pref) {
+inline int auto_tile(int count, int pref_f64, int pref_f32) {
   int pb = (count + 2 * 152 - 1) / (2 * 152);
-  if (sizeof(T) == 8 && pb > pref) pb = pref;
+  const int pref = sizeof(T) == 8 ? pref_f64 : pref_f32;
+  if (pref > 0 && pb > pref) pb = pref;
   return pb;
 }
 
@@ -288,7 +293,7 @@ static cudaError_t mvs_color_k(const void* tabp, const LevelGeom& g, T* x, const
   a.dinv = h->dinv;
   using C = Mvs2Cfg<T, K>;
   // patches per block: enough blocks for two waves on 152 SMs, at most PB_MAX
-  int pb = pb_req > 0 ? pb_req : auto_tile<T>(count, kMvs2TileF64[K]);
+  int pb = pb_req > 0 ? pb_req : auto_tile<T>(count, kMvs2TileF64[K], kMvs2TileF32[K]);
   pb = pb < 1 ? 1 : (pb > C::PB_MAX ? C::PB_MAX : pb);
   a.pb = pb;
   // opt in to the dynamic shared memory once per instantiation (thread-safe static init)
@@ -319,14 +324,14 @@ static cudaError_t mvs3_color_k(const void* tabp, const LevelGeom& g, T* x, cons
   a.pscale = pscale;
   a.dinv = h->dinv;
   using C = Mvs3Cfg<T, K>;
-  int pb = pb_req > 0 ? pb_req : auto_tile<T>(count, kMvs3TileF64[K]);
+  int pb = pb_req > 0 ? pb_req : auto_tile<T>(count, kMvs3TileF64[K], kMvs3TileF32[K]);
   pb = pb < 1 ? 1 : (pb > C::PB_MAX ? C::PB_MAX : pb);
   a.pb = pb;
   static const cudaError_t attr = cudaFuncSetAttribute(
       mvs3_color_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       (int)C::smem_bytes(C::PB_MAX));
   if (attr != cudaSuccess) return attr;
-  mvs3_color_kernel<T, K><<<(unsigned)((count + pb - 1) / pb), 256, C::smem_bytes(pb), st>>>(
+  mvs3_color_kernel<T, K><<<(unsigned)((count + pb - 1) / pb), C::THREADS, C::smem_bytes(pb), st>>>(
       h->mvs, a);
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();

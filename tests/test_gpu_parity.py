@@ -226,6 +226,28 @@ def test_mixed_precision_solve(bh, d, k, L, mode):
     assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
 
 
+@pytest.mark.parametrize("k", [6, 7])
+def test_mixed_precision_3d_high_degree(bh, k):
+    """3D, k = 6 and 7 on 4^3 cells (the FP32 3D smoothing kernel at its largest
+    patch tensors, 512 threads per block): both FP32 V-cycles reach a 1e-8
+    true residual with at most one iteration more than FP64, the residual
+    evaluated by the oracle's Kronecker form."""
+    d, L = 3, 2
+    n = (k * 2 ** L - 1) ** d
+    b = workload.rhs_uniform(n, 41)
+    Aop = kron.KronOperator(d, k, 2 ** L)
+    res = {}
+    for pr in (bh.FP64, bh.MIXED_FP32, bh.MIXED_FP32_R64):
+        with make_ctx(bh, d, k, L, precision=pr, gmres_side=bh.RIGHT) as ctx:
+            X = torch.empty(n, dtype=torch.float64, device="cuda")
+            res[pr] = ctx.solve(cuda(b), X, 1e-8, 100) + (host(X),)
+    it64 = res[bh.FP64][0]
+    for pr, (it, rr, x) in res.items():
+        true = np.linalg.norm(b - Aop @ x) / np.linalg.norm(b)
+        assert rr <= 1.0001e-8 and true <= 1.01e-8, (pr, rr, true)
+        assert it <= it64 + 1, (pr, it, it64)
+
+
 @pytest.mark.parametrize("k,L", [(6, 8), (7, 7)])
 def test_fp64_defects_keep_the_fp32_vcycle_converging_on_fine_meshes(bh, k, L):
     """2D, high degree, fine mesh (2.4 M and 0.8 M unknowns): with FP64
@@ -338,6 +360,9 @@ def test_small_config_end_to_end(bh):
         assert rr <= 1.0001e-8
         u = np.linalg.solve(A.toarray(), b)
         assert relerr(host(X), u) <= 1e-7
+        st = ctx.stats()
+        assert st["solves"] == 1 and st["last_iters"] == it and st["last_relres"] == rr
+        assert st["last_solve_ms"] > 0.0
 
 
 def test_full_size_apply_and_sampled_avs(bh):
