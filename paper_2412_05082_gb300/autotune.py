@@ -1,10 +1,20 @@
 """Autotuner for the batched form's tile shapes.
 
-For every degree k (2D) it times the batched V-cycle graph of a small batch of
-problems of that degree at a representative size for each candidate tile
-shape (patches per thread block of the fused multiplicative-smoother kernel)
-and keeps the fastest.  Results are cached as JSON keyed by dimension, degree
-and device architecture, in $BIHARM_TUNE_CACHE or ~/.cache/biharm_gb300/tiles.json.
+tiles_for: for every degree k (2D) it times the batched V-cycle graph of a
+small batch of problems of that degree at a representative size for each
+candidate tile shape (patches per thread block of the fused multiplicative-
+smoother kernel) and keeps the fastest.
+
+tune_batch: tiles for one given batch, timed on that batch's own V-cycle
+graph: the per-degree tiles of tiles_for are the start, then one pass of
+coordinate descent over the batch's degrees tries every candidate for one
+degree with the others fixed.  The degrees share one launch per color, whose
+shared memory per block is the largest any of their tiles needs, so the best
+tile of a degree depends on the mix.
+
+Results are cached as JSON keyed by dimension, degree (or the batch's
+problem list) and device architecture, in $BIHARM_TUNE_CACHE or
+~/.cache/biharm_gb300/tiles.json.
 """
 
 import json
@@ -85,3 +95,38 @@ def tiles_for(degrees, refresh=False, verbose=False):
 def apply(batch, degrees, refresh=False):
     for k, pb in tiles_for(degrees, refresh).items():
         batch.set_tile(k, pb)
+
+
+def tune_batch(batch, problems, refresh=False, reps=5, verbose=False):
+    """{k: patches per block} for `batch`, built from `problems` (a list of
+    (d, k, level)); applied to the batch before returning."""
+    import paper_2412_05082_gb300 as bh
+    degrees = sorted({k for _, k, _ in problems})
+    cache = load_cache()
+    key = "batch_%s_%s" % ("-".join("%d.%d.%d" % p for p in sorted(problems)), _arch())
+    if not refresh and key in cache:
+        tiles = {int(k): int(v) for k, v in cache[key]["tiles"].items()}
+        for k, pb in tiles.items():
+            batch.set_tile(k, pb)
+        return tiles
+    tiles = tiles_for(degrees)
+    for k, pb in tiles.items():
+        batch.set_tile(k, pb)
+    best = batch.vcycle_time(reps)
+    for k in degrees:
+        for pb in CANDIDATES:
+            if pb == tiles[k]:
+                continue
+            try:
+                batch.set_tile(k, pb)
+            except bh.BiharmError:
+                continue
+            t = batch.vcycle_time(reps)
+            if verbose:
+                print("k=%d pb=%d: %.3f ms (best %.3f)" % (k, pb, t, best))
+            if t < best:
+                best, tiles[k] = t, pb
+        batch.set_tile(k, tiles[k])
+    cache[key] = {"tiles": tiles, "vcycle_ms": best}
+    save_cache(cache)
+    return tiles

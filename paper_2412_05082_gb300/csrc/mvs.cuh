@@ -50,8 +50,10 @@ struct Mvs2Cfg {
   static constexpr int W = 4 * K + 1;   // window nodes per direction
   static constexpr int WM = 2 * K + 1;  // rows of T_L, T_B
   static constexpr int NC = 3 * K + 1, BW = 4 * K + 1;
-  // values per patch: window, T_M, T_L, T_B, two m x m buffers
-  static constexpr int PER = W * W + W * M + 2 * WM * M + 2 * M * M;
+  // values per patch: window, T_M, T_L, T_B; the two m x m buffers of the
+  // residual and the FDM reuse the window's space once the x-split has read it
+  static constexpr int PER = W * W + W * M + 2 * WM * M;
+  static_assert(2 * M * M <= W * W, "FDM buffers must fit in the window region");
   static constexpr int TABLES = 3 * NC * BW + 4 * M * M;
   static constexpr int BUDGET = 96 * 1024;  // bytes of shared memory per block
   static constexpr int FIT = (BUDGET / (int)sizeof(T) - TABLES) / PER;
@@ -156,7 +158,7 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
   T* sTM = sX + pb * W * W;    // [pb][W][M]
   T* sTL = sTM + pb * W * M;   // [pb][WM][M]
   T* sTB = sTL + pb * WM * M;  // [pb][WM][M]
-  T* sR = sTB + pb * WM * M;   // [pb][M][M]
+  T* sR = sX;                  // [pb][M][M], over the window after the x-split
   T* sF = sR + pb * MM;        // [pb][M][M]
   __shared__ int sV[32][2], sTy[32][2], sCombo[32];
 
@@ -461,7 +463,7 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   T* sTM = sX + pb * W * W;
   T* sTL = sTM + pb * W * M;
   T* sTB = sTL + pb * WM * M;
-  T* sR = sTB + pb * WM * M;
+  T* sR = sX;  // over the window after the x-split
   T* sF = sR + pb * MM;
   __shared__ int sVi[32][2];
   const int N = a.N, n = a.n;

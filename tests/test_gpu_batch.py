@@ -82,3 +82,30 @@ def test_batch_tiles_and_graph(bh):
             batch.set_tile(7, 33)
     with pytest.raises(bh.BiharmError):
         bh.Batch([bh.default_params(3, 2, 3)])      # batched form is 2D
+
+
+def test_batch_autotuner_keeps_results(bh, tmp_path, monkeypatch):
+    """tune_batch times the batch's own V-cycle for candidate tiles, caches the
+    choice, and the tuned batch reaches the same solutions as the batch with
+    default tiles (a tile shape only decides which patches share a block, and
+    whether a patch takes the interior or the general path: rounding-level
+    differences)."""
+    from paper_2412_05082_gb300 import autotune
+    monkeypatch.setenv("BIHARM_TUNE_CACHE", str(tmp_path / "tiles.json"))
+    probs = [(2, 2, 5), (2, 5, 3), (2, 7, 3)]
+    params = [bh.default_params(d, k, L) for d, k, L in probs]
+    bs = [torch.tensor(workload.rhs_uniform((k * 2 ** L - 1) ** 2, 60 + k), dtype=torch.float64,
+                       device="cuda") for _, k, L in probs]
+    xs0 = [torch.empty_like(b) for b in bs]
+    xs1 = [torch.empty_like(b) for b in bs]
+    with bh.Batch(params) as batch:
+        its0, _ = batch.solve(bs, xs0, 1e-8, 50)
+    with bh.Batch(params) as batch:
+        tiles = autotune.tune_batch(batch, probs, reps=1)
+        assert set(tiles) == {2, 5, 7} and all(pb >= 1 for pb in tiles.values())
+        its1, _ = batch.solve(bs, xs1, 1e-8, 50)
+    with bh.Batch(params) as batch:        # second call: read from the cache
+        assert autotune.tune_batch(batch, probs) == tiles
+    assert all(abs(a - b) <= 1 for a, b in zip(its1, its0))
+    for a, b in zip(xs0, xs1):
+        assert (a - b).abs().max().item() <= 1e-6 * b.abs().max().item()
