@@ -520,6 +520,7 @@ def main():
     executed = 2 * mvs2_fp64_ops_interior(k) * patches / 8 / (t_step / 8) / 1e12
     result["roofline"].update({
         "fp64_fma_probe_tflops": probe, "frac_of_probe": achieved / probe,
+        "fp64_tensor_mma_probe_tflops": bh.fp64_mma_rate(stream),
         "executed_ops_per_interior_patch": mvs2_fp64_ops_interior(k),
         "executed_tflops": executed, "executed_frac_of_probe": executed / probe})
     n4 = ctx.num_unknowns()

@@ -202,6 +202,11 @@ long long bh_kernel_launches(void);
  * small device buffer; synchronous.  BH_ECUDA without a device. */
 bh_status bh_fp64_fma_rate(void* stream, double* tflops);
 
+/* The same for the FP64 tensor-core instruction (mma.sync m8n8k4 f64, four
+ * independent accumulator tiles per warp): the rate a DMMA formulation of the
+ * FP64 contractions could reach on this device.  No paper counterpart. */
+bh_status bh_fp64_mma_rate(void* stream, double* tflops);
+
 /* Host-only 1D setup in FP64 on a line of `cells` cells of size 1 (the level
  * scaling is applied by the caller): which = 0, 1, 2 returns the mass M,
  * stiffness L and bulk-plus-face matrix B of Eq. (matrix1d) / Eq. (ev) on the
@@ -220,9 +225,9 @@ bh_status bh_setup_fdm(int degree, double gamma, int type, double* S, double* la
  * Many independent 2D problems with their own degree and level, solved
  * together.  Every level operation of their V-cycles runs as ONE launch over
  * all problems (a work list of (problem, range) entries dispatched on the
- * degree); the patch work of one color is one persistent launch over the
- * tiles of all problems; the lockstep V-cycle is captured once as a CUDA
- * graph; GMRES (left preconditioning) runs in lockstep with one host
+ * degree); the patch work of one color is one launch per degree present,
+ * forked into parallel branches so that each uses its own tile shape; the
+ * lockstep V-cycle is captured once as a CUDA graph; GMRES (left preconditioning) runs in lockstep with one host
  * synchronization per iteration for the whole batch.  Each problem follows
  * the arithmetic of its own context, so its result matches bh_solve on the
  * same parameters up to rounding order. */

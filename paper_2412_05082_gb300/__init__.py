@@ -65,6 +65,7 @@ SIGNATURES = {
     "bh_last_error": (_c.c_char_p, []),
     "bh_kernel_launches": (_c.c_longlong, []),
     "bh_fp64_fma_rate": (_I, [_P, _c.POINTER(_D)]),
+    "bh_fp64_mma_rate": (_I, [_P, _c.POINTER(_D)]),
     "bh_setup_1d": (_I, [_I, _D, _I, _I, _P]),
     "bh_setup_fdm": (_I, [_I, _D, _I, _P, _P]),
     "bh_apply_A_noalloc": (_I, [_I, _I, _I, _D, _P, _P, _P]),
@@ -142,6 +143,14 @@ def fp64_fma_rate(stream=None):
     out = ctypes.c_double()
     st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     _check(load().bh_fp64_fma_rate(st, ctypes.byref(out)))
+    return out.value
+
+
+def fp64_mma_rate(stream=None):
+    """Measured FP64 tensor-core (m8n8k4 MMA) throughput of the device (TFLOP/s)."""
+    out = ctypes.c_double()
+    st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    _check(load().bh_fp64_mma_rate(st, ctypes.byref(out)))
     return out.value
 
 

@@ -2,9 +2,10 @@
 // solved together.  Every level operation of the V-cycle processes all
 // problems in ONE launch: the launch walks a precomputed work list of
 // (problem, range) entries and dispatches on the problem's degree.  The
-// smoother's patch work is one persistent launch per color over the tiles of
-// all problems, with the tile shape (patches per block) chosen per degree by
-// the autotuner.  The V-cycle runs in lockstep by depth (depth t works on
+// smoother's patch work of one color is one launch per degree present (one
+// block per tile, each launch with the shared memory of its own tile shape),
+// the launches forked into parallel branches of the graph; the tile shape
+// (patches per block) of each degree comes from the autotuner.  The V-cycle runs in lockstep by depth (depth t works on
 // level L_p - t of every problem p) and is captured once as a CUDA graph;
 // GMRES (left preconditioning, the paper's protocol) runs in lockstep with a
 // per-problem activity mask, one host synchronization per iteration for all
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(256) mvs2_batch_kernel(Meta m, const MvsArgs<T
                                                          const int* pid, const Tile* tiles,
                                                          int ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {  // persistent over the tiles
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {  // any grid size (one block per tile)
     __syncthreads();  // the previous tile's last stage still reads shared memory
     const Tile tl = tiles[t];
     const int p = pid[tl.s];
@@ -282,7 +283,9 @@ struct VecOpList {
 
 struct Depth {  // operations at depth t of the lockstep V-cycle
   bool smooth = false, coarse = false;
-  MvsOp mvs[8];
+  // per color, one MVS launch per degree present at this depth (each with the
+  // shared memory its own tile needs); they run as parallel graph branches
+  std::vector<MvsOp> mvs[8];
   SweepOp res_x, res_y;
   XferOp restr[2], prol[2];
   VecOpList zero_coarse;  // x at level - 1
@@ -327,6 +330,11 @@ struct bh_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<double*> stage_b, stage_x;  // device staging for bh_batch_solve_host
+  // side streams and events that fork the per-degree MVS launches of one
+  // color into parallel branches of the captured V-cycle graph
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
   long long launches = 0;        // kernels run by the batch (graph replays count their nodes)
   long long graph_kernels = 0;   // kernel nodes of the captured V-cycle graph
   std::vector<int> last_iters;
@@ -507,10 +515,11 @@ bh_status build_depths(bh_batch* b) {
     std::vector<std::pair<int, Vec>> zc;
     std::vector<Symv> sv;
     std::vector<int> svp;
-    std::vector<std::vector<MvsArgs<T>>> margs(8);
-    std::vector<std::vector<int>> mpid(8);
-    std::vector<std::vector<Tile>> mtiles(8);
-    size_t smem = 0;
+    // per color and degree (index k): patch-list arguments, problems, tiles
+    std::vector<std::vector<MvsArgs<T>>> margs(8 * (kMaxK + 1));
+    std::vector<std::vector<int>> mpid(8 * (kMaxK + 1));
+    std::vector<std::vector<Tile>> mtiles(8 * (kMaxK + 1));
+    size_t smem_k[kMaxK + 1] = {0};
     for (int p = 0; p < P; ++p) {
       const int l = b->L[p] - t;
       if (l < 1) continue;
@@ -535,7 +544,7 @@ bh_status build_depths(bh_batch* b) {
       zc.push_back({p, Vec{Lc.x64, nullptr, Lc.g.nd, 0, 0}});
       const int k = b->k[p];
       const int pb = std::min(mvs_pb(b, k), mvs_pb_max(k));
-      smem = std::max(smem, mvs_smem(k, pb));
+      smem_k[k] = mvs_smem(k, pb);
       const DevTables dt = Ops<T>::device_tables(c->tab64, k);
       for (int col = 0; col < 8; ++col) {
         MvsArgs<T> a{};
@@ -549,10 +558,11 @@ bh_status build_depths(bh_batch* b) {
         a.ascale = Lv.ascale;
         a.pscale = c->p.omega * Lv.pscale;
         a.dinv = static_cast<const T*>(dt.dinv);
-        const int s = (int)margs[col].size();
-        margs[col].push_back(a);
-        mpid[col].push_back(p);
-        for (int f = 0; f < a.count; f += pb) mtiles[col].push_back(Tile{s, f, std::min(pb, a.count - f)});
+        const int g = col * (kMaxK + 1) + k;
+        const int s = (int)margs[g].size();
+        margs[g].push_back(a);
+        mpid[g].push_back(p);
+        for (int f = 0; f < a.count; f += pb) mtiles[g].push_back(Tile{s, f, std::min(pb, a.count - f)});
       }
     }
     D.smooth = !rx.empty();
@@ -566,10 +576,16 @@ bh_status build_depths(bh_batch* b) {
       BCKS(make_xfer(b, p1, D.prol[1]));
       BCKS(make_vec(b, zc, D.zero_coarse));
       for (int col = 0; col < 8; ++col) {
-        BCKS(upload(b, margs[col], D.mvs[col].args));
-        BCKS(upload(b, mpid[col], D.mvs[col].pid));
-        BCKS(upload(b, mtiles[col], D.mvs[col].tiles));
-        D.mvs[col].smem = smem;
+        for (int k = 0; k <= kMaxK; ++k) {
+          const int g = col * (kMaxK + 1) + k;
+          if (mtiles[g].empty()) continue;
+          D.mvs[col].emplace_back();
+          MvsOp& op = D.mvs[col].back();
+          BCKS(upload(b, margs[g], op.args));
+          BCKS(upload(b, mpid[g], op.pid));
+          BCKS(upload(b, mtiles[g], op.tiles));
+          op.smem = smem_k[k];
+        }
       }
     }
     if (D.coarse) {
@@ -632,22 +648,29 @@ cudaError_t run_dot(bh_batch* b, const VecOpList& op, int cslot, int yslot = 0, 
   return cudaGetLastError();
 }
 
-cudaError_t run_mvs(bh_batch* b, const MvsOp& op) {
-  if (op.tiles.n == 0) return cudaSuccess;
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mvs2_batch_kernel, 256,
-                                                                op.smem);
-  if (e != cudaSuccess) return e;
-  int sms = 152;
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess)
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(op.tiles.n, std::max(1, per_sm) * sms));
-  mvs2_batch_kernel<<<grid, 256, op.smem, b->st>>>(meta(b), op.args.d, op.pid.d, op.tiles.d,
-                                                   op.tiles.n);
-  b->launches++;
-  g_kernel_launches.fetch_add(1);
-  return cudaGetLastError();
+// one color: a launch per degree group, one block per tile, each with the
+// shared memory of its own tile shape; with several groups the launches fork
+// from b->st onto side streams and join back (parallel graph branches)
+cudaError_t run_mvs(bh_batch* b, const std::vector<MvsOp>& ops) {
+  if (ops.empty()) return cudaSuccess;
+  cudaError_t e;
+  const bool fork = ops.size() > 1;
+  if (fork && (e = cudaEventRecord(b->fork, b->st)) != cudaSuccess) return e;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const MvsOp& op = ops[i];
+    cudaStream_t st = fork ? b->side[i] : b->st;
+    if (fork && (e = cudaStreamWaitEvent(st, b->fork, 0)) != cudaSuccess) return e;
+    mvs2_batch_kernel<<<op.tiles.n, 256, op.smem, st>>>(meta(b), op.args.d, op.pid.d, op.tiles.d,
+                                                        op.tiles.n);
+    b->launches++;
+    g_kernel_launches.fetch_add(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (fork && (e = cudaEventRecord(b->join[i], st)) != cudaSuccess) return e;
+  }
+  if (fork)
+    for (size_t i = 0; i < ops.size(); ++i)
+      if ((e = cudaStreamWaitEvent(b->st, b->join[i], 0)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 // lockstep V-cycle from depth t: x_L = MG(b_L) with x_L zero on entry
@@ -732,6 +755,19 @@ bh_status prepare(bh_batch* b) {
     smem = std::max(smem, mvs_smem(b->k[p], std::min(mvs_pb(b, b->k[p]), mvs_pb_max(b->k[p]))));
   BCK(cudaFuncSetAttribute(mvs2_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem));
+  // one side stream and join event per degree present (created once)
+  int groups = 0;
+  for (int k = 0; k <= kMaxK; ++k)
+    groups += std::find(b->k.begin(), b->k.end(), k) != b->k.end() ? 1 : 0;
+  if (!b->fork) BCK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  while ((int)b->side.size() < groups) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    BCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    b->side.push_back(st);
+    BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    b->join.push_back(ev);
+  }
   BCKS(build_depths(b));
   return capture_vcycle(b);
 }
@@ -873,6 +909,9 @@ bh_status bh_batch_destroy(bh_batch* b) {
   for (void* p : b->allocs) cudaFree(p);
   for (bh_ctx* c : b->ctx) bh_destroy(c);
   if (b->ev) cudaEventDestroy(b->ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  for (cudaStream_t st : b->side) cudaStreamDestroy(st);
   if (b->st) cudaStreamDestroy(b->st);
   delete b->plan;
   delete b;

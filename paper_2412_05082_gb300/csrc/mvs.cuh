@@ -54,8 +54,9 @@ struct Mvs2Cfg {
   // residual and the FDM reuse the window's space once the x-split has read it
   static constexpr int PER = W * W + W * M + 2 * WM * M;
   static_assert(2 * M * M <= W * W, "FDM buffers must fit in the window region");
-  static constexpr int TABLES = 3 * NC * BW + 4 * M * M;
-  static constexpr int BUDGET = 96 * 1024;  // bytes of shared memory per block
+  // M, L, B class tables, the four S, and the interior type's 1 / (l_x + l_y)
+  static constexpr int TABLES = 3 * NC * BW + 5 * M * M;
+  static constexpr int BUDGET = 110 * 1024;  // bytes of shared memory per block (2 per SM)
   static constexpr int FIT = (BUDGET / (int)sizeof(T) - TABLES) / PER;
   static constexpr int PB_MAX = FIT < 1 ? 1 : (FIT > 32 ? 32 : FIT);
   static size_t smem_bytes(int pb) { return sizeof(T) * (size_t)(TABLES + pb * PER) + 64; }
@@ -154,7 +155,7 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
   T* sB = sL + NC * BW;
   T* sS = sB + NC * BW;  // [4][M][M]
   const int pb = a.pb;
-  T* sX = sS + 4 * MM;         // [pb][W][W]
+  T* sX = reinterpret_cast<T*>(smem_raw) + C::TABLES;  // [pb][W][W]
   T* sTM = sX + pb * W * W;    // [pb][W][M]
   T* sTL = sTM + pb * W * M;   // [pb][WM][M]
   T* sTB = sTL + pb * WM * M;  // [pb][WM][M]
@@ -468,12 +469,15 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   __shared__ int sVi[32][2];
   const int N = a.N, n = a.n;
   // operator and eigenvector tables staged in shared memory (layout of OpTab
-  // and FdmTab), read at compile-time offsets
+  // and FdmTab), read at compile-time offsets, and the interior type's
+  // reciprocal eigenvalue sums
+  constexpr int NOP = 3 * C::NC * C::BW;
+  T* sDinv = reinterpret_cast<T*>(smem_raw) + NOP + 4 * MM;
   {
     T* sT = reinterpret_cast<T*>(smem_raw);
-    constexpr int NOP = 3 * C::NC * C::BW;
     for (int e = threadIdx.x; e < NOP; e += blockDim.x) sT[e] = (&op.M[0][0])[e];
     for (int e = threadIdx.x; e < 4 * MM; e += blockDim.x) sT[NOP + e] = (&fdm.S[0][0][0])[e];
+    for (int e = threadIdx.x; e < MM; e += blockDim.x) sDinv[e] = a.dinv[e];  // combination 0
   }
   const OpTab<T, K>& op_s = *reinterpret_cast<const OpTab<T, K>*>(smem_raw);
   const FdmTab<T, K>& fdm_s =
@@ -544,7 +548,7 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
     const int half = e / (np * M), p = (e / M) % np, c0 = e % M;
     const T* src = sF + p * MM + c0;
     T* dst = sR + p * MM + c0;
-    const T* dv = a.dinv + c0;  // type combination 0 (interior x interior)
+    const T* dv = sDinv + c0;  // type combination 0 (interior x interior)
     auto put = [&](int c1, T v) { dst[c1 * M] = v * dv[c1 * M]; };
     if (half == 0)
       fdm_fwd_canon<T, K, 0>(fdm_s, src, M, put);

@@ -1,7 +1,8 @@
-// FP64 FMA throughput probe: the denominator against which the FP64 kernels
-// of this library can be read.  Every thread runs ILP independent chains of
-// dependent fused multiply-adds on registers (no memory traffic inside the
-// timed loop); the rate is timed with CUDA events on the caller's stream.
+// FP64 throughput probes: the denominators against which the FP64 kernels of
+// this library can be read.  Every thread runs ILP independent chains of
+// dependent fused multiply-adds (or FP64 tensor-core MMAs) on registers, no
+// memory traffic inside the timed loop; the rate is timed with CUDA events on
+// the caller's stream.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -33,14 +34,38 @@ __global__ void __launch_bounds__(128) fma_chains(double* out, double a, double 
   out[blockIdx.x * blockDim.x + threadIdx.x] = acc;  // keeps the chains alive
 }
 
+// the same with the FP64 tensor-core instruction: D = A B + C on 8x8x4 tiles
+// (mma.sync, 512 flops per warp instruction), ILP independent accumulators
+__global__ void __launch_bounds__(128) mma_chains(double* out, double a, double b, int iters) {
+  double c[kIlp][2];
+#pragma unroll
+  for (int i = 0; i < kIlp; ++i) c[i][0] = c[i][1] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r)
+#pragma unroll
+      for (int i = 0; i < kIlp; ++i)
+        asm volatile(
+            "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+            : "+d"(c[i][0]), "+d"(c[i][1])
+            : "d"(a), "d"(b));
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int i = 0; i < kIlp; ++i) acc += c[i][0] + c[i][1];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 bh_status perr(bh_status s, const std::string& m) {
   bh::set_last_error(m);
   return s;
 }
 
-}  // namespace
-
-extern "C" bh_status bh_fp64_fma_rate(void* stream, double* tflops) {
+// time `kernel` over 4 blocks of 128 threads per SM; flops_per_thread_iter:
+// flops one thread contributes per loop iteration
+template <typename Kernel>
+bh_status rate(Kernel kernel, double a, double b, double flops_per_thread_iter, void* stream,
+               double* tflops) {
   if (!tflops) return perr(BH_EINVAL, "null output");
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -61,21 +86,31 @@ extern "C" bh_status bh_fp64_fma_rate(void* stream, double* tflops) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     status = perr(BH_ECUDA, "event creation failed");
   } else {
-    fma_chains<<<blocks, threads, 0, st>>>(out, 0.999999, 1e-7, iters);  // warm-up
+    kernel<<<blocks, threads, 0, st>>>(out, a, b, iters);  // warm-up
     cudaEventRecord(e0, st);
-    fma_chains<<<blocks, threads, 0, st>>>(out, 0.999999, 1e-7, iters);
+    kernel<<<blocks, threads, 0, st>>>(out, a, b, iters);
     cudaEventRecord(e1, st);
     bh::g_kernel_launches.fetch_add(2);
     if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
         !(ms > 0.f))
       status = perr(BH_ECUDA, std::string("probe: ") + cudaGetErrorString(cudaGetLastError()));
   }
-  if (status == BH_OK) {
-    const double fmas = (double)blocks * threads * iters * kUnroll * kIlp;
-    *tflops = 2.0 * fmas / (ms * 1e-3) / 1e12;
-  }
+  if (status == BH_OK)
+    *tflops = (double)blocks * threads * iters * flops_per_thread_iter / (ms * 1e-3) / 1e12;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(out);
   return status;
+}
+
+}  // namespace
+
+extern "C" bh_status bh_fp64_fma_rate(void* stream, double* tflops) {
+  // 2 flops per FMA, kUnroll x kIlp FMAs per thread and iteration
+  return rate(fma_chains, 0.999999, 1e-7, 2.0 * kUnroll * kIlp, stream, tflops);
+}
+
+extern "C" bh_status bh_fp64_mma_rate(void* stream, double* tflops) {
+  // 512 flops per warp-wide 8x8x4 MMA = 16 per thread, kUnroll x kIlp per iteration
+  return rate(mma_chains, 0.999999, 1e-7, 16.0 * kUnroll * kIlp, stream, tflops);
 }
