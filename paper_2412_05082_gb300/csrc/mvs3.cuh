@@ -77,7 +77,10 @@ __device__ __forceinline__ void line_half(const T* tab, bool canon, int g0, int 
   }
 }
 
-template <typename T, int K>
+// INTERIOR: every patch of the tile lies away from the boundary in all three
+// directions, so the row classes and patch types are compile-time constants
+// (coefficients at fixed offsets, folded FDM on every axis)
+template <typename T, int K, bool INTERIOR = false>
 __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T, K>& fdm,
                                           const MvsArgs<T>& a, int first, int np,
                                           unsigned char* smem_raw) {
@@ -142,7 +145,7 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
       w[i] = (inside && gx >= 1 && gx <= n) ? xrow[i] : T(0);
     }
     T* tm = regA + p * C::RA + row * M;
-    const bool canon = sTy[p][0] == 0;
+    const bool canon = INTERIOR || sTy[p][0] == 0;
     if (half == 0)
       line_half<T, K, 0, 0, 0, false>(sM, canon, gx0, N, w, 1, tm, 1, one);
     else
@@ -163,7 +166,7 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
     }
     T* tl = regA + p * C::RA + C::TM + r * M;
     T* tb = tl + C::TLB;
-    const bool canon = sTy[p][0] == 0;
+    const bool canon = INTERIOR || sTy[p][0] == 0;
     if (half == 0) {
       line_half<T, K, 0, 1, K, false>(sL, canon, gx0, N, w, 1, tl, 1, one);
       line_half<T, K, 0, 2, K, false>(sB, canon, gx0, N, w, 1, tb, 1, one);
@@ -185,7 +188,7 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
 #pragma unroll
     for (int i = 0; i <= 2 * K; ++i) col[i] = A[cross_row<K>(K + i, z) * M + j];
     T* ub = regB + p * C::RB + z * MM + j;  // [z][i][j], i stride M
-    const bool canon = sTy[p][1] == 0;
+    const bool canon = INTERIOR || sTy[p][1] == 0;
     const int gy0 = K * (sV[p][1] - 1);
     if (half == 0)
       line_half<T, K, 0, 0, 0, false>(sM, canon, gy0, N, col, 1, ub, M, one);
@@ -207,7 +210,7 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
     }
     T* um = regB + p * C::RB + C::UB + zr * MM + j;
     T* ul = um + C::UML;
-    const bool canon = sTy[p][1] == 0;
+    const bool canon = INTERIOR || sTy[p][1] == 0;
     const int gy0 = K * (sV[p][1] - 1);
     const T two = T(2);
     if (half == 0) {
@@ -239,7 +242,7 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
       cul[z] = Bp[C::UB + C::UML + z * MM + r];
     }
     T* R = regA + p * C::RA + r;  // R[kz][i][j], kz stride MM
-    const bool canon = sTy[p][2] == 0;
+    const bool canon = INTERIOR || sTy[p][2] == 0;
     const int gz0 = K * (sV[p][2] - 1);
     if (half == 0) {
       line_half<T, K, 0, 0, 0, false>(sM, canon, gz0, N, cum, 1, R, MM, one);
@@ -309,7 +312,7 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
         const int half = e / (np * MM), p = (e / MM) % np, q = e % MM;
         // first element of line q (the two other coordinates) in [z][y][x] order
         const int l0 = ax == 0 ? q * M : (ax == 1 ? (q / M) * MM + q % M : q);
-        const int t = sTy[p][ax];
+        const int t = INTERIOR ? 0 : sTy[p][ax];
         const T* S = sS + t * MM;
         const T* src = in + p * istride + l0;
         T* dst = outp + p * ostride + l0;
@@ -332,12 +335,32 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
   }
 }
 
+// true on every thread iff all np patches of the tile lie away from the boundary
+template <typename T>
+__device__ __forceinline__ bool mvs3_tile_is_interior(const MvsArgs<T>& a, int first, int np) {
+  int ok = 1;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    int vid = a.verts[first + p];
+    for (int ax = 0; ax < 3; ++ax) {
+      const int v = vid % (a.N - 1) + 1;
+      vid /= (a.N - 1);
+      ok &= (v >= 2 && v <= a.N - 2) ? 1 : 0;
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
 template <typename T, int K>
 __global__ void __launch_bounds__(Mvs3Cfg<T, K>::THREADS)
     mvs3_color_kernel(const __grid_constant__ MvsTab<T, K> tab, const MvsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int first = blockIdx.x * a.pb;
-  mvs3_tile<T, K>(tab.op, tab.fdm, a, first, min(a.pb, a.count - first), smem_raw);
+  const int np = min(a.pb, a.count - first);
+  if (np <= 0) return;
+  if (mvs3_tile_is_interior(a, first, np))
+    mvs3_tile<T, K, true>(tab.op, tab.fdm, a, first, np, smem_raw);
+  else
+    mvs3_tile<T, K, false>(tab.op, tab.fdm, a, first, np, smem_raw);
 }
 
 }  // namespace bh
