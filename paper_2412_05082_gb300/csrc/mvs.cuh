@@ -141,6 +141,24 @@ __device__ __forceinline__ void ycombine_half(const T* sM, const T* sL, const T*
   }
 }
 
+// Asynchronous global -> shared copy of one value (cp.async, no register
+// staging, so all of a thread's window loads are in flight together); when
+// `valid` is false no byte is read and the value is filled with zero.  The
+// caller waits with async_copy_wait before the barrier that publishes it.
+template <typename T>
+__device__ __forceinline__ void async_copy_or_zero(T* dst, const T* src, bool valid) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte values");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned bytes = valid ? (unsigned)sizeof(T) : 0u;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src),
+               "n"(sizeof(T)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void async_copy_wait() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Patches first .. first + np - 1 of a.verts by one thread block; tables read
 // from `op` / `fdm` (kernel parameters or device memory) into shared memory.
 // smem_raw: dynamic shared memory of at least Mvs2Cfg::smem_bytes(a.pb) bytes.
@@ -187,9 +205,10 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
   for (int e = threadIdx.x; e < np * W * W; e += blockDim.x) {
     const int p = e / (W * W), wy = (e / W) % W, wx = e % W;
     const int gx = K * (sV[p][0] - 2) + wx, gy = K * (sV[p][1] - 2) + wy;
-    sX[e] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? a.x[(int64_t)(gy - 1) * n + (gx - 1)]
-                                                       : T(0);
+    const bool in = gx >= 1 && gx <= n && gy >= 1 && gy <= n;
+    async_copy_or_zero(sX + e, a.x + (in ? (int64_t)(gy - 1) * n + (gx - 1) : 0), in);
   }
+  async_copy_wait();
   __syncthreads();
   // x-split: T_M on every window row, one half-line (half, patch, row) per item
   for (int e = threadIdx.x; e < 2 * np * W; e += blockDim.x) {
@@ -491,9 +510,11 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   for (int e = threadIdx.x; e < np * W * W; e += blockDim.x) {
     const int p = e / (W * W), wy = (e / W) % W, wx = e % W;
     const int gx = K * (sVi[p][0] - 2) + wx, gy = K * (sVi[p][1] - 2) + wy;
-    sX[e] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? a.x[(int64_t)(gy - 1) * n + (gx - 1)]
-                                                       : T(0);
+    const bool in = gx >= 1 && gx <= n && gy >= 1 && gy <= n;
+    // outside the interior the (unread) source is the first value of x
+    async_copy_or_zero(sX + e, a.x + (in ? (int64_t)(gy - 1) * n + (gx - 1) : 0), in);
   }
+  async_copy_wait();
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * np * W; e += blockDim.x) {
     const int half = e / (np * W), p = (e / W) % np, wy = e % W;
