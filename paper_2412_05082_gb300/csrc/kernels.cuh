@@ -243,6 +243,24 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ OpTa
 // ---------------------------------------------------------------------------
 // vertex-patch kernels
 // ---------------------------------------------------------------------------
+// Asynchronous global -> shared copy of one value (cp.async, no register
+// staging, so all of a thread's window loads are in flight together); when
+// `valid` is false no byte is read and the value is filled with zero.  The
+// caller waits with async_copy_wait before the barrier that publishes it.
+template <typename T>
+__device__ __forceinline__ void async_copy_or_zero(T* dst, const T* src, bool valid) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte values");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned bytes = valid ? (unsigned)sizeof(T) : 0u;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src),
+               "n"(sizeof(T)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void async_copy_wait() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 template <typename T>
 struct PatchArgs {
   const T* r;
@@ -325,8 +343,9 @@ __global__ void __launch_bounds__(256) patch_fdm_kernel(const __grid_constant__ 
     int c[3] = {0, 0, 0};
     local_coords<D, M>(l, c);
     const int64_t gi = sBase[p] + c[0] + c[1] * n + (D == 3 ? c[2] * n2 : 0);
-    bufA[e] = a.r[gi];
+    async_copy_or_zero(bufA + e, a.r + gi, true);
   }
+  async_copy_wait();
   __syncthreads();
   T* in = bufA;
   T* out = bufB;
@@ -396,8 +415,9 @@ __global__ void __launch_bounds__(256) patch_exact_kernel(const PatchArgs<T> a) 
     const int p = e / MD, l = e % MD;
     int c[3] = {0, 0, 0};
     local_coords<D, M>(l, c);
-    buf[e] = a.r[sBase[p] + c[0] + c[1] * n + (D == 3 ? c[2] * n2 : 0)];
+    async_copy_or_zero(buf + e, a.r + sBase[p] + c[0] + c[1] * n + (D == 3 ? c[2] * n2 : 0), true);
   }
+  async_copy_wait();
   __syncthreads();
   const T sc = (T)a.scale;
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {

@@ -141,24 +141,6 @@ __device__ __forceinline__ void ycombine_half(const T* sM, const T* sL, const T*
   }
 }
 
-// Asynchronous global -> shared copy of one value (cp.async, no register
-// staging, so all of a thread's window loads are in flight together); when
-// `valid` is false no byte is read and the value is filled with zero.  The
-// caller waits with async_copy_wait before the barrier that publishes it.
-template <typename T>
-__device__ __forceinline__ void async_copy_or_zero(T* dst, const T* src, bool valid) {
-  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte values");
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const unsigned bytes = valid ? (unsigned)sizeof(T) : 0u;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src),
-               "n"(sizeof(T)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void async_copy_wait() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
 // Patches first .. first + np - 1 of a.verts by one thread block; tables read
 // from `op` / `fdm` (kernel parameters or device memory) into shared memory.
 // smem_raw: dynamic shared memory of at least Mvs2Cfg::smem_bytes(a.pb) bytes.
