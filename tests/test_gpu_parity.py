@@ -415,8 +415,44 @@ def along(P, X, a):
     return np.moveaxis(np.moveaxis(X, ax, -1) @ P.T, -1, ax)
 
 
+@pytest.mark.parametrize("d,k,N", [(3, 7, 64), (3, 3, 128), (2, 7, 256)])
+def test_full_size_apply_on_sampled_rows(bh, d, k, N):
+    """apply_A at the largest sweep sizes (3D Q7 on 64^3 cells: 89 M unknowns;
+    3D Q3 on 128^3; 2D Q7 on 256^2) on 256 sampled rows, each evaluated from
+    the oracle's 1D factors on the node's neighbourhood."""
+    L = workload.level_of(N)
+    n1 = k * N - 1
+    with make_ctx(bh, d, k, L) as ctx:
+        n = ctx.num_unknowns(L)
+        x = workload.vector_uniform(n, 12)
+        X = cuda(x)
+        Y = torch.empty_like(X)
+        ctx.apply_A(L, X, Y)
+        got = host(Y)
+        del X, Y
+    M1, L1, B1 = (np.asarray(m.todense()) if hasattr(m, "todense") else np.asarray(m)
+                  for m in kron.global_1d(k, N))
+    terms = ([(1.0, (B1, M1)), (1.0, (M1, B1)), (2.0, (L1, L1))] if d == 2 else
+             [(1.0, (B1, M1, M1)), (1.0, (M1, B1, M1)), (1.0, (M1, M1, B1)),
+              (2.0, (L1, L1, M1)), (2.0, (M1, L1, L1)), (2.0, (L1, M1, L1))])
+    X0 = x.reshape((n1,) * d)
+    rng = np.random.default_rng(13)
+    scale = np.abs(got).max()
+    for idx in rng.integers(0, n, 256):
+        c = np.unravel_index(int(idx), (n1,) * d)[::-1]    # (i_x, i_y[, i_z])
+        win = [np.arange(max(0, c[a] - 2 * k - 1), min(n1, c[a] + 2 * k + 2)) for a in range(d)]
+        xw = X0[np.ix_(*[win[a] for a in reversed(range(d))])]
+        y = 0.0
+        for cf, ops in terms:
+            T = xw
+            for a, P in enumerate(ops):
+                T = along(P[np.ix_([c[a]], win[a])], T, a)
+            y += cf * T.item()
+        assert abs(got[idx] - y) <= 1e-12 * scale, (idx, got[idx], y)
+
+
 @pytest.mark.parametrize("d,k,N,color", [(2, 4, 512, 0), (2, 7, 256, 5), (3, 4, 64, 0),
-                                         (3, 2, 128, 9)])
+                                         (3, 2, 128, 9), (3, 7, 64, 15)])
 def test_full_size_mvs_color_on_sampled_patches(bh, d, k, N, color):
     """One color of the colored MVS at the sweep sizes (2D Q4 on 512^2 and Q7
     on 256^2, 3D Q4 on 64^3 and Q2 on 128^3 cells), in the launch
