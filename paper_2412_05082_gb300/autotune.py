@@ -8,9 +8,9 @@ smoother kernel) and keeps the fastest.
 tune_batch: tiles for one given batch, timed on that batch's own V-cycle
 graph: the per-degree tiles of tiles_for are the start, then one pass of
 coordinate descent over the batch's degrees tries every candidate for one
-degree with the others fixed.  The degrees share one launch per color, whose
-shared memory per block is the largest any of their tiles needs, so the best
-tile of a degree depends on the mix.
+degree with the others fixed.  The degrees' patch launches of one color run
+concurrently and compete for the SMs, so the best tile of a degree can depend
+on the mix.
 
 Results are cached as JSON keyed by dimension, degree (or the batch's
 problem list) and device architecture, in $BIHARM_TUNE_CACHE or
