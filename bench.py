@@ -7,8 +7,10 @@ and one post-smoothing step, fast-diagonalization local solvers, left
 preconditioning: the protocol of Sec. 5.1), which runs apply_A, the residual,
 the patch gather / solve / scatter, the transfers, the V-cycle and GMRES.  The
 six solves run as one batch (bh_batch_solve: each level operation one launch
-over all problems, the lockstep V-cycle replayed as a CUDA graph); every
-problem takes the iterations and arithmetic of its own solve.
+over all problems, the patch work of a color one launch per degree as parallel
+graph branches, the lockstep V-cycle replayed as a CUDA graph, tiles tuned on
+the batch itself); every problem takes the iterations and arithmetic of its
+own solve.
 
 value = sum of the paper's DoF counts (kN+1)^2 solved / device time (CUDA
 events), the solve inputs resident in HBM; L2 is flushed (256 MiB write)
