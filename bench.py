@@ -265,8 +265,7 @@ def measure_serving(bh, nreq):
 
 def breakdown_3d(bh, torch, dev, stream, time_op):
     """The 3D sweep (Q2, Q3 on 128^3, Q4-Q7 on 64^3 cells): apply, one colored
-    MVS step (inexact; exact local solvers for k <= 4, whose dense inverses at
-    higher k take minutes to set up), the FP64 MG-GMRES solve, the FP32
+    MVS step (inexact, and exact local solvers), the FP64 MG-GMRES solve, the FP32
     V-cycle inside flexible GMRES for k <= 4 and the FP32 V-cycle with FP64
     defects for every k."""
     out = {}
@@ -284,9 +283,8 @@ def breakdown_3d(bh, torch, dev, stream, time_op):
             it = ctx.solve(b, x, 1e-8, 100)
             row["solve_fp64"] = dofs / time_op(lambda: ctx.solve(b, x, 1e-8, 100), 1)
             row["solve_iters"], row["true_relres"] = it[0], it[1]
-        if k <= 4:
-            with bh.Context(bh.default_params(d, k, L, local_solver=bh.EXACT), stream) as c2:
-                row["mvs_exact_step"] = dofs / time_op(lambda: c2.smooth(L, x, b, 1), 3)
+        with bh.Context(bh.default_params(d, k, L, local_solver=bh.EXACT), stream) as c2:
+            row["mvs_exact_step"] = dofs / time_op(lambda: c2.smooth(L, x, b, 1), 2)
         # flexible GMRES on the true residual: the FP64 V-cycle (one timed
         # solve, the first on its context), the FP32 V-cycle of Sec. 5.2 (Q2-Q4)
         # and the FP32 V-cycle with FP64 defects (every degree)

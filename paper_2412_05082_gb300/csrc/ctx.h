@@ -1,8 +1,10 @@
 // Context internals shared by api.cu (single problem) and batch.cu (batched
 // form): one multigrid hierarchy with its device buffers and tables.
 #pragma once
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
+#include <array>
 #include <vector>
 
 #include "biharm.h"
@@ -10,6 +12,13 @@
 #include "setup.h"
 
 namespace bh {
+
+// Patch size m^d from which the exact local solver multiplies the patches of a
+// run with its dense inverse as one matrix product (cuBLAS): the per-patch
+// product streams the whole inverse from L2 for every few patches.  Measured
+// on one 3D MVS step: at m^d = 343 (k = 4) the per-patch kernel is still 15 %
+// faster; at 729 and above the product is the only usable form.
+constexpr int kExactGemmMin = 512;
 
 struct Level {
   LevelGeom g{};
@@ -22,6 +31,9 @@ struct Level {
   double *db64 = nullptr, *dx64 = nullptr;
   int* verts = nullptr;  // vertex ids sorted by color
   int coff[17] = {0};    // color offsets into verts
+  // exact local solver by dense products: per color, runs of verts sharing a
+  // boundary-type combination {first, count, combination slot}
+  std::vector<std::array<int, 3>> runs[16];
 };
 
 }  // namespace bh
@@ -41,6 +53,13 @@ struct bh_ctx {
   int coarse_n = 0;
   double* ainv64 = nullptr;
   float* ainv32 = nullptr;
+  // exact local solver on large patches (m^d >= kExactGemmMin): the patch
+  // tensors of one run as matrix columns, multiplied by the inverse with cuBLAS
+  bool exact_gemm = false;
+  int gemm_cols = 0;  // largest run
+  double *gR64 = nullptr, *gY64 = nullptr;
+  float *gR32 = nullptr, *gY32 = nullptr;
+  cublasHandle_t blas = nullptr;
   // GMRES workspace (allocated on first solve)
   int m = 0;
   double* V = nullptr;

@@ -436,6 +436,48 @@ __global__ void __launch_bounds__(256) patch_exact_kernel(const PatchArgs<T> a) 
   }
 }
 
+// patch tensors as the columns of a matrix (column j = patch verts[j], local
+// node l at row l): R[l + j MD] = r[node], and the reverse x[node] += Y[...]
+template <typename T, int D, int K>
+__global__ void __launch_bounds__(256) patch_gather_kernel(const T* __restrict__ r,
+                                                           const int* verts, int count, int N,
+                                                           int n, T* __restrict__ R) {
+  using C = PatchCfg<T, D, K>;
+  constexpr int M = C::M, MD = C::MD;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)count * MD) return;
+  const int j = (int)(e / MD), l = (int)(e % MD);
+  int type[D], combo;
+  int64_t base;
+  patch_geom<D>(verts[j], N, n, K, type, base, combo);
+  int c[3] = {0, 0, 0};
+  local_coords<D, M>(l, c);
+  const int64_t nn = n;
+  R[e] = r[base + c[0] + c[1] * nn + (D == 3 ? c[2] * nn * nn : 0)];
+}
+
+template <typename T, int D, int K, bool ATOMIC>
+__global__ void __launch_bounds__(256) patch_scatter_kernel(const T* __restrict__ Y,
+                                                            const int* verts, int count, int N,
+                                                            int n, T* x) {
+  using C = PatchCfg<T, D, K>;
+  constexpr int M = C::M, MD = C::MD;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)count * MD) return;
+  const int j = (int)(e / MD), l = (int)(e % MD);
+  int type[D], combo;
+  int64_t base;
+  patch_geom<D>(verts[j], N, n, K, type, base, combo);
+  int c[3] = {0, 0, 0};
+  local_coords<D, M>(l, c);
+  const int64_t nn = n;
+  T* o = x + base + c[0] + c[1] * nn + (D == 3 ? c[2] * nn * nn : 0);
+  if (ATOMIC)
+    atomicAdd(o, Y[e]);
+  else
+    *o += Y[e];
+}
+
 // ---------------------------------------------------------------------------
 // transfers: embedding prolongation and its transpose, one axis per pass
 // ---------------------------------------------------------------------------

@@ -62,6 +62,14 @@ struct Ops {
                                  const int* verts, int count, double scale, bool atomic,
                                  cudaStream_t st);
 
+  // R[:, j] = R_v r for the patches v = verts[j] (m^d rows, column-major), and
+  // x += R_v^T Y[:, j] (atomic for overlapping patches): the gather and scatter
+  // around a dense-matrix product of the exact local solver.
+  static cudaError_t patch_gather(const LevelGeom& g, const T* r, const int* verts, int count,
+                                  T* R, cudaStream_t st);
+  static cudaError_t patch_scatter(const LevelGeom& g, const T* Y, const int* verts, int count,
+                                   T* x, bool atomic, cudaStream_t st);
+
   // xf += P xc (embedding), fine geometry given; s0, s1 scratch of fine nd each.
   static cudaError_t prolongate_add(const void* tab, const LevelGeom& fine, const T* xc, T* xf,
                                     T* s0, T* s1, cudaStream_t st);

@@ -394,6 +394,61 @@ cudaError_t Ops<T>::patch_exact(const LevelGeom& g, const T* Ainv, const T* r, T
   return cudaErrorInvalidValue;
 }
 
+template <typename T, int D, int K>
+static cudaError_t patch_gather_k(const LevelGeom& g, const T* r, const int* verts, int count,
+                                  T* R, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t tot = (int64_t)count * PatchCfg<T, D, K>::MD;
+  patch_gather_kernel<T, D, K><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(r, verts, count,
+                                                                            g.N, g.n, R);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <typename T, int D, int K>
+static cudaError_t patch_scatter_k(const LevelGeom& g, const T* Y, const int* verts, int count,
+                                   T* x, bool atomic, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t tot = (int64_t)count * PatchCfg<T, D, K>::MD;
+  const unsigned grid = (unsigned)((tot + 255) / 256);
+  if (atomic)
+    patch_scatter_kernel<T, D, K, true><<<grid, 256, 0, st>>>(Y, verts, count, g.N, g.n, x);
+  else
+    patch_scatter_kernel<T, D, K, false><<<grid, 256, 0, st>>>(Y, verts, count, g.N, g.n, x);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::patch_gather(const LevelGeom& g, const T* r, const int* verts, int count,
+                                 T* R, cudaStream_t st) {
+  if (g.d == 2) {
+#define BH_CALL(KK) return patch_gather_k<T, 2, KK>(g, r, verts, count, R, st)
+    BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  } else {
+#define BH_CALL(KK) return patch_gather_k<T, 3, KK>(g, r, verts, count, R, st)
+    BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Ops<T>::patch_scatter(const LevelGeom& g, const T* Y, const int* verts, int count,
+                                  T* x, bool atomic, cudaStream_t st) {
+  if (g.d == 2) {
+#define BH_CALL(KK) return patch_scatter_k<T, 2, KK>(g, Y, verts, count, x, atomic, st)
+    BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  } else {
+#define BH_CALL(KK) return patch_scatter_k<T, 3, KK>(g, Y, verts, count, x, atomic, st)
+    BH_K_DISPATCH(g.k, BH_CALL)
+#undef BH_CALL
+  }
+  return cudaErrorInvalidValue;
+}
+
 // one transfer pass along `axis`; shapes per axis given for input and output
 template <typename T, int K, bool PROLONG>
 static cudaError_t xfer_pass(const XferTab<T, K>& tab, int d, int axis, const int* din,

@@ -113,6 +113,9 @@ SMOOTH_CASES = [
     (3, 4, 4, "mvs", "inexact"), (3, 5, 4, "mvs", "inexact"), (3, 7, 2, "mvs", "inexact"),
     (3, 6, 2, "mvs", "inexact"), (3, 3, 8, "mvs", "inexact"),
     (2, 3, 16, "mvs", "inexact"), (2, 5, 8, "mvs", "inexact"), (2, 7, 8, "mvs", "inexact"),
+    # exact local solvers: per-patch products (3D k = 4) and, for patches of
+    # m^3 >= 512 unknowns, one dense product per run of a type combination
+    (3, 4, 4, "mvs", "exact"), (3, 5, 4, "avs", "exact"), (3, 5, 2, "mvs", "exact"),
 ]
 
 

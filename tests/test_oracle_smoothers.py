@@ -164,3 +164,31 @@ def test_single_patch_exact_step_solves():
         b = np.random.default_rng(5).standard_normal(A.shape[0])
         x = smoothers.avs_step(A, loc, b, np.zeros_like(b), 1.0)
         assert np.allclose(A @ x, b, atol=1e-10 * np.abs(b).max())
+
+
+@pytest.mark.parametrize("d,k", [(2, 4), (3, 3)])
+def test_patch_matrices_related_by_reflection_and_axis_permutation(d, k):
+    """Every exact patch matrix A_v (N = 4: left-boundary, interior and right-
+    boundary vertices in each direction) equals a canonical one (no right-
+    boundary direction, boundary directions first) with the right-boundary
+    axes reversed and the axes permuted: the reflection and permutation
+    symmetry of the tensor form, which lets the library invert 4 (3D) instead
+    of 27 patch matrices."""
+    N, m = 4, 2 * k - 1
+    loc = LocalSolvers(assemble.c0ip_matrix(d, k, N), d, k, N)
+    mats = {v: loc.matrix(v) for v in itertools.product(range(1, N), repeat=d)}
+    kind = {1: "left", 2: "interior", 3: "right"}
+    for v, Av in mats.items():
+        t = [kind[x] for x in v]
+        refl = [ti == "right" for ti in t]
+        bnd = [ti != "interior" for ti in t]
+        order = sorted(range(d), key=lambda a: not bnd[a])      # boundary axes first
+        vc = tuple(1 if bnd[a] else 2 for a in order)           # canonical vertex
+        idx = []
+        for I in range(m ** d):
+            ii = [(I // m ** a) % m for a in range(d)]
+            idx.append(sum((m - 1 - ii[order[b]] if refl[order[b]] else ii[order[b]]) * m ** b
+                           for b in range(d)))
+        idx = np.array(idx)
+        G = mats[vc][np.ix_(idx, idx)]
+        assert np.abs(G - Av).max() <= 1e-13 * np.abs(Av).max(), v
