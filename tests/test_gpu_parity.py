@@ -229,6 +229,27 @@ def test_mixed_precision_solve(bh, d, k, L, mode):
     assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
 
 
+def test_mixed_precision_exact_local_solver_3d(bh):
+    """3D k = 5 with exact local solvers (one dense product per run of a type
+    combination, cuBLAS DGEMM / SGEMM): FP64 and the FP32 V-cycle with FP64
+    defects reach the 1e-8 true residual, at most one iteration apart, both
+    within 1e-6 of the dense solve."""
+    d, k, L = 3, 5, 2
+    n = (k * 2 ** L - 1) ** d
+    b = workload.rhs_uniform(n, 23)
+    exact = np.linalg.solve(oracle_A(d, k, 2 ** L).toarray(), b)
+    res = {}
+    for pr in (bh.FP64, bh.MIXED_FP32_R64):
+        with make_ctx(bh, d, k, L, precision=pr, local_solver=bh.EXACT,
+                      gmres_side=bh.RIGHT) as ctx:
+            X = torch.empty(n, dtype=torch.float64, device="cuda")
+            res[pr] = ctx.solve(cuda(b), X, 1e-8, 100) + (host(X),)
+    (it64, rr64, x64), (it32, rr32, x32) = res[bh.FP64], res[bh.MIXED_FP32_R64]
+    assert rr64 <= 1.0001e-8 and rr32 <= 1.0001e-8
+    assert abs(it32 - it64) <= 1, (it32, it64)
+    assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
+
+
 @pytest.mark.parametrize("k", [6, 7])
 def test_mixed_precision_3d_high_degree(bh, k):
     """3D, k = 6 and 7 on 4^3 cells (the FP32 3D smoothing kernel at its largest
