@@ -17,7 +17,7 @@
 //   x-split: T_M on the 4k+1 window rows, T_L and T_B on the 2k+1 middle rows
 //   y-combine: m^2 residual values, (5k+6) FMAs each
 //   FDM: 4 m^3 FMAs + m^2 scalings (tiles touching the boundary), or the
-//   folded form, 4 m (2k^2 + k - 2) operations (interior tiles)
+//   folded form, 2 m (4k^2 + k - 3) operations (interior tiles)
 // Every stage is split into half-lines or single points so that all threads of
 // a warp run the same FP64 instruction stream.
 #pragma once
@@ -289,7 +289,8 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
 // loads the window values of its half-line into registers, so that each FP64
 // FMA needs one shared-memory load instead of two.  The interior 1D
 // pencil is centrosymmetric, so the FDM lines take the folded form (even and
-// odd eigenvectors, 2K^2 + K - 2 operations per line instead of (2K-1)^2).
+// odd eigenvectors: 2K^2 + K - 2 operations per forward line and 2K^2 - 1 per
+// backward line instead of (2K-1)^2).
 
 // T_M along a window row: o[j - 1] = (M x)(j) for the half's positions j.  The
 // window values live in registers, so each output is stored as soon as it is
