@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -753,8 +754,17 @@ bh_status prepare(bh_batch* b) {
   size_t smem = 0;
   for (int p = 0; p < b->P; ++p)
     smem = std::max(smem, mvs_smem(b->k[p], std::min(mvs_pb(b, b->k[p]), mvs_pb_max(b->k[p]))));
-  BCK(cudaFuncSetAttribute(mvs2_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem));
+  {
+    // only ever raise the kernel's limit: graphs of other live batches may
+    // launch it with more shared memory than this batch needs
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa{};
+    BCK(cudaFuncGetAttributes(&fa, mvs2_batch_kernel));
+    if ((int)smem > fa.maxDynamicSharedSizeBytes)
+      BCK(cudaFuncSetAttribute(mvs2_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  }
   // one side stream and join event per degree present (created once)
   int groups = 0;
   for (int k = 0; k <= kMaxK; ++k)

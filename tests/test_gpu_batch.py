@@ -109,3 +109,26 @@ def test_batch_autotuner_keeps_results(bh, tmp_path, monkeypatch):
     assert all(abs(a - b) <= 1 for a, b in zip(its1, its0))
     for a, b in zip(xs0, xs1):
         assert (a - b).abs().max().item() <= 1e-6 * b.abs().max().item()
+
+
+def test_two_live_batches_with_different_tile_memory(bh):
+    """A batch whose tiles need little shared memory, created while another
+    batch with large tiles is alive, must not lower the kernel's limit under
+    the first batch's captured graph: both keep solving."""
+    big = [(2, 7, 4), (2, 6, 4)]
+    small = [(2, 2, 5)]
+    rhs = {p: torch.tensor(workload.rhs_uniform((p[1] * 2 ** p[2] - 1) ** 2, p[1]),
+                           dtype=torch.float64, device="cuda") for p in big + small}
+    with bh.Batch([bh.default_params(d, k, L) for d, k, L in big]) as b1:
+        b1.set_tile(7, 6)
+        xs1 = [torch.empty_like(rhs[p]) for p in big]
+        its1, _ = b1.solve([rhs[p] for p in big], xs1, 1e-8, 50)
+        with bh.Batch([bh.default_params(d, k, L) for d, k, L in small]) as b2:
+            b2.set_tile(2, 1)
+            xs2 = [torch.empty_like(rhs[p]) for p in small]
+            b2.solve([rhs[p] for p in small], xs2, 1e-8, 50)
+            again = [torch.empty_like(rhs[p]) for p in big]
+            its2, _ = b1.solve([rhs[p] for p in big], again, 1e-8, 50)
+    assert its2 == its1
+    for a, b in zip(xs1, again):
+        assert torch.equal(a, b)
