@@ -874,7 +874,10 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
       }
     }
   }
-  if (cudaDeviceSynchronize() != cudaSuccess)
+  // the uploads above are synchronous; wait only for this context's stream, not
+  // for the device, so that a context created while others solve (the serving
+  // form's slots) does not wait for their work
+  if (cudaStreamSynchronize(c->st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return bail(fail(BH_ECUDA, std::string("setup: ") + cudaGetErrorString(cudaGetLastError())));
   *out = c;
   return BH_OK;
