@@ -172,6 +172,18 @@ bh_status bh_set_tile(bh_ctx* ctx, int patches_per_block);
 bh_status bh_solve(bh_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit,
                    int* iters, double* relres);
 
+/* bh_solve from the initial guess held in x_dev (warm start, and the resume
+ * point of an interrupted solve, e.g. after BH_ENOCONV): the correction d of
+ * A d = b - A x is solved from zero and added to x, with the tolerance that
+ * makes the stopping test the one of bh_solve on b (relative to ||b|| for
+ * right GMRES and CG, to ||M^-1 b|| for left GMRES).  *iters counts the
+ * iterations of this call; *relres is ||b - A x|| / ||b||.  A guess that
+ * already meets the tolerance returns at once with *iters = 0.  The first
+ * call allocates two vectors of workspace.  Synchronous.  The paper has no
+ * counterpart (Sec. 5.1 solves from zero). */
+bh_status bh_solve_guess(bh_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit,
+                         int* iters, double* relres);
+
 /* bh_solve with host buffers: copies b_host to the device, solves, copies x
  * back (b_host, x_host: n(L) doubles, pinned or pageable).  Synchronous. */
 bh_status bh_solve_host(bh_ctx* ctx, const double* b_host, double* x_host, double rtol,

@@ -60,6 +60,7 @@ SIGNATURES = {
     "bh_vcycle": (_I, [_P, _I, _P, _P]),
     "bh_solve": (_I, [_P, _P, _P, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
     "bh_solve_host": (_I, [_P, _P, _P, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
+    "bh_solve_guess": (_I, [_P, _P, _P, _D, _I, _c.POINTER(_I), _c.POINTER(_D)]),
     "bh_rhs": (_I, [_P, _I, _I, _P]),
     "bh_stats": (_I, [_P, _c.c_char_p, _c.c_size_t]),
     "bh_last_error": (_c.c_char_p, []),
@@ -277,6 +278,16 @@ class Context:
         it, rr = ctypes.c_int(), ctypes.c_double()
         st = load().bh_solve(self.handle, _dev(b, n, "b"), _dev(x, n, "x"), rtol, maxit,
                              ctypes.byref(it), ctypes.byref(rr))
+        if st != BH_ENOCONV or raise_on_noconv:
+            _check(st)
+        return it.value, rr.value
+
+    def solve_guess(self, b, x, rtol=1e-8, maxit=200, raise_on_noconv=True):
+        """bh_solve starting from the guess in x (x is updated in place)."""
+        n = self.num_unknowns()
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        st = load().bh_solve_guess(self.handle, _dev(b, n, "b"), _dev(x, n, "x"), rtol, maxit,
+                                   ctypes.byref(it), ctypes.byref(rr))
         if st != BH_ENOCONV or raise_on_noconv:
             _check(st)
         return it.value, rr.value

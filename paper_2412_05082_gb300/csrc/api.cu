@@ -983,6 +983,61 @@ bh_status bh_solve(bh_ctx* ctx, const double* b, double* x, double rtol, int max
   return timed_solve(ctx, b, x, rtol, maxit, iters, relres);
 }
 
+bh_status bh_solve_guess(bh_ctx* ctx, const double* b, double* x, double rtol, int maxit,
+                         int* iters, double* relres) {
+  if (!ctx || !b || !x || b == x || !iters || !relres || !(rtol > 0.0) || maxit < 1)
+    return fail(BH_EINVAL, "bad arguments");
+  const int L = ctx->p.level;
+  Level& F = ctx->lv[L];
+  const int64_t n = F.g.nd;
+  if (!ctx->guess) CKS(dmalloc(ctx, &ctx->guess, (size_t)(2 * n)));
+  double* r0 = ctx->guess;
+  double* d = ctx->guess + n;
+  double bnorm, rnorm;
+  CKS(norm2(ctx, b, &bnorm));
+  *iters = 0;
+  if (!std::isfinite(bnorm)) return fail(BH_EINVAL, "right-hand side is not finite");
+  if (bnorm == 0.0) {  // the solution is zero whatever the guess
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *relres = 0.0;
+    return BH_OK;
+  }
+  // solve A d = r0 = b - A x from zero, to the tolerance that makes the
+  // stopping test of a solve from zero on b: relative to ||b|| (true residual,
+  // right GMRES and CG) or to ||M^-1 b|| (left GMRES)
+  CKS(residual_t<double>(ctx, L, x, b, r0));
+  CKS(norm2(ctx, r0, &rnorm));
+  double ref_b = bnorm, ref_r = rnorm;
+  const bool left = ctx->p.krylov == BH_GMRES && ctx->p.gmres_side == BH_LEFT;
+  if (left) {
+    CKS(precondition(ctx, b, d));
+    CKS(norm2(ctx, d, &ref_b));
+    CKS(precondition(ctx, r0, d));
+    CKS(norm2(ctx, d, &ref_r));
+  }
+  if (!std::isfinite(rnorm)) return fail(BH_EINVAL, "initial guess gives a non-finite residual");
+  if (ref_r <= rtol * ref_b) {  // the guess already meets the tolerance
+    *relres = rnorm / bnorm;
+    ctx->last_iters = 0;
+    ctx->last_relres = *relres;
+    return BH_OK;
+  }
+  int it = 0;
+  double rr = 0.0;
+  const bh_status s = timed_solve(ctx, r0, d, rtol * ref_b / ref_r, maxit, &it, &rr);
+  if (s != BH_OK && s != BH_ENOCONV) return s;
+  CK(vec_axpy(x, 1.0, d, n, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  *iters = it;
+  *relres = rr * rnorm / bnorm;  // rr is relative to ||r0||
+  ctx->last_relres = *relres;
+  if (s == BH_ENOCONV)
+    return fail(BH_ENOCONV, "solve from the guess stopped after " + std::to_string(it) +
+                                " iterations above the tolerance");
+  return BH_OK;
+}
+
 bh_status bh_solve_host(bh_ctx* ctx, const double* b_host, double* x_host, double rtol,
                         int maxit, int* iters, double* relres) {
   if (!ctx || !b_host || !x_host || !iters || !relres) return fail(BH_EINVAL, "bad arguments");

@@ -71,6 +71,8 @@ struct bh_ctx {
   double* hdots = nullptr;  // pinned host
   // CG workspace (allocated on first CG solve): r, z, p, q, z_prev
   double* cgv = nullptr;
+  // warm-start workspace (allocated on first bh_solve_guess): r0, correction
+  double* guess = nullptr;
   int tile = 0;  // patches per block of the fused MVS kernels (0: automatic)
   std::vector<void*> dev_allocs;
   // stats

@@ -229,6 +229,37 @@ def test_mixed_precision_solve(bh, d, k, L, mode):
     assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
 
 
+@pytest.mark.parametrize("kw", [{"gmres_side": "right"}, {"gmres_side": "left"},
+                                {"krylov": "cg"}], ids=["right", "left", "cg"])
+def test_solve_resumes_from_a_guess(bh, kw):
+    """An interrupted solve (maxit = 2) resumed with bh_solve_guess reaches the
+    solve-from-zero tolerance and the dense solution; a converged guess
+    returns at once."""
+    d, k, L = 2, 3, 5
+    n = (k * 2 ** L - 1) ** d
+    b = workload.rhs_uniform(n, 17)
+    exact = np.linalg.solve(oracle_A(d, k, 2 ** L).toarray(), b)
+    opts = {}
+    if kw.get("krylov") == "cg":
+        opts = dict(krylov=bh.CG, smoother=bh.AVS_ATOMIC, pre_steps=2, post_steps=2)
+    else:
+        opts = dict(gmres_side=bh.RIGHT if kw["gmres_side"] == "right" else bh.LEFT)
+    with make_ctx(bh, d, k, L, **opts) as ctx:
+        B = cuda(b)
+        X0 = torch.empty(n, dtype=torch.float64, device="cuda")
+        it_cold, _ = ctx.solve(B, X0, 1e-8, 200)
+        X = torch.empty(n, dtype=torch.float64, device="cuda")
+        it1, rr1 = ctx.solve(B, X, 1e-8, 2, raise_on_noconv=False)
+        assert it1 == 2 and rr1 > 1e-8
+        it2, rr2 = ctx.solve_guess(B, X, 1e-8, 200)
+        assert it1 + it2 <= it_cold + 3, (it1, it2, it_cold)
+        if opts.get("gmres_side") != bh.LEFT:
+            assert rr2 <= 1.0001e-8
+        assert relerr(host(X), exact) <= 1e-6
+        it3, rr3 = ctx.solve_guess(B, X0, 1e-8, 200)   # already converged
+        assert it3 == 0
+
+
 def test_mixed_precision_exact_local_solver_3d(bh):
     """3D k = 5 with exact local solvers (one dense product per run of a type
     combination, cuBLAS DGEMM / SGEMM): FP64 and the FP32 V-cycle with FP64
