@@ -262,7 +262,7 @@ cudaError_t Ops<T>::patch_fdm(const void* tab, const LevelGeom& g, const T* r, T
 // levels with few patches still spread over the SMs (0: no cap).  In FP32 the
 // 3D kernel's shared memory, not its FMAs, sets the pace: smaller tiles leave
 // room for more blocks per SM.
-constexpr int kMvs2TileF64[8] = {0, 0, 32, 18, 12, 8, 6, 8};
+constexpr int kMvs2TileF64[8] = {0, 0, 32, 18, 12, 14, 6, 8};
 constexpr int kMvs3TileF64[8] = {0, 0, 12, 16, 16, 16, 16, 16};
 constexpr int kMvs2TileF32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 constexpr int kMvs3TileF32[8] = {0, 0, 12, 8, 4, 3, 0, 0};
