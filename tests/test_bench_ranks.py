@@ -66,3 +66,57 @@ def test_reference_arm_under_torchrun_prints_once_on_rank_0():
     r = json.loads(lines[0])
     assert r["impl"] == "reference" and r["value"] > 0 and r["steps"] == 1
     assert r["e2e"]["h2d_bytes_per_step"] == 0 and r["cpu_baseline"]["kind"] == "oracle"
+
+
+def _fake_smi(tmp_path, lines):
+    """A stand-in for nvidia-smi that prints fixed samples and then waits to
+    be terminated, as the real one does under -lms."""
+    smi = tmp_path / "nvidia-smi"
+    body = "".join("echo '%s'\n" % ln for ln in lines)
+    smi.write_text("#!/bin/sh\n" + body + "sleep 30\n")
+    smi.chmod(0o755)
+    return str(tmp_path)
+
+
+def _sample_clocks(monkeypatch, bindir, keep_path=None):
+    import time
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("PATH", bindir + os.pathsep + os.environ["PATH"])
+    if keep_path:
+        monkeypatch.setenv("BH_CLOCKS_CSV", keep_path)
+    else:
+        monkeypatch.delenv("BH_CLOCKS_CSV", raising=False)
+    with bench.Clocks(0) as clk:
+        time.sleep(0.5)
+    return clk, clk.summary()
+
+
+def test_clock_summary_median_max_and_reasons(tmp_path, monkeypatch):
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2055, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "garbage line"]
+    clk, s = _sample_clocks(monkeypatch, _fake_smi(tmp_path, lines))
+    assert s["samples"] == 3
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    assert not os.path.exists(clk.path)  # the temporary sample file is removed
+
+
+def test_clock_summary_keeps_samples_where_asked(tmp_path, monkeypatch):
+    lines = ["0, 2070, 2070, 900.1, 0x0, Active, Not Active, Not Active, Not Active"]
+    keep = str(tmp_path / "clocks.csv")
+    clk, s = _sample_clocks(monkeypatch, _fake_smi(tmp_path, lines), keep)
+    assert s["reasons"] == ["hw_slowdown"] and s["samples"] == 1
+    assert clk.path == keep and os.path.exists(keep)
+
+
+def test_clock_summary_without_nvidia_smi(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("PATH", str(tmp_path))
+    with bench.Clocks(0) as clk:
+        pass
+    assert clk.summary()["reasons"] == ["nvidia-smi unavailable"]
+    assert clk.fh.closed and not os.path.exists(clk.path)
