@@ -196,7 +196,13 @@ bh_status bh_rhs(bh_ctx* ctx, int level, int kind, double* b_dev);
 
 /* Counters of the context and the CUDA-event device time of its last
  * bh_solve / bh_solve_host ("last_solve_ms") as a JSON object written to buf
- * (NUL-terminated, truncated to len).  Host only. */
+ * (NUL-terminated, truncated to len).  Host only.  Of the last solve:
+ * "last_iters", "last_relres" (the true ||b - A x|| / ||b|| that the call
+ * returned) and "last_estimate", the ratio its stopping test compared with
+ * rtol: the Givens estimate of the minimized residual over its initial value
+ * for GMRES (preconditioned for BH_LEFT, true for BH_RIGHT), ||r_j|| / ||b||
+ * for CG; for bh_solve_guess, relative to the reference of a solve from zero.
+ * The fractional iteration count of Sec. 5.1 is -8 iters / log10(estimate). */
 bh_status bh_stats(const bh_ctx* ctx, char* buf, size_t len);
 
 /* Message of the last failed call on this thread ("" if none). */

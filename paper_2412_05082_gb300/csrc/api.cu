@@ -458,6 +458,7 @@ bh_status solve_cg(bh_ctx* c, const double* b, double* x, double rtol, int maxit
   c->n_solve++;
   c->last_iters = it;
   c->last_relres = *relres;
+  c->last_estimate = rn / bnorm;
   if (!(rn <= rtol * bnorm))
     return fail(BH_ENOCONV, "CG stopped after " + std::to_string(it) +
                                 " iterations above the tolerance");
@@ -551,6 +552,7 @@ bh_status solve_dev(bh_ctx* c, const double* b, double* x, double rtol, int maxi
   c->n_solve++;
   c->last_iters = it;
   c->last_relres = *relres;
+  c->last_estimate = est / ref;
   if (!(est <= rtol * ref)) return fail(BH_ENOCONV, "GMRES stopped after " + std::to_string(it) +
                                                         " iterations above the tolerance");
   return BH_OK;
@@ -1021,6 +1023,7 @@ bh_status bh_solve_guess(bh_ctx* ctx, const double* b, double* x, double rtol, i
     *relres = rnorm / bnorm;
     ctx->last_iters = 0;
     ctx->last_relres = *relres;
+    ctx->last_estimate = ref_r / ref_b;
     return BH_OK;
   }
   int it = 0;
@@ -1032,6 +1035,7 @@ bh_status bh_solve_guess(bh_ctx* ctx, const double* b, double* x, double rtol, i
   *iters = it;
   *relres = rr * rnorm / bnorm;  // rr is relative to ||r0||
   ctx->last_relres = *relres;
+  ctx->last_estimate *= ref_r / ref_b;  // the inner estimate is relative to ref_r
   if (s == BH_ENOCONV)
     return fail(BH_ENOCONV, "solve from the guess stopped after " + std::to_string(it) +
                                 " iterations above the tolerance");
@@ -1111,12 +1115,13 @@ bh_status bh_stats(const bh_ctx* ctx, char* buf, size_t len) {
                 "{\"dim\": %d, \"degree\": %d, \"level\": %d, \"gamma\": %.17g, \"omega\": %.17g, "
                 "\"smoother\": %d, \"local_solver\": %d, \"precision\": %d, \"applies\": %lld, "
                 "\"smooth_steps\": %lld, \"vcycles\": %lld, \"solves\": %lld, "
-                "\"last_iters\": %d, \"last_relres\": %.17g, \"last_solve_ms\": %.6g, "
+                "\"last_iters\": %d, \"last_relres\": %.17g, \"last_estimate\": %.17g, "
+                "\"last_solve_ms\": %.6g, "
                 "\"kernel_launches\": %lld}",
                 ctx->p.dim, ctx->p.degree, ctx->p.level, ctx->p.gamma, ctx->p.omega,
                 ctx->p.smoother, ctx->p.local_solver, ctx->p.precision, ctx->n_apply,
                 ctx->n_smooth, ctx->n_vcycle, ctx->n_solve, ctx->last_iters, ctx->last_relres,
-                ctx->last_solve_ms, (long long)g_kernel_launches.load());
+                ctx->last_estimate, ctx->last_solve_ms, (long long)g_kernel_launches.load());
   return BH_OK;
 }
 

@@ -79,6 +79,7 @@ struct bh_ctx {
   long long n_apply = 0, n_smooth = 0, n_vcycle = 0, n_solve = 0;
   int last_iters = 0;
   double last_relres = 0;
+  double last_estimate = 0;           // the stopping test's residual ratio at the last stop
   double last_solve_ms = 0;           // CUDA-event device time of the last bh_solve(_host)
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int ncolors() const { return p.dim == 2 ? 8 : 16; }

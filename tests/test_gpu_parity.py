@@ -198,10 +198,16 @@ def test_solve_matches_oracle(bh, d, k, L, side):
     with make_ctx(bh, d, k, L, gmres_side=bh.LEFT if side == "left" else bh.RIGHT) as ctx:
         X = torch.empty(len(b), dtype=torch.float64, device="cuda")
         it, rr = ctx.solve(cuda(b), X, 1e-8, 100)
+        est = ctx.stats()["last_estimate"]
     assert abs(it - it_ref) <= 1
     if side == "right":
         assert rr <= 1.0001e-8
     assert relerr(host(X), xr) <= 1e-6
+    # the stopping test's ratio (preconditioned for left GMRES), which the
+    # fractional iteration counts of Sec. 5.1 are computed from
+    assert est <= 1e-8
+    if it == it_ref:
+        assert abs(est / (hist[-1] / hist[0]) - 1.0) <= 1e-3, (est, hist[-1] / hist[0])
 
 
 @pytest.mark.parametrize("d,k,L,mode", [(2, 2, 5, "fp32"), (2, 3, 5, "fp32"), (2, 4, 4, "fp32"),
@@ -337,8 +343,12 @@ def test_cg_solve_matches_oracle(bh, d, k, L, sm, ls):
                   krylov=bh.CG) as ctx:
         X = torch.empty(len(b), dtype=torch.float64, device="cuda")
         it, rr = ctx.solve(cuda(b), X, 1e-8, 300)
+        est = ctx.stats()["last_estimate"]
     assert abs(it - it_ref) <= 1, (it, it_ref)
     assert rr <= 1.5e-8 and rr_ref <= 1.5e-8
+    assert est <= 1e-8
+    if it == it_ref:
+        assert abs(est / (hist[-1] / hist[0]) - 1.0) <= 1e-3, (est, hist[-1] / hist[0])
     assert relerr(host(X), xr) <= 1e-6
 
 
