@@ -346,9 +346,12 @@ def test_cg_solve_matches_oracle(bh, d, k, L, sm, ls):
         est = ctx.stats()["last_estimate"]
     assert abs(it - it_ref) <= 1, (it, it_ref)
     assert rr <= 1.5e-8 and rr_ref <= 1.5e-8
-    assert est <= 1e-8
-    if it == it_ref:
-        assert abs(est / (hist[-1] / hist[0]) - 1.0) <= 1e-3, (est, hist[-1] / hist[0])
+    # CG stops on its recursively updated residual, which stays within
+    # rounding of the true one on these small problems.  Its last value is
+    # not compared with the oracle's: the residual norm of CG is not monotone,
+    # and perturbing the oracle's preconditioner by 1e-13 relative already
+    # moves it by a few per cent and can add an iteration.
+    assert est <= 1e-8 and abs(est - rr) <= 1e-10, (est, rr)
     assert relerr(host(X), xr) <= 1e-6
 
 
