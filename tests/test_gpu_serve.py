@@ -43,8 +43,17 @@ def test_results_same_alone_and_in_the_mix(bh):
         tickets = [srv.submit(d, k, L, b, x) for (d, k, L), b, x in zip(REQS, rhs, outs)]
         res = [srv.wait(t, 300.0) for t in tickets]
         st = srv.stats()
+        # a shape whose hierarchy is resident and idle reuses it (two requests
+        # of one shape that overlap in time need two, so the mix above may
+        # have created one per request)
+        xr = np.zeros_like(rhs[0])
+        again = srv.wait(srv.submit(*REQS[0], rhs[0], xr), 300.0)
+        st2 = srv.stats()
     assert st["completed"] == len(REQS)
-    assert st["created"] <= len(set(REQS))  # shapes reuse their resident hierarchy
+    assert len(set(REQS)) <= st["created"] <= len(REQS)
+    assert again["status"] == bh.BH_OK and st2["created"] == st["created"]
+    assert again["iters"] == res[0]["iters"]
+    assert np.abs(xr - outs[0]).max() <= 1e-12 * np.abs(outs[0]).max()
     for (d, k, L), b, x, r in zip(REQS, rhs, outs, res):
         assert r["status"] == bh.BH_OK
         assert r["relres"] <= 1.0001e-8
