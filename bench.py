@@ -352,11 +352,24 @@ TABLE_COLUMNS = {
 }
 
 
+def table_entries(golden):
+    """Every printed entry of the tables as (DoFs, column, row, col, d, k, L),
+    smallest problem first."""
+    entries = []
+    for name, (d, _, _, _) in TABLE_COLUMNS.items():
+        levels = golden["tab3_levels"] if d == 3 else golden["levels"]
+        for i, L in enumerate(levels):
+            for j, k in enumerate(golden["degrees"]):
+                if golden[name][i][j] is not None:
+                    entries.append(((k * 2 ** L + 1) ** d, name, i, j, d, k, L))
+    return sorted(entries)
+
+
 def run_tables(args):
     """Fractional iteration counts nu_frac = -8 n / log10(|r_n| / |r_0|) of the
     paper's Tables 1-3 (Sec. 5.1) on the GPU at the printed levels, with r the
     residual each Krylov method's stopping test measures (preconditioned for
-    left GMRES, as in deal.II, whose solvers the tables come from): the paper's
+    left GMRES, the convention of deal.II, the library of Sec. 5): the paper's
     sine right-hand side, CG with the additive smoother (atomic AVS) and left-
     preconditioned GMRES with the colored multiplicative one, the damping of
     Sec. 5.1, exact coarse solve, relative reduction 1e-8.  Entries are run in
@@ -367,14 +380,7 @@ def run_tables(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     golden = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_tables_nu_frac.json")))
-    entries = []
-    for name, (d, smoother, steps, ls) in TABLE_COLUMNS.items():
-        levels = golden["tab3_levels"] if d == 3 else golden["levels"]
-        for i, L in enumerate(levels):
-            for j, k in enumerate(golden["degrees"]):
-                if golden[name][i][j] is not None:
-                    entries.append(((k * 2 ** L + 1) ** d, name, i, j, d, k, L))
-    entries.sort()
+    entries = table_entries(golden)
     out = {}
     for name in TABLE_COLUMNS:
         rows, cols = len(golden[name]), len(golden["degrees"])

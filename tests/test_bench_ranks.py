@@ -120,3 +120,21 @@ def test_clock_summary_without_nvidia_smi(tmp_path, monkeypatch):
         pass
     assert clk.summary()["reasons"] == ["nvidia-smi unavailable"]
     assert clk.fh.closed and not os.path.exists(clk.path)
+
+
+def test_table_entries_cover_every_printed_value():
+    """The --tables mode runs one solve per printed entry of Tables 1-3, with
+    the DoF count (kN+1)^d of the paper's convention, smallest first."""
+    sys.path.insert(0, ROOT)
+    import bench
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_tables_nu_frac.json")))
+    assert set(bench.TABLE_COLUMNS) == {n for n in golden if n.startswith("tab") and n != "tab3_levels"}
+    entries = bench.table_entries(golden)
+    printed = sum(v is not None for n in bench.TABLE_COLUMNS for row in golden[n] for v in row)
+    assert len(entries) == printed == 192
+    assert [e[0] for e in entries] == sorted(e[0] for e in entries)
+    for dofs, name, i, j, d, k, L in entries:
+        assert golden[name][i][j] is not None and dofs == (k * 2 ** L + 1) ** d
+        assert d == (3 if name.startswith("tab3") else 2)
+    # the paper's caption: only levels with 5e4 to 1e7 DoFs (2D) were computed
+    assert min(e[0] for e in entries if e[4] == 2) >= 5e4
