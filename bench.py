@@ -183,7 +183,24 @@ for k in range(2, 8):
     done.append(k)
     if t_tot > %f:
         break
-print(json.dumps({"t": t_tot, "dofs": dofs, "ks": done}))
+# the two kernels of the path on their own, 2D Q4: apply_A (CSR product) on
+# 64^2 cells and one multiplicative smoothing step on 16^2 cells, best of 3
+from oracle import smoothers
+def best(fn):
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter(); fn(); ts.append(time.perf_counter() - t0)
+    return min(ts)
+Ha = mg.Hierarchy(2, 4, 6)
+xa = workload.vector_uniform(Ha.A[6].shape[0], 1)
+t_apply = best(lambda: Ha.A[6] @ xa)
+Hs = mg.Hierarchy(2, 4, 4)
+ns = Hs.A[4].shape[0]
+xs, bs = workload.vector_uniform(ns, 2), workload.rhs_uniform(ns, 3)
+t_mvs = best(lambda: smoothers.smooth("mvs", Hs.A[4], Hs.local[4], bs, xs, Hs.omega, 1))
+print(json.dumps({"t": t_tot, "dofs": dofs, "ks": done,
+                  "apply": workload.paper_dofs(2, 4, 64) / t_apply,
+                  "mvs_step": workload.paper_dofs(2, 4, 16) / t_mvs}))
 """ % (ROOT, budget_s)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
@@ -196,6 +213,10 @@ print(json.dumps({"t": t_tot, "dofs": dofs, "ks": done}))
             "sample": "oracle MG-GMRES solves (MVS 1+1, inexact local solvers by dense LU, left "
                       "preconditioning, 1e-8) of the 2D sweep family at N = 16 cells, k = %s; "
                       "paper DoF count / CPU time, one thread" % r["ks"],
+            "apply_dofs_per_s": r["apply"], "mvs_step_dofs_per_s": r["mvs_step"],
+            "kernels_sample": "2D Q4: oracle apply_A (CSR product) on 64^2 cells, one oracle "
+                              "MVS step (separable local matrices by dense LU, sequential patch loop) "
+                              "on 16^2 cells, best of 3",
             "host_cpus": os.cpu_count()}
 
 
