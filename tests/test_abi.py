@@ -106,3 +106,21 @@ def test_host_fdm_matches_oracle_patch_matrices(lib, k):
             # columns 0..k-1 and odd ones in k..m-1, exactly
             assert np.array_equal(S[::-1, :k], S[:, :k])
             assert np.array_equal(S[::-1, k:], -S[:, k:])
+
+
+def test_no_cpu_fallback(lib):
+    """Without a CUDA device the library refuses to build a hierarchy
+    (BH_ECUDA), and the binding refuses host tensors: nothing runs on the CPU
+    in their place."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+
+    class NoStream:
+        cuda_stream = 0
+
+    with pytest.raises(lib.BiharmError) as e:
+        lib.Context(lib.default_params(2, 2, 3), NoStream())
+    assert e.value.status == lib.BH_ECUDA
+    with pytest.raises(TypeError):
+        lib._dev(torch.zeros(3, dtype=torch.float64), 3, "x")
