@@ -56,6 +56,23 @@ def test_gmres_identity_preconditioner_solves_small_system():
     assert all(h1 <= h0 * (1 + 1e-12) for h0, h1 in zip(hist, hist[1:]))
 
 
+@pytest.mark.parametrize("side,j", [("left", 3), ("left", 7), ("right", 4)])
+def test_gmres_estimate_is_the_residual_of_the_iterate(side, j):
+    """The Givens estimate at step j is the norm of the residual that the
+    side minimizes, evaluated directly at the j-th iterate: M^-1 (b - A x_j)
+    for left preconditioning, b - A x_j for right.  The fractional iteration
+    counts are computed from this estimate."""
+    d, k, L = 2, 2, 4
+    H = mg.Hierarchy(d, k, L)
+    b = assemble.load_vector(d, k, 2 ** L, assemble.paper_sine_f)
+    x, it, hist, rr = krylov.gmres(H.A[L], b, H.preconditioner, 0.0, side=side, maxit=j)
+    assert it == j and len(hist) == j + 1
+    r = b - H.A[L] @ x
+    direct = np.linalg.norm(H.preconditioner(r) if side == "left" else r)
+    assert abs(hist[-1] / direct - 1.0) <= 1e-6  # rounding of a 1e-7 residual
+    assert abs(rr - np.linalg.norm(r) / np.linalg.norm(b)) <= 1e-12
+
+
 def test_gmres_restart_still_converges():
     A = assemble.c0ip_matrix(2, 2, 3)
     b = np.random.default_rng(1).standard_normal(A.shape[0])
