@@ -46,6 +46,19 @@ def test_prolongation_2d_reproduces_tensor_polynomials():
     assert np.allclose(P @ C, F, atol=1e-13)
 
 
+def test_prolongation_3d_reproduces_tensor_polynomials():
+    """The 3D embedding reproduces a coarse polynomial of degree <= k per
+    axis (vanishing on the boundary) at the fine interior nodes, with the
+    unknowns in x-fastest order."""
+    k, Nc = 3, 2
+    P = mg.prolongation(3, k, Nc)
+    f = lambda x, y, z: x * (1 - x) * (x + 0.5) * y * (1 - y) * z * (1 - z) * (2 - z)
+    xc, xf = _nodes(k, Nc)[1:-1], _nodes(k, 2 * Nc)[1:-1]
+    Zc, Yc, Xc = np.meshgrid(xc, xc, xc, indexing="ij")
+    Zf, Yf, Xf = np.meshgrid(xf, xf, xf, indexing="ij")
+    assert np.allclose(P @ f(Xc, Yc, Zc).ravel(), f(Xf, Yf, Zf).ravel(), atol=1e-13)
+
+
 def test_gmres_identity_preconditioner_solves_small_system():
     A = assemble.c0ip_matrix(2, 2, 3)
     b = np.random.default_rng(0).standard_normal(A.shape[0])

@@ -115,7 +115,8 @@ def test_avs_exact_error_propagation_spectrum(d, k, N):
     assert evE.min() > -1.0 and evE.max() < 1.0
 
 
-@pytest.mark.parametrize("d,k,N,ls", [(2, 2, 4, "exact"), (2, 3, 3, "exact"), (2, 2, 4, "inexact")])
+@pytest.mark.parametrize("d,k,N,ls", [(2, 2, 4, "exact"), (2, 3, 3, "exact"), (2, 2, 4, "inexact"),
+                                    (3, 2, 3, "exact")])
 def test_mvs_error_propagation_is_a_contraction(d, k, N, ls):
     A = assemble.c0ip_matrix(d, k, N)
     src = A if ls == "exact" else assemble.c0ip_matrix(d, k, N, mixed=False)
