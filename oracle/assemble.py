@@ -36,6 +36,8 @@ def default_gamma(k):
 
 
 def n_unknowns(d, k, N):
+    """Number of unknowns of V_l (Eq. (fespace)): the interior support points,
+    k N - 1 per direction, the boundary values being fixed to zero."""
     return (k * N - 1) ** d
 
 

@@ -31,6 +31,10 @@ def _u_hessian(x, a, b):
 
 
 def energy_error(d, k, N, u_interior, gamma=None):
+    """|u - u_l|_l of Eq. (hnorm) for the manufactured u and the discrete
+    solution u_l given by its interior coefficients: the broken H^2
+    seminorm by Gauss quadrature cell by cell, plus the penalty-weighted
+    jumps of the normal derivative of u_l on every face."""
     if gamma is None:
         gamma = default_gamma(k)
     h = 1.0 / N

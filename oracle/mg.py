@@ -50,6 +50,8 @@ def prolongation_1d(k, Nc, full=False):
 
 
 def prolongation(d, k, Nc):
+    """The embedding V_(l-1) -> V_l on interior unknowns (Sec. 3): the
+    Kronecker product of the 1D embedding over the d axes."""
     P1 = sp.csr_matrix(prolongation_1d(k, Nc))
     P = P1
     for _ in range(d - 1):
@@ -58,6 +60,10 @@ def prolongation(d, k, Nc):
 
 
 class Hierarchy:
+    """Levels 1..L of one problem: the rediscretized matrices A_l of Eq.
+    (bfc0ip), the local solvers of each level, the embeddings, and the
+    coarse factorization; vcycle is Algorithm 1."""
+
     def __init__(self, d, k, L, gamma=None, smoother="mvs", local_solver="inexact",
                  omega=None, pre=1, post=1, coarse="exact", operators=None):
         if gamma is None:
@@ -78,12 +84,14 @@ class Hierarchy:
         self.coarse_lu = sla.lu_factor(self.A[1].toarray())
 
     def coarse_solve(self, b):
+        """Level 1: the exact solve, or one smoothing step (Sec. 5.1)."""
         if self.coarse == "exact":
             return sla.lu_solve(self.coarse_lu, b)
         return smooth(self.smoother, self.A[1], self.local[1], b, np.zeros_like(b),
                       self.omega, 1)
 
     def vcycle(self, l, x, b):
+        """MG_l(x, b) of Algorithm 1."""
         if l == 1:
             return self.coarse_solve(b)
         A, loc = self.A[l], self.local[l]

@@ -34,12 +34,16 @@ def vertices(d, N):
 
 
 def color(v):
+    """MVS color of vertex v (Sec. 3, Fig. 1): the parity class of v, split
+    red-black by the parity of sum_a floor(v_a / 2) (the numbering is the
+    reading in the module docstring)."""
     par = sum((va % 2) << a for a, va in enumerate(v))
     rb = sum(va // 2 for va in v) % 2
     return 2 * par + rb
 
 
 def n_colors(d):
+    """8 colors in 2D, 16 in 3D (Sec. 3)."""
     return 2 ** (d + 1)
 
 
@@ -69,13 +73,17 @@ class LocalSolvers:
         self._lu = {}
 
     def dofs(self, v):
+        """R_v as an index list (Sec. 3)."""
         return patch_dofs(self.d, self.k, self.N, v)
 
     def matrix(self, v):
+        """The local matrix R_v A R_v^T of the source matrix: A_v (exact) or
+        the separable A~_v (Eq. (localsolverbila))."""
         I = self.dofs(v)
         return self.src[I][:, I].toarray()
 
     def solve(self, v, r):
+        """The local solve (local matrix)^-1 r by dense LU, factored once."""
         if v not in self._lu:
             self._lu[v] = sla.lu_factor(self.matrix(v))
         return sla.lu_solve(self._lu[v], r)

@@ -23,6 +23,8 @@ from .patches import color, vertices
 
 
 def avs_step(A, local, b, x, omega, verts=None):
+    """One additive vertex-patch step (Sec. 3): one residual, every patch's
+    local correction damped by omega and added."""
     if verts is None:
         verts = vertices(local.d, local.N)
     r = b - A @ x
@@ -34,6 +36,7 @@ def avs_step(A, local, b, x, omega, verts=None):
 
 
 def mvs_order(d, N):
+    """The vertex order of the colored MVS: by color, lexicographic inside."""
     vs = vertices(d, N)
     return sorted(vs, key=lambda v: (color(v), v[::-1]))
 
@@ -68,6 +71,7 @@ def mvs_colored_step(A, local, b, x, omega):
 
 
 def smooth(kind, A, local, b, x, omega, steps):
+    """`steps` applications of S_l (x, b) with the AVS or MVS of Sec. 3."""
     for _ in range(steps):
         if kind == "avs":
             x = avs_step(A, local, b, x, omega)
