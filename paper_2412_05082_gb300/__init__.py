@@ -232,21 +232,25 @@ class Context:
         self.close()
 
     def num_unknowns(self, level=None):
+        """bh_num_unknowns: (k N - 1)^d on `level` (default: the finest)."""
         level = self.params.level if level is None else level
         n = ctypes.c_int64()
         _check(load().bh_num_unknowns(self.handle, level, ctypes.byref(n)))
         return n.value
 
     def apply_A(self, level, x, y):
+        """bh_apply_A: y = A_l x (Eq. (bfc0ip) in the Kronecker form of Sec. 4)."""
         n = self.num_unknowns(level)
         _check(load().bh_apply_A(self.handle, level, _dev(x, n, "x"), _dev(y, n, "y")))
 
     def residual(self, level, x, b, r):
+        """bh_residual: r = b - A_l x."""
         n = self.num_unknowns(level)
         _check(load().bh_residual(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b"),
                                   _dev(r, n, "r")))
 
     def smooth(self, level, x, b, steps=1):
+        """bh_smooth: `steps` steps of the context's smoother (Sec. 3), x in place."""
         n = self.num_unknowns(level)
         _check(load().bh_smooth(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b"), steps))
 
@@ -257,15 +261,18 @@ class Context:
                                        first_color, end_color))
 
     def prolongate_add(self, level, xc, xf):
+        """bh_prolongate_add: xf += P xc, the embedding from level - 1 (Sec. 3)."""
         _check(load().bh_prolongate_add(self.handle, level,
                                         _dev(xc, self.num_unknowns(level - 1), "xc"),
                                         _dev(xf, self.num_unknowns(level), "xf")))
 
     def restrict(self, level, rf, bc):
+        """bh_restrict: bc = P^T rf onto level - 1."""
         _check(load().bh_restrict(self.handle, level, _dev(rf, self.num_unknowns(level), "rf"),
                                   _dev(bc, self.num_unknowns(level - 1), "bc")))
 
     def vcycle(self, level, x, b):
+        """bh_vcycle: x = MG_level(x, b), Algorithm 1."""
         n = self.num_unknowns(level)
         _check(load().bh_vcycle(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b")))
 
@@ -274,6 +281,8 @@ class Context:
         _check(load().bh_set_tile(self._h, int(patches_per_block)))
 
     def solve(self, b, x, rtol=1e-8, maxit=200, raise_on_noconv=True):
+        """bh_solve: x = A^-1 b by the context's Krylov method preconditioned by
+        one V-cycle (Sec. 5.1), from x = 0; returns (iterations, true relres)."""
         n = self.num_unknowns()
         it, rr = ctypes.c_int(), ctypes.c_double()
         st = load().bh_solve(self.handle, _dev(b, n, "b"), _dev(x, n, "x"), rtol, maxit,
@@ -308,9 +317,12 @@ class Context:
         return it.value, rr.value
 
     def rhs(self, level, kind, b):
+        """bh_rhs: the load vector of RHS_MANUFACTURED or RHS_PAPER_SINE on `level`."""
         _check(load().bh_rhs(self.handle, level, kind, _dev(b, self.num_unknowns(level), "b")))
 
     def stats(self):
+        """bh_stats as a dict (counters, last_iters, last_relres, last_estimate,
+        last_solve_ms)."""
         import json
         buf = ctypes.create_string_buffer(4096)
         _check(load().bh_stats(self.handle, buf, len(buf)))
