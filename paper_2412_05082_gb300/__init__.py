@@ -347,6 +347,7 @@ class Batch:
         self._h = h
 
     def sizes(self):
+        """Unknowns of each problem's finest level, in the batch's order."""
         return [(p.degree * 2 ** p.level - 1) ** p.dim for p in self.params]
 
     def close(self):
@@ -363,14 +364,17 @@ class Batch:
         self.close()
 
     def set_tile(self, degree, patches_per_block):
+        """bh_batch_set_tile: patches per block of the fused MVS launch of one degree."""
         _check(load().bh_batch_set_tile(self._h, degree, patches_per_block))
 
     def vcycle_time(self, reps=5):
+        """bh_batch_vcycle_time: device time (ms) of one replay of the batch's V-cycle graph."""
         ms = ctypes.c_double()
         _check(load().bh_batch_vcycle_time(self._h, reps, ctypes.byref(ms)))
         return ms.value
 
     def launches(self):
+        """bh_batch_stats: kernel and graph launches the batch has issued so far."""
         n = ctypes.c_longlong()
         _check(load().bh_batch_stats(self._h, ctypes.byref(n)))
         return n.value
@@ -396,6 +400,8 @@ class Batch:
         return list(it), list(rr)
 
     def solve(self, bs, xs, rtol=1e-8, maxit=50, raise_on_noconv=True):
+        """bh_batch_solve on device tensors; returns per-problem iterations and
+        true relative residuals."""
         P = len(self.params)
         sizes = self.sizes()
         bp = (ctypes.c_void_p * P)(*[_dev(b, n, "b").value for b, n in zip(bs, sizes)])
@@ -442,6 +448,8 @@ class Server:
         return t.value
 
     def wait(self, ticket, timeout=-1.0):
+        """bh_server_wait: the request's status, iterations, relres and latencies
+        (timeout in seconds, < 0: no limit)."""
         r = ServerResult()
         _check(load().bh_server_wait(self._h, ticket, timeout, ctypes.byref(r)))
         self._keep.pop(ticket, None)
@@ -449,6 +457,8 @@ class Server:
                 "latency_s": r.latency_s, "service_s": r.service_s}
 
     def stats(self):
+        """bh_server_stats as a dict: queue, slot and memory counters (admitted,
+        completed, created, evictions, reserved and budget bytes, busy time)."""
         import json
         buf = ctypes.create_string_buffer(4096)
         _check(load().bh_server_stats(self._h, buf, len(buf)))

@@ -25,6 +25,7 @@ SWEEP_3D = [(3, 2, 128), (3, 3, 128), (3, 4, 64), (3, 5, 64), (3, 6, 64), (3, 7,
 
 
 def level_of(N):
+    """Level l of a mesh with N = 2^l cells per direction."""
     L = int(N).bit_length() - 1
     if 2 ** L != N or L < 1:
         raise ValueError("N must be a power of two >= 2")
