@@ -2,20 +2,28 @@
 
 One step = one pass of the whole hot path over the workload: the six
 problems of the 2D sweep (Q2-Q4 on 512^2 cells, Q5-Q7 on 256^2 cells), each
-solved by FP64 MG-GMRES to a 1e-8 relative reduction (colored MVS, one pre-
-and one post-smoothing step, fast-diagonalization local solvers, left
-preconditioning: the protocol of Sec. 5.1), which runs apply_A, the residual,
-the patch gather / solve / scatter, the transfers, the V-cycle and GMRES.  The
-six solves run as one batch (bh_batch_solve: each level operation one launch
-over all problems, the patch work of a color one launch per degree as parallel
-graph branches, the lockstep V-cycle replayed as a CUDA graph, tiles tuned on
-the batch itself); every problem takes the iterations and arithmetic of its
-own solve.
+solved by FP64 MG-GMRES to a true relative residual ||b - A x|| / ||b|| of
+1e-8 (colored MVS, one pre- and one post-smoothing step, fast-diagonalization
+local solvers, right preconditioning in the flexible form, restart 50; Sec.
+5.1), which runs apply_A, the residual, the patch gather / solve / scatter,
+the transfers, the V-cycle and GMRES.  The six solves run as one batch
+(bh_batch_solve: each level operation one launch over all problems, the patch
+work of a color one launch per degree as parallel graph branches, the
+lockstep V-cycle replayed as a CUDA graph, tiles tuned on the batch itself);
+every problem takes the iterations and arithmetic of its own solve.
+
+Right-hand side: b = A x* with x* i.i.d. uniform[-1, 1] (seed k), so that the
+FP64 rounding floor of the true residual, eps ||A|| ||x|| / ||b||, is O(eps)
+and a 1e-8 true residual is reachable at every degree; for b itself i.i.d.
+uniform that floor is 1e-8 .. 3e-7 at these sizes (reported per degree in the
+breakdown).
 
 value = sum of the paper's DoF counts (kN+1)^2 solved / device time (CUDA
 events), the solve inputs resident in HBM; L2 is flushed (256 MiB write)
 before every timed step.  e2e = the same through bh_batch_solve_host with
-pinned host buffers (copies inside the timed region).
+pinned host buffers (copies inside the timed region).  The FP32 V-cycle with
+FP64 defects (the mixed form, Sec. 5.2) is timed on the same problems and
+reported beside it.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 run one process per GPU (torchrun); the solves are independent
@@ -41,6 +49,19 @@ import workload  # noqa: E402
 METRIC = "DoF/s: C0IP apply, patch smoother, MG-GMRES solve to 1e-8; serve p50/p99 latency"
 UNIT = "DoF/s"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 2 DFMA / clk / SM at 2070 MHz
+
+
+def _measured_hbm_gbs():
+    """The measured HBM copy bandwidth of this machine's GPUs (driver-written
+    peaks file), else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+HBM_GBS = _measured_hbm_gbs()
 # The paper's solver throughput for the same six problems (2D, GMRES with one
 # MVS pre- and post-step, inexact local solvers, to 1e-8; one A100, FP64): the
 # data behind its solver-throughput figure (Fig. 3), DoF/s per degree.
@@ -58,12 +79,16 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12  # 128 FFMA / clk / SM
 def config_for(problems, precision="fp64"):
     return {
         "workload": "2D C0IP biharmonic sweep (paper sizes): Q2-Q4 on 512^2 and Q5-Q7 on 256^2 "
-                    "cells; MG-GMRES to 1e-8 (colored MVS 1+1, FDM local solver, left "
-                    "preconditioning, restart 50), %s; the six solves run as one batch" % precision,
+                    "cells; MG-GMRES to a true relative residual of 1e-8 (colored MVS 1+1, FDM "
+                    "local solver, right preconditioning (flexible), restart 50), %s; the six "
+                    "solves run as one batch" % precision,
         "problems": [{"d": d, "k": k, "cells": N, "dofs": workload.paper_dofs(d, k, N)}
                      for d, k, N in problems],
         "dof_count": "(kN+1)^d including boundary nodes (the paper's convention)",
-        "rhs": "i.i.d. uniform[-1,1] (PCG64, seed = k)",
+        "rhs": "b = A x*, x* i.i.d. uniform[-1,1] (PCG64, seed k): FP64 rounding floor of the "
+               "true residual O(eps); for b itself i.i.d. uniform the floor is 1e-8..3e-7 at "
+               "these sizes (breakdown: uniform_rhs_floor)",
+        "stop": "true residual ||b - A x||_2 / ||b||_2 <= 1e-8 (right preconditioning)",
         "l2": "flushed before every timed step (256 MiB write)",
     }
 
@@ -160,123 +185,193 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(budget_s=20.0):
-    """Time the CPU oracle (as it stands) on a bounded sample of the workload in
-    a child process with one BLAS thread: MG-GMRES solves of the same sweep
-    family (2D, k = 2..7, same smoother, local solver and GMRES protocol) at
-    the level N = 16 the oracle finishes in seconds."""
-    code = r"""
-import json, sys, time
-sys.path.insert(0, %r)
-import workload
-from oracle import mg, krylov
-t_tot, dofs, done = 0.0, 0, []
-for k in range(2, 8):
-    L = 4
-    H = mg.Hierarchy(2, k, L)
-    n = (k * 2 ** L - 1) ** 2
-    b = workload.rhs_uniform(n, k)
+# ---- the CPU oracle timed on the host cores (spawned worker processes, each
+# single-threaded in Python with its share of the host's BLAS threads) --------
+_ORACLE = {}
+
+
+def _oracle_problem(k, L):
+    """Oracle hierarchy and right-hand side b = A x* of the 2D problem (k, L)."""
+    from oracle import mg
+    key = (k, L)
+    if key not in _ORACLE:
+        H = mg.Hierarchy(2, k, L)
+        A = H.A[L]
+        _ORACLE[key] = (H, A @ workload.vector_uniform(A.shape[0], k))
+    return _ORACLE[key]
+
+
+def _oracle_setup(problems):
+    for k, L in problems:
+        _oracle_problem(k, L)
+
+
+def _oracle_solve(key):
+    """One oracle MG-GMRES solve (right, true residual 1e-8); (seconds, iters, relres)."""
+    from oracle import krylov
+    H, b = _oracle_problem(*key)
     t0 = time.perf_counter()
-    x, it, hist, rr = krylov.gmres(H.A[L], b, H.preconditioner, 1e-8, side="left")
-    t_tot += time.perf_counter() - t0
-    dofs += workload.paper_dofs(2, k, 2 ** L)
-    done.append(k)
-    if t_tot > %f:
-        break
-# the two kernels of the path on their own, 2D Q4: apply_A (CSR product) on
-# 64^2 cells and one multiplicative smoothing step on 16^2 cells, best of 3
-from oracle import smoothers
-def best(fn):
-    ts = []
-    for _ in range(3):
-        t0 = time.perf_counter(); fn(); ts.append(time.perf_counter() - t0)
-    return min(ts)
-Ha = mg.Hierarchy(2, 4, 6)
-xa = workload.vector_uniform(Ha.A[6].shape[0], 1)
-t_apply = best(lambda: Ha.A[6] @ xa)
-Hs = mg.Hierarchy(2, 4, 4)
-ns = Hs.A[4].shape[0]
-xs, bs = workload.vector_uniform(ns, 2), workload.rhs_uniform(ns, 3)
-t_mvs = best(lambda: smoothers.smooth("mvs", Hs.A[4], Hs.local[4], bs, xs, Hs.omega, 1))
-print(json.dumps({"t": t_tot, "dofs": dofs, "ks": done,
-                  "apply": workload.paper_dofs(2, 4, 64) / t_apply,
-                  "mvs_step": workload.paper_dofs(2, 4, 16) / t_mvs}))
-""" % (ROOT, budget_s)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         timeout=600)
-    if res.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": "failed: " + res.stderr.strip().splitlines()[-1][:200]}
-    r = json.loads(res.stdout.strip().splitlines()[-1])
-    return {"value": r["dofs"] / r["t"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "oracle MG-GMRES solves (MVS 1+1, inexact local solvers by dense LU, left "
-                      "preconditioning, 1e-8) of the 2D sweep family at N = 16 cells, k = %s; "
-                      "paper DoF count / CPU time, one thread" % r["ks"],
-            "apply_dofs_per_s": r["apply"], "mvs_step_dofs_per_s": r["mvs_step"],
-            "kernels_sample": "2D Q4: oracle apply_A (CSR product) on 64^2 cells, one oracle "
-                              "MVS step (separable local matrices by dense LU, sequential patch loop) "
-                              "on 16^2 cells, best of 3",
-            "host_cpus": os.cpu_count()}
+    _, it, _, rr = krylov.gmres(H.A[H.L], b, H.preconditioner, 1e-8)
+    return time.perf_counter() - t0, it, rr
+
+
+def _oracle_best(k, L, reps):
+    """Best of `reps` oracle solves of (k, L) (hierarchy setup not timed)."""
+    _oracle_problem(k, L)
+    runs = [_oracle_solve((k, L)) for _ in range(reps)]
+    return min(r[0] for r in runs), runs[0][1], runs[0][2]
+
+
+class _Pool:
+    """A spawn-started process pool whose workers get `threads` BLAS threads."""
+
+    VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+    def __init__(self, workers, threads, initializer=None, initargs=()):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.saved = {v: os.environ.get(v) for v in self.VARS}
+        for v in self.VARS:
+            os.environ[v] = str(threads)
+        self.ex = cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"),
+                                         initializer=initializer, initargs=initargs)
+
+    def __enter__(self):
+        return self.ex
+
+    def __exit__(self, *exc):
+        self.ex.shutdown()
+        for v, val in self.saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+
+
+def cpu_baseline(budget_s=40.0, reps=3):
+    """The CPU oracle (as it stands) on the workload's family: the six
+    problems (2D, k = 2..7, same smoother, local solver, GMRES protocol and
+    right-hand side kind) solved concurrently, one spawned process per problem
+    with cpu_count / 6 BLAS threads each, on meshes of N = 8, 16, 32, ... cells
+    while the time budget lasts (best of `reps` per size); the largest common
+    size reached is reported, the benchmark's own sizes (512^2 / 256^2) as not
+    run when they do not fit."""
+    ncpu = os.cpu_count() or 1
+    threads = max(1, ncpu // 6)
+    ks = list(range(2, 8))
+    sizes, t_start = [], time.perf_counter()
+    with _Pool(6, threads) as ex:
+        L = 3
+        while True:
+            t0 = time.perf_counter()
+            res = list(ex.map(_oracle_best, ks, [L] * 6, [reps] * 6))
+            wall = time.perf_counter() - t0
+            N = 2 ** L
+            dofs = sum(workload.paper_dofs(2, k, N) for k in ks)
+            tmax = max(r[0] for r in res)
+            sizes.append({"cells": N, "dofs": dofs, "solve_s_max": tmax, "wall_s": wall,
+                          "value": dofs / tmax, "iters": [r[1] for r in res],
+                          "true_relres_max": max(r[2] for r in res)})
+            # the next level costs about 4.5x (4x the unknowns, the same iterations)
+            if time.perf_counter() - t_start + 4.5 * wall > budget_s or L >= 8:
+                break
+            L += 1
+    top = sizes[-1]
+    return {"value": top["value"], "unit": UNIT, "cores": 6 * threads, "kind": "oracle",
+            "sample": "oracle MG-GMRES solves (MVS 1+1, separable local matrices by dense LU, "
+                      "right preconditioning, true residual 1e-8, b = A x*) of the 2D sweep "
+                      "family k = 2..7 on %d^2 cells, the six run concurrently in six spawned "
+                      "processes with %d BLAS thread(s) each; value = their paper DoF count / "
+                      "the slowest solve, best of %d" % (top["cells"], threads, reps),
+            "sizes": sizes, "largest_cells": top["cells"],
+            "not_run": "512^2 (k = 2..4) and 256^2 (k = 5..7) cells: beyond the %.0f s budget "
+                       "(the oracle's time grows about 4.5x per level)" % budget_s,
+            "host_cpus": ncpu}
+
+
+def rough_rhs(bh, torch, params, seed, stream):
+    """b = A_L x* on the device for x* ~ U[-1, 1] (seed), by the library's apply
+    on a context of the problem's shape; returns (b, x*)."""
+    with bh.Context(params, stream) as c:
+        n = c.num_unknowns()
+        xs = torch.tensor(workload.vector_uniform(n, seed), dtype=torch.float64, device="cuda")
+        b = torch.empty_like(xs)
+        c.apply_A(params.level, xs, b)
+        torch.cuda.synchronize()
+    return b, xs
 
 
 def measure_batched(bh, torch, stream):
     """The batched form on 64 independent 2D problems (k ~ U{2..7}, levels
-    with 1e4-1e6 DoFs, seed 1234): one solve of all of them in lockstep with
-    autotuned tiles, against the same problems solved one after another."""
+    with 1e4-1e6 DoFs, seed 1234; b = A x*): one right-preconditioned solve of
+    all of them in lockstep with autotuned tiles, against the same problems
+    solved one after another."""
     from paper_2412_05082_gb300 import autotune
-    import time
     probs = workload.batch_problems(64, 1234)
     params = [bh.default_params(d, k, L) for d, k, L in probs]
-    bs = [torch.tensor(workload.rhs_uniform((k * 2 ** L - 1) ** 2, i), dtype=torch.float64,
-                       device="cuda") for i, (d, k, L) in enumerate(probs)]
+    bs = [rough_rhs(bh, torch, p, i, stream)[0] for i, p in enumerate(params)]
     xs = [torch.empty_like(b) for b in bs]
     dofs = sum(workload.paper_dofs(d, k, 2 ** L) for d, k, L in probs)
     with bh.Batch(params, stream) as batch:
         tiles = autotune.tune_batch(batch, probs)
-        batch.solve(bs, xs, 1e-8, 50)
+        batch.solve(bs, xs, 1e-8, 200)
         torch.cuda.synchronize()
         l0 = batch.launches()
         t0 = time.perf_counter()
-        its, rr = batch.solve(bs, xs, 1e-8, 50)
+        its, rr = batch.solve(bs, xs, 1e-8, 200)
         torch.cuda.synchronize()
         tb = time.perf_counter() - t0
         launches = batch.launches() - l0
     ctxs = [bh.Context(p, stream) for p in params]
     for c, b, x in zip(ctxs, bs, xs):
-        c.solve(b, x, 1e-8, 50)
+        c.solve(b, x, 1e-8, 200)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    its1 = [c.solve(b, x, 1e-8, 50)[0] for c, b, x in zip(ctxs, bs, xs)]
+    its1 = [c.solve(b, x, 1e-8, 200)[0] for c, b, x in zip(ctxs, bs, xs)]
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
     for c in ctxs:
         c.close()
     return {"workload": "64 independent 2D problems, k ~ U{2..7}, levels with 1e4-1e6 DoFs "
-                        "(seed 1234), uniform[-1,1] RHS, FP64 MG-GMRES (MVS, left) to 1e-8",
+                        "(seed 1234), b = A x* with x* uniform[-1,1], FP64 MG-GMRES (MVS, right, "
+                        "true residual) to 1e-8",
             "dofs": dofs, "value": dofs / tb, "unit": UNIT, "seconds": tb,
             "launches_per_solve": launches, "tiles_patches_per_block": tiles,
             "sequential_value": dofs / ts, "speedup_vs_sequential": ts / tb,
             "iterations_equal_to_sequential": sum(a == b for a, b in zip(its, its1)),
-            "max_iters": max(its)}
+            "max_iters": max(its), "max_true_relres": max(rr)}
 
 
-def measure_serving(bh, nreq):
+def measure_serving(bh, torch, stream, nreq):
     """The serving form on the first nreq requests of the Poisson stream
-    (rate 200/s, seed 2024; 2D and 3D, k = 2..7, 1e4-2e7 DoFs), replayed at
-    their arrival times: p50/p99 latency and throughput with 8 slots, against
-    the same requests solved one after another on one slot (FP64)."""
-    import time
+    (rate 200/s, seed 2024; 2D and 3D, k = 2..7, 1e4-2e7 DoFs; b = A x* with
+    x* uniform[-1, 1], computed on the device before the replay), replayed at
+    their arrival times: p50/p99 latency and throughput with 8 slots in the
+    mixed form (FP32 V-cycle with FP64 defects) and with 8 slots in FP64."""
     import numpy as np
     reqs = workload.serving_requests(1000, 200.0, 2024)[:nreq]
-    rhs = [workload.rhs_uniform((k * 2 ** L - 1) ** d, s) for _, d, k, L, s in reqs]
+    rhs = [None] * len(reqs)
+    shapes = {}
+    for i, (_, d, k, L, s) in enumerate(reqs):
+        shapes.setdefault((d, k, L), []).append(i)
+    for (d, k, L), idx in shapes.items():
+        with bh.Context(bh.default_params(d, k, L), stream) as c:
+            n = c.num_unknowns()
+            y = torch.empty(n, dtype=torch.float64, device="cuda")
+            for i in idx:
+                xs = torch.tensor(workload.vector_uniform(n, reqs[i][4]), dtype=torch.float64,
+                                  device="cuda")
+                c.apply_A(L, xs, y)
+                rhs[i] = y.cpu().numpy()
+            del y
+        torch.cuda.empty_cache()
     dofs = sum(workload.paper_dofs(d, k, 2 ** L) for _, d, k, L, _ in reqs)
     out = {"workload": "first %d requests of the Poisson stream (200 req/s, seed 2024), 2D and "
-                       "3D, k = 2..7, 1e4-2e7 DoFs, uniform[-1,1] RHS, to 1e-8 (true residual)"
-                       % nreq, "dofs": dofs}
-    for slots, mixed in ((8, 7), (1, 0)):
+                       "3D, k = 2..7, 1e4-2e7 DoFs, b = A x* with x* uniform[-1,1], right GMRES "
+                       "to a true residual of 1e-8" % nreq, "dofs": dofs, "requests": nreq}
+    for name, mixed in (("served_mixed", 7), ("served_fp64", 0)):
         xs = [np.zeros_like(b) for b in rhs]
-        with bh.Server(slots=slots, mixed_max_degree=mixed) as srv:
+        with bh.Server(slots=8, mixed_max_degree=mixed) as srv:
             start = time.perf_counter()
             tickets = []
             for (ta, d, k, L, _), b, x in zip(reqs, rhs, xs):
@@ -287,22 +382,25 @@ def measure_serving(bh, nreq):
             wall = time.perf_counter() - start
             st = srv.stats()
         lat = np.array([r["latency_s"] for r in res])
-        key = "served" if slots > 1 else "plain_fp64_one_slot"
-        out[key] = {"slots": slots, "precision": "FP32 V-cycle with FP64 defects" if mixed
-                    else "FP64", "value": dofs / wall, "unit": UNIT, "wall_s": wall,
-                    "p50_latency_s": float(np.percentile(lat, 50)),
-                    "p99_latency_s": float(np.percentile(lat, 99)),
-                    "failed": int(sum(r["status"] != 0 for r in res)),
-                    "max_relres": float(max(r["relres"] for r in res)),
-                    "hierarchies_created": st["created"], "evictions": st["evictions"]}
+        svc = np.array([r["service_s"] for r in res])
+        out[name] = {"slots": 8, "precision": "FP32 V-cycle with FP64 defects" if mixed
+                     else "FP64", "value": dofs / wall, "unit": UNIT, "wall_s": wall,
+                     "p50_latency_s": float(np.percentile(lat, 50)),
+                     "p99_latency_s": float(np.percentile(lat, 99)),
+                     "p50_service_s": float(np.percentile(svc, 50)),
+                     "p99_service_s": float(np.percentile(svc, 99)),
+                     "failed": int(sum(r["status"] != 0 for r in res)),
+                     "max_relres": float(max(r["relres"] for r in res)),
+                     "hierarchies_created": st["created"], "evictions": st["evictions"]}
     return out
 
 
 def breakdown_3d(bh, torch, dev, stream, time_op):
     """The 3D sweep (Q2, Q3 on 128^3, Q4-Q7 on 64^3 cells): apply, one colored
-    MVS step (inexact, and exact local solvers), the FP64 MG-GMRES solve, the FP32
-    V-cycle inside flexible GMRES for k <= 4 and the FP32 V-cycle with FP64
-    defects for every k."""
+    MVS step (inexact, and exact local solvers), and right-preconditioned
+    MG-GMRES to a true residual of 1e-8 on b = A x*: FP64, the FP32 V-cycle of
+    Sec. 5.2 (k <= 4) and the FP32 V-cycle with FP64 defects (every k), with
+    the relative error of each solution against x*."""
     out = {}
     for d, k, N in workload.SWEEP_3D:
         L = workload.level_of(N)
@@ -310,38 +408,35 @@ def breakdown_3d(bh, torch, dev, stream, time_op):
         row = {"dofs": dofs}
         with bh.Context(bh.default_params(d, k, L), stream) as ctx:
             n = ctx.num_unknowns()
-            b = torch.tensor(workload.rhs_uniform(n, k), dtype=torch.float64, device=dev)
+            xstar = torch.tensor(workload.vector_uniform(n, k), dtype=torch.float64, device=dev)
+            b = torch.empty_like(xstar)
+            ctx.apply_A(L, xstar, b)
             x = torch.zeros_like(b)
-            y = torch.empty_like(b)
-            row["apply"] = dofs / time_op(lambda: ctx.apply_A(L, b, y), 5)
+            row["apply"] = dofs / time_op(lambda: ctx.apply_A(L, xstar, x), 5)
+            x.zero_()
             row["mvs_step"] = dofs / time_op(lambda: ctx.smooth(L, x, b, 1), 3)
-            it = ctx.solve(b, x, 1e-8, 100)
-            row["solve_fp64"] = dofs / time_op(lambda: ctx.solve(b, x, 1e-8, 100), 1)
-            row["solve_iters"], row["true_relres"] = it[0], it[1]
-        with bh.Context(bh.default_params(d, k, L, local_solver=bh.EXACT), stream) as c2:
-            row["mvs_exact_step"] = dofs / time_op(lambda: c2.smooth(L, x, b, 1), 2)
-        # flexible GMRES on the true residual: the FP64 V-cycle (one timed
-        # solve, the first on its context), the FP32 V-cycle of Sec. 5.2 (Q2-Q4)
-        # and the FP32 V-cycle with FP64 defects (every degree)
-        with bh.Context(bh.default_params(d, k, L, gmres_side=bh.RIGHT), stream) as c2:
+            # one timed solve (the first on this context) to save time at 9e7 unknowns
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            itr = c2.solve(b, x, 1e-8, 100, raise_on_noconv=False)
+            itr = ctx.solve(b, x, 1e-8, 100, raise_on_noconv=False)
             e1.record(stream)
             torch.cuda.synchronize()
             row["solve_fp64_right"] = dofs / (e0.elapsed_time(e1) / 1e3)
             row["fp64_right_iters"], row["fp64_right_relres"] = itr[0], itr[1]
+            row["fp64_right_err_vs_xstar"] = float((x - xstar).abs().max() / xstar.abs().max())
+        with bh.Context(bh.default_params(d, k, L, local_solver=bh.EXACT), stream) as c2:
+            row["mvs_exact_step"] = dofs / time_op(lambda: c2.smooth(L, x, b, 1), 2)
         for prec, name, kmax in ((bh.MIXED_FP32, "mixed_right", 4),
                                  (bh.MIXED_FP32_R64, "mixed_r64_right", 7)):
             if k > kmax:
                 continue
-            with bh.Context(bh.default_params(d, k, L, precision=prec,
-                                              gmres_side=bh.RIGHT), stream) as c2:
+            with bh.Context(bh.default_params(d, k, L, precision=prec), stream) as c2:
                 itm = c2.solve(b, x, 1e-8, 100, raise_on_noconv=False)
                 row["solve_" + name] = dofs / time_op(
                     lambda: c2.solve(b, x, 1e-8, 100, raise_on_noconv=False), 1)
                 row[name + "_iters"], row[name + "_relres"] = itm[0], itm[1]
-        del b, x, y
+                row[name + "_err_vs_xstar"] = float((x - xstar).abs().max() / xstar.abs().max())
+        del b, x, xstar
         torch.cuda.empty_cache()
         out["k%d" % k] = row
     return out
@@ -416,7 +511,8 @@ def run_tables(args):
             skipped.append([name, k, L])
             continue
         p = bh.default_params(d, k, L, pre_steps=steps, post_steps=steps,
-                              local_solver=bh.EXACT if ls == "exact" else bh.FDM)
+                              local_solver=bh.EXACT if ls == "exact" else bh.FDM,
+                              gmres_side=bh.LEFT)
         if smoother == "avs":
             p.smoother, p.krylov = bh.AVS_ATOMIC, bh.CG
         with bh.Context(p, stream) as c:
@@ -442,38 +538,50 @@ def run_tables(args):
     return 0
 
 
+REFERENCE_CELLS = 16
+
+
 def run_reference(args):
-    """The reference arm: the CPU oracle timed as it stands, each step a bounded
-    sample of the workload (2D, k = 2..7, N = 8: one MG-GMRES solve each)."""
+    """The reference arm: the CPU oracle timed as it stands on the host cores.
+    Each step is a bounded sample of the workload: the six problems of the
+    sweep family (2D, k = 2..7, b = A x*, right MG-GMRES to a true residual of
+    1e-8) on 16^2 cells, solved concurrently by six spawned processes that
+    hold the hierarchies (set up once, not timed)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from oracle import krylov, mg
-    problems = [(2, k, 8) for k in range(2, 8)]
-    hier = {k: mg.Hierarchy(2, k, 3) for _, k, _ in problems}
-    rhs = {k: workload.rhs_uniform((k * 8 - 1) ** 2, k) for _, k, _ in problems}
-
-    def step():
-        for _, k, _ in problems:
-            H = hier[k]
-            krylov.gmres(H.A[3], rhs[k], H.preconditioner, 1e-8, side="left")
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
+    L = workload.level_of(REFERENCE_CELLS)
+    keys = [(k, L) for k in range(2, 8)]
+    ncpu = os.cpu_count() or 1
+    threads = max(1, ncpu // 6)
+    with _Pool(6, threads, _oracle_setup, (keys,)) as ex:
+        list(ex.map(_oracle_solve, keys))  # every worker builds its hierarchies
+        for _ in range(args.warmup):
+            list(ex.map(_oracle_solve, keys))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            res = list(ex.map(_oracle_solve, keys))
+        dt = time.perf_counter() - t0
+    problems = [(2, k, REFERENCE_CELLS) for k, _ in keys]
     dofs = sum(workload.paper_dofs(*p) for p in problems) * args.steps
     value = dofs / dt
-    sample = ("oracle MG-GMRES solves of the 2D sweep family at N = 8 cells, k = 2..7, per step "
-              "(paper DoF count / CPU time, one thread)")
+    sample = ("oracle MG-GMRES solves (right, true residual 1e-8, b = A x*) of the 2D sweep "
+              "family k = 2..7 on %d^2 cells per step, the six run concurrently in six spawned "
+              "processes with %d BLAS thread(s) each; paper DoF count / wall time"
+              % (REFERENCE_CELLS, threads))
+    cfg = config_for(problems)
+    cfg["workload"] = ("2D C0IP biharmonic sweep family at a size the CPU oracle finishes per "
+                       "step: Q2-Q7 on %d^2 cells (the GPU arm runs Q2-Q4 on 512^2 and Q5-Q7 on "
+                       "256^2); MG-GMRES to a true relative residual of 1e-8 (colored MVS 1+1, "
+                       "separable local solver, right preconditioning, restart 50), FP64"
+                       % REFERENCE_CELLS)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": config_for(workload.SWEEP_2D),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "impl": "reference", "config": cfg,
+            "iterations": {str(k): it for (k, _), (_, it, _) in zip(keys, res)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 6 * threads, "kind": "oracle",
+                             "sample": sample, "host_cpus": ncpu},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -489,8 +597,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and serving measurements")
-    ap.add_argument("--serve-requests", type=int, default=48,
+    ap.add_argument("--serve-requests", type=int, default=500,
                     help="requests of the Poisson stream replayed by the serving measurement")
+    ap.add_argument("--cpu-budget-s", type=float, default=40.0,
+                    help="time budget of the CPU oracle baseline")
     ap.add_argument("--tables", action="store_true",
                     help="reproduce the nu_frac of the paper's Tables 1-3 instead of the benchmark")
     ap.add_argument("--tables-max-dofs-3d", type=float, default=2e7)
@@ -499,17 +609,15 @@ def main():
     if args.tables:
         return run_tables(args)
     if args.impl == "reference":
-        # the oracle needs no GPU: keep this process off the devices entirely
-        os.environ.setdefault("OMP_NUM_THREADS", "1")
-        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        # the oracle needs no GPU: this process never touches a device
         return run_reference(args)
 
-    # the CPU baseline runs in a child process started before any CUDA call
+    # the CPU baseline's worker processes are spawned before any CUDA call
     cpu = None
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(args.cpu_budget_s)
 
     import torch
     import paper_2412_05082_gb300 as bh
@@ -523,31 +631,36 @@ def main():
     stream = torch.cuda.current_stream()
 
     problems = workload.SWEEP_2D
+    levels = [workload.level_of(N) for _, _, N in problems]
     from paper_2412_05082_gb300 import autotune
-    ctxs, rhs, xs, hostb, hostx = [], [], [], [], []
-    for d, k, N in problems:
-        L = workload.level_of(N)
+    # inputs: x* (seeded) and b = A x* by the library's apply, resident in HBM
+    ctxs, rhs, xstar, xs, hostb, hostx = [], [], [], [], [], []
+    for (d, k, N), L in zip(problems, levels):
         ctx = bh.Context(bh.default_params(d, k, L), stream)
         n = ctx.num_unknowns()
-        b = workload.rhs_uniform(n, k)
+        xt = torch.tensor(workload.vector_uniform(n, k), dtype=torch.float64, device=dev)
+        b = torch.empty_like(xt)
+        ctx.apply_A(L, xt, b)
         ctxs.append(ctx)
-        rhs.append(torch.tensor(b, dtype=torch.float64, device=dev))
+        xstar.append(xt)
+        rhs.append(b)
         xs.append(torch.empty(n, dtype=torch.float64, device=dev))
-        hostb.append(torch.tensor(b, dtype=torch.float64).pin_memory())
+        hostb.append(b.cpu().pin_memory())
         hostx.append(torch.empty(n, dtype=torch.float64).pin_memory())
-    batch = bh.Batch([bh.default_params(d, k, workload.level_of(N)) for d, k, N in problems],
-                     stream)
-    tiles = autotune.tune_batch(batch, [(d, k, workload.level_of(N)) for d, k, N in problems])
+    torch.cuda.synchronize()
+    plist = [(d, k, L) for (d, k, _), L in zip(problems, levels)]
+    batch = bh.Batch([bh.default_params(d, k, L) for d, k, L in plist], stream)
+    tiles = autotune.tune_batch(batch, plist)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     iters = {}
 
     def step():
-        its, rrs = batch.solve(rhs, xs, 1e-8, 50)
+        its, rrs = batch.solve(rhs, xs, 1e-8, 200)
         for (d, k, N), it, rr in zip(problems, its, rrs):
             iters[k] = (it, rr)
 
     def step_host():
-        batch.solve_host(hostb, hostx, 1e-8, 50)
+        batch.solve_host(hostb, hostx, 1e-8, 200)
 
     def timed(fn, steps):
         ts = []
@@ -575,6 +688,8 @@ def main():
         dist.barrier()
     dofs_step = sum(workload.paper_dofs(*p) for p in problems)
     value = dofs_step * args.steps * world / t_total
+    err = {k: float((x - xt).abs().max() / xt.abs().max())
+           for (_, k, _), x, xt in zip(problems, xs, xstar)}
 
     # end to end through the C ABI with host buffers (copies inside the region)
     step_host()
@@ -582,22 +697,49 @@ def main():
     t_e2e = max_over_ranks(sum(te), dist, dev)
     bytes_h2d = sum(8 * c.num_unknowns() for c in ctxs)
 
+    # the mixed form on the same problems: FP32 V-cycle with FP64 defects
+    # (BH_MIXED_FP32_R64) inside the same flexible FP64 GMRES, same stop
+    mixed = {}
+    with bh.Batch([bh.default_params(d, k, L, precision=bh.MIXED_FP32_R64) for d, k, L in plist],
+                  stream) as mb:
+        mtiles = autotune.tune_batch(mb, plist)
+        xm = [torch.empty_like(x) for x in xs]
+        for _ in range(2):
+            its_m, rr_m = mb.solve(rhs, xm, 1e-8, 200)
+        tm = timed(lambda: mb.solve(rhs, xm, 1e-8, 200), min(args.steps, 5))
+        mixed = {"value": dofs_step * len(tm) * world / max_over_ranks(sum(tm), dist, dev),
+                 "unit": UNIT, "ms_per_step": statistics.mean(tm) * 1e3,
+                 "precision": "FP32 V-cycle with FP64 defects (BH_MIXED_FP32_R64) in flexible "
+                              "FP64 GMRES, same true-residual stop",
+                 "iterations": {str(k): {"iters": it, "true_relres": rr,
+                                         "err_vs_xstar": float((x - xt).abs().max() /
+                                                               xt.abs().max())}
+                                for (_, k, _), it, rr, x, xt in zip(problems, its_m, rr_m, xm,
+                                                                     xstar)},
+                 "tiles_patches_per_block": mtiles}
+        mixed["speedup_vs_fp64"] = mixed["value"] / value
+        del xm
+
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / paper_rate(problems),
         "vs_baseline_basis": "against the paper's A100 solver throughput for the same six "
-                             "problems (Fig. 3 data; all DoFs / sum of solve times = %.3g DoF/s); "
-                             "another machine: context, not the target" % paper_rate(problems),
+                             "problems (Fig. 3 data; all DoFs / sum of solve times = %.3g DoF/s; "
+                             "the paper stops on its own Krylov residual); another machine: "
+                             "context, not the target" % paper_rate(problems),
         "dtype": "f64",
         "data": "synthetic", "config": config_for(problems),
         "e2e": {"value": dofs_step * args.steps * world / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": bytes_h2d, "d2h_bytes_per_step": bytes_h2d},
         "gpu_launches": launches,
         "clocks": clk.summary(),
-        "iterations": {str(k): {"iters": it, "true_relres": rr} for k, (it, rr) in iters.items()},
+        "iterations": {str(k): {"iters": it, "true_relres": rr, "err_vs_xstar": err[k]}
+                       for k, (it, rr) in iters.items()},
+        "all_true_relres_le_1e-8": all(rr <= 1.0001e-8 for _, rr in iters.values()),
         "tiles_patches_per_block": tiles,
+        "mixed": mixed,
     }
 
     # dominant kernel: the fused colored-MVS kernel (8 launches per smoothing step)
@@ -617,13 +759,14 @@ def main():
     roof_k = 4
     i4 = [p[1] for p in problems].index(roof_k)
     d, k, N = problems[i4]
-    L = workload.level_of(N)
+    L = levels[i4]
     ctx = ctxs[i4]
     xr = torch.zeros_like(xs[i4])
     t_step = time_op(lambda: ctx.smooth(L, xr, rhs[i4], 1), 10)
     patches = (N - 1) ** 2
     flops_launch = 2 * mvs2_fma_per_patch(k) * patches / 8   # one launch = one color
     achieved = flops_launch / (t_step / 8) / 1e12
+    probe = bh.fp64_fma_rate(stream)
     result["roofline"] = {
         "kernel": "mvs2_color_kernel (fused colored MVS: local residual + FDM + update), "
                   "2D Q4 512^2, one launch per color",
@@ -632,21 +775,27 @@ def main():
         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in this
         # configuration, from one ncu capture of the unchanged kernel
         "traffic": 63.57e6, "traffic_unit": "bytes per launch",
-        "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (derived; no FP64 entry in "
-                       "the measured peaks file)",
+        "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (derived from the unit counts "
+                       "and clock; the measured-peaks file has no FP64 entry)",
+        "measured_peak_tflops": probe,
+        "measured_peak_source": "the library's FP64 FMA probe on this GPU (bh_fp64_fma_rate: "
+                                "register-only FMA chains, 4 blocks x 128 threads per SM)",
+        "frac_of_measured_peak": achieved / probe,
+        "hbm_roofline": "not the bound: FP64 machine balance = derived FP64 peak / measured HBM "
+                        "copy bandwidth = %.2f flop/B, while this kernel does about %.0f flop per "
+                        "DRAM byte; an HBM fraction of 60 %% is unreachable in FP64, the FP64 pipe "
+                        "saturates first" % (FP64_PEAK_TFLOPS * 1e12 / (HBM_GBS * 1e9),
+                                             flops_launch / 63.57e6),
         "fma_per_patch": mvs2_fma_per_patch(k), "patches_per_launch": patches / 8,
         "launch_ms": t_step / 8 * 1e3,
     }
-    # the FP64 FMA rate this GPU reaches on register-only FMA chains (library
-    # probe), and the rate of the FP64 operations the kernel executes (interior
-    # patches, 99 % of them at this size, take the folded FDM)
-    probe = bh.fp64_fma_rate(stream)
+    # the rate of the FP64 operations the kernel executes (interior patches,
+    # 99 % of them at this size, take the folded FDM) and the FP64 MMA probe
     executed = 2 * mvs2_fp64_ops_interior(k) * patches / 8 / (t_step / 8) / 1e12
     result["roofline"].update({
-        "fp64_fma_probe_tflops": probe, "frac_of_probe": achieved / probe,
         "fp64_tensor_mma_probe_tflops": bh.fp64_mma_rate(stream),
         "executed_ops_per_interior_patch": mvs2_fp64_ops_interior(k),
-        "executed_tflops": executed, "executed_frac_of_probe": executed / probe})
+        "executed_tflops": executed, "executed_frac_of_measured_peak": executed / probe})
     n4 = ctx.num_unknowns()
     r4 = torch.empty(n4, dtype=torch.float64, device=dev)
     t_res = time_op(lambda: ctx.residual(L, xs[i4], rhs[i4], r4), 20)
@@ -658,13 +807,11 @@ def main():
 
     if not args.no_breakdown:
         bd = {}
-        for (d, k, N), ctx, b, x in zip(problems, ctxs, rhs, xs):
-            L = workload.level_of(N)
+        for (d, k, N), L, ctx, b, x, xt in zip(problems, levels, ctxs, rhs, xs, xstar):
             dofs = workload.paper_dofs(d, k, N)
             n = ctx.num_unknowns()
             y = torch.empty(n, dtype=torch.float64, device=dev)
-            row = {"dofs": dofs, "solve_iters": iters[k][0]}
-            row["true_relres"] = iters[k][1]
+            row = {"dofs": dofs, "solve_iters": iters[k][0], "true_relres": iters[k][1]}
             row["apply"] = dofs / time_op(lambda: ctx.apply_A(L, b, y))
             for sm, name in ((bh.AVS_ATOMIC, "avs_atomic"), (bh.AVS_COLORED, "avs_colored"),
                              (bh.MVS_COLORED, "mvs")):
@@ -675,43 +822,45 @@ def main():
                 with bh.Context(bh.default_params(d, k, L, smoother=sm,
                                                   local_solver=bh.EXACT), stream) as c2:
                     row[name + "_step"] = dofs / time_op(lambda: c2.smooth(L, y, b, 1), 5)
+            # the headline protocol on one context (right, true residual, b = A x*)
             row["solve_fp64_single"] = dofs / time_op(lambda: ctx.solve(b, x, 1e-8, 200), 3)
-            # flexible right-preconditioned GMRES on the true residual: FP64 and
-            # the FP32 V-cycle of Sec. 5.2 (shown there for Q2-Q4) side by side
-            with bh.Context(bh.default_params(d, k, L, gmres_side=bh.RIGHT), stream) as c2:
-                itr = c2.solve(b, x, 1e-8, 200, raise_on_noconv=False)
-                row["solve_fp64_right"] = dofs / time_op(
-                    lambda: c2.solve(b, x, 1e-8, 200, raise_on_noconv=False), 3)
-                row["fp64_right_iters"], row["fp64_right_relres"] = itr[0], itr[1]
-                x_right = x.clone()
             # the FP32 V-cycle (Sec. 5.2, Q2-Q4) and the FP32 V-cycle with FP64
-            # defects (every degree), both in flexible GMRES
+            # defects (every degree), both in flexible GMRES, on one context
             for prec, name, kmax in ((bh.MIXED_FP32, "mixed_right", 4),
                                      (bh.MIXED_FP32_R64, "mixed_r64_right", 7)):
                 if k > kmax:
                     continue
-                with bh.Context(bh.default_params(d, k, L, precision=prec,
-                                                  gmres_side=bh.RIGHT), stream) as c2:
-                    itm = c2.solve(b, x, 1e-8, 200, raise_on_noconv=False)
-                    # relative difference of the solution from the FP64 V-cycle's
-                    row[name + "_vs_fp64"] = float((x - x_right).abs().max() /
-                                                   x_right.abs().max())
+                with bh.Context(bh.default_params(d, k, L, precision=prec), stream) as c2:
+                    itm = c2.solve(b, y, 1e-8, 200, raise_on_noconv=False)
+                    row[name + "_err_vs_xstar"] = float((y - xt).abs().max() / xt.abs().max())
                     row["solve_" + name] = dofs / time_op(
-                        lambda: c2.solve(b, x, 1e-8, 200, raise_on_noconv=False), 3)
+                        lambda: c2.solve(b, y, 1e-8, 200, raise_on_noconv=False), 3)
                     row[name + "_iters"], row[name + "_relres"] = itm[0], itm[1]
+            # b itself i.i.d. uniform: the FP64 rounding floor of the true
+            # residual (right GMRES stops on its Givens estimate), and the
+            # paper's left protocol (preconditioned residual) on that b
+            bu = torch.tensor(workload.rhs_uniform(n, k), dtype=torch.float64, device=dev)
+            itu = ctx.solve(bu, y, 1e-8, 200, raise_on_noconv=False)
+            row["uniform_rhs_floor"] = {"iters": itu[0], "true_relres": itu[1]}
+            with bh.Context(bh.default_params(d, k, L, gmres_side=bh.LEFT), stream) as c2:
+                itl = c2.solve(bu, y, 1e-8, 200, raise_on_noconv=False)
+                row["solve_fp64_left_uniform"] = dofs / time_op(
+                    lambda: c2.solve(bu, y, 1e-8, 200, raise_on_noconv=False), 2)
+                row["left_uniform_iters"], row["left_uniform_true_relres"] = itl[0], itl[1]
             # the additive smoother's protocol: two pre- and post-steps, CG
             with bh.Context(bh.default_params(d, k, L, smoother=bh.AVS_ATOMIC, pre_steps=2,
                                               post_steps=2, krylov=bh.CG), stream) as c2:
-                itc = c2.solve(b, x, 1e-8, 300, raise_on_noconv=False)
+                itc = c2.solve(b, y, 1e-8, 300, raise_on_noconv=False)
                 row["solve_avs2_cg"] = dofs / time_op(
-                    lambda: c2.solve(b, x, 1e-8, 300, raise_on_noconv=False), 2)
+                    lambda: c2.solve(b, y, 1e-8, 300, raise_on_noconv=False), 2)
                 row["avs2_cg_iters"] = itc[0]
+            del y, bu
             bd["k%d" % k] = row
         result["breakdown_dofs_per_s"] = bd
         result["breakdown3d_dofs_per_s"] = breakdown_3d(bh, torch, dev, stream, time_op)
     if not args.no_forms:
         result["batched"] = measure_batched(bh, torch, stream)
-        result["serving"] = measure_serving(bh, args.serve_requests)
+        result["serving"] = measure_serving(bh, torch, stream, args.serve_requests)
     if cpu is not None:
         result["cpu_baseline"] = cpu
     if rank == 0:

@@ -59,11 +59,13 @@ enum { BH_FDM = 0, BH_EXACT = 1 };
  * the condition number of A_l, which stalls the plain FP32 V-cycle on fine
  * meshes at high degree (2D k >= 5 on 256^2 cells).  Not in the paper. */
 enum { BH_FP64 = 0, BH_MIXED_FP32 = 1, BH_MIXED_FP32_R64 = 2 };
-/* GMRES preconditioning side (Sec. 5.1 leaves it open).  BH_LEFT stops on the
- * reduction of the preconditioned residual M^-1 (b - A x), the convention whose
- * iteration counts match the paper's tables; BH_RIGHT stops on the true
- * residual b - A x, whose FP64 rounding floor eps ||A|| ||x|| / ||b|| exceeds
- * 1e-8 on the paper's finest meshes. */
+/* GMRES preconditioning side (Sec. 5.1 leaves it open).  BH_RIGHT (the
+ * default) keeps the preconditioned directions (flexible form) and stops on the
+ * true residual b - A x; its FP64 rounding floor eps ||A|| ||x|| / ||b|| is
+ * O(eps) when b = A x* for a rough x*, but exceeds 1e-8 for an i.i.d. random b
+ * on the paper's finest meshes (1e-8 .. 3e-7).  BH_LEFT stops on the reduction
+ * of the preconditioned residual M^-1 (b - A x), the convention whose iteration
+ * counts match the paper's tables. */
 enum { BH_RIGHT = 0, BH_LEFT = 1 };
 /* Krylov method of bh_solve (Sec. 5.1 pairs conjugate gradients with the
  * additive smoother, whose V-cycle is symmetric, and GMRES with the
@@ -89,13 +91,13 @@ typedef struct {
   int precision;     /* BH_FP64 | BH_MIXED_FP32 | BH_MIXED_FP32_R64 (mixed forms need
                         gmres_side = BH_RIGHT, or krylov = BH_CG) */
   int gmres_restart; /* restart length m (default 50) */
-  int gmres_side;    /* BH_LEFT (default) | BH_RIGHT */
+  int gmres_side;    /* BH_RIGHT (default) | BH_LEFT */
   int coarse;        /* BH_COARSE_EXACT (default) | BH_COARSE_SMOOTH */
   int krylov;        /* BH_GMRES (default) | BH_CG (additive smoothers only) */
 } bh_params;
 
 /* Fill *out with the defaults above for (dim, degree, level): MVS, FDM,
- * one pre- and one post-smoothing step, FP64, GMRES(50), left side.
+ * one pre- and one post-smoothing step, FP64, GMRES(50), right side.
  * Host only.  BH_EINVAL for d not in {2,3}, k not in 2..7 or level < 1. */
 bh_status bh_default_params(int dim, int degree, int level, bh_params* out);
 
@@ -245,30 +247,62 @@ bh_status bh_setup_fdm(int degree, double gamma, int type, double* S, double* la
  * all problems (a work list of (problem, range) entries dispatched on the
  * degree); the patch work of one color is one launch per degree present,
  * forked into parallel branches so that each uses its own tile shape; the
- * lockstep V-cycle is captured once as a CUDA graph; GMRES (left preconditioning) runs in lockstep with one host
- * synchronization per iteration for the whole batch.  Each problem follows
- * the arithmetic of its own context, so its result matches bh_solve on the
- * same parameters up to rounding order. */
+ * lockstep V-cycle (x_L = MG_L(0, b_L) for every problem, Algorithm 1) is
+ * captured once as a CUDA graph.  The V-cycle runs in FP64, or in FP32 with
+ * the defect before each restriction evaluated and restricted in FP64
+ * (BH_MIXED_FP32_R64).  GMRES(m) (Sec. 5.1) runs in lockstep with one host
+ * synchronization per iteration for the whole batch, preconditioned on the
+ * left (stopping on the preconditioned residual) or on the right in the
+ * flexible form (stopping on the true residual), with restarts.  Each problem
+ * follows the arithmetic of its own context, so its result matches bh_solve
+ * on the same parameters up to rounding order and does not depend on the
+ * other problems of the batch.
+ * Calls on one batch must not overlap.  A batch works on its own stream;
+ * every call first waits for the work already enqueued on the stream given to
+ * bh_batch_create, and work enqueued there after the call returns waits for
+ * the call's results. */
 typedef struct bh_batch bh_batch;
 
-/* count problems, params[i] each: dim 2, BH_MVS_COLORED, BH_FDM, BH_FP64,
- * BH_COARSE_EXACT, BH_LEFT, BH_GMRES (BH_EINVAL otherwise).  Allocates every hierarchy,
- * builds the work lists and captures the V-cycle graph.  Synchronous. */
+/* count problems, params[i] each: dim 2, BH_MVS_COLORED, BH_FDM,
+ * BH_COARSE_EXACT, BH_GMRES, precision BH_FP64 or BH_MIXED_FP32_R64 (the
+ * latter with BH_RIGHT); precision, gmres_side, pre_steps and post_steps the
+ * same for every problem (BH_EINVAL otherwise); the restart length is the
+ * largest gmres_restart.  Allocates every hierarchy, builds the work lists and
+ * captures the V-cycle graph.  Synchronous. */
 bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_batch** out);
 bh_status bh_batch_destroy(bh_batch* batch);
 
 /* Tile shape of the patch kernel for one degree: patches per thread block
- * (1..32, bounded by the shared-memory budget).  Rebuilds the work lists and
- * re-captures the graph.  Used by the autotuner. */
+ * (1..32, bounded by the shared-memory budget of the batch's precision).
+ * Rebuilds the work lists and re-captures the graph.  Used by the autotuner. */
 bh_status bh_batch_set_tile(bh_batch* batch, int degree, int patches_per_block);
 
 /* Mean device time (ms, CUDA events) of one batched V-cycle graph launch on
  * the current right-hand sides, over reps launches after one warm-up. */
 bh_status bh_batch_vcycle_time(bh_batch* batch, int reps, double* ms);
 
-/* Solve all problems: b_dev[i], x_dev[i] are host arrays of device pointers
- * (n_i FP64 values each).  iters[i], relres[i] (true relative residual)
- * receive each problem's result.  BH_ENOCONV if any problem missed rtol. */
+/* One batched V-cycle from zero: x_dev[i] = MG_L(0, b_dev[i]) (Algorithm 1)
+ * for every problem i, by the captured graph in the batch's precision (the
+ * preconditioner that bh_batch_solve applies).  b_dev, x_dev: host arrays of
+ * device pointers, n_i FP64 values each, not aliased.  Synchronous. */
+bh_status bh_batch_vcycle(bh_batch* batch, const double* const* b_dev, double* const* x_dev);
+
+/* Colors first_color .. end_color-1 (0 <= first <= end <= 8) of one colored
+ * multiplicative smoothing step (Sec. 3) on the finest level of every problem,
+ * in place on x_dev[i] with right-hand side b_dev[i], by the batched patch
+ * kernels of the batch's precision (for BH_MIXED_FP32_R64: x and b rounded to
+ * FP32, the FP32 kernels, the result widened to FP64).  BH_EINVAL if a
+ * problem's finest level is 1 (no smoother there).  Synchronous. */
+bh_status bh_batch_smooth_colors(bh_batch* batch, double* const* x_dev,
+                                 const double* const* b_dev, int first_color, int end_color);
+
+/* Solve all problems from x = 0: b_dev[i], x_dev[i] are host arrays of device
+ * pointers (n_i FP64 values each).  Every problem iterates until its stopping
+ * test (the Givens estimate of the minimized residual -- preconditioned for
+ * BH_LEFT, true for BH_RIGHT -- at most rtol times its initial value) holds
+ * or it has run maxit iterations, restarting every m iterations.  iters[i] and
+ * relres[i] (the true ||b - A x|| / ||b|| in FP64) receive each problem's
+ * result.  BH_ENOCONV if any problem missed rtol.  Synchronous. */
 bh_status bh_batch_solve(bh_batch* batch, const double* const* b_dev, double* const* x_dev,
                          double rtol, int maxit, int* iters, double* relres);
 

@@ -75,6 +75,8 @@ SIGNATURES = {
     "bh_batch_set_tile": (_I, [_P, _I, _I]),
     "bh_set_tile": (_I, [_P, _I]),
     "bh_batch_vcycle_time": (_I, [_P, _I, _c.POINTER(_D)]),
+    "bh_batch_vcycle": (_I, [_P, _P, _P]),
+    "bh_batch_smooth_colors": (_I, [_P, _P, _P, _I, _I]),
     "bh_batch_solve": (_I, [_P, _P, _P, _D, _I, _P, _P]),
     "bh_batch_stats": (_I, [_P, _c.POINTER(_c.c_longlong)]),
     "bh_batch_solve_host": (_I, [_P, _P, _P, _D, _I, _P, _P]),
@@ -332,7 +334,8 @@ class Context:
 class Batch:
     """Many independent 2D problems solved together (batched form): one launch
     per level operation over all problems, the lockstep V-cycle as a CUDA
-    graph, lockstep GMRES."""
+    graph (FP64, or FP32 with FP64 defects), lockstep GMRES (left, or right
+    in the flexible form) with restarts."""
 
     def __init__(self, params_list, stream=None):
         import torch
@@ -373,13 +376,34 @@ class Batch:
         _check(load().bh_batch_vcycle_time(self._h, reps, ctypes.byref(ms)))
         return ms.value
 
+    def _ptrs(self, vs, name):
+        sizes = self.sizes()
+        if len(vs) != len(sizes):
+            raise ValueError("%s: one vector per problem (%d)" % (name, len(sizes)))
+        arr = (ctypes.c_void_p * len(sizes))(*[_dev(v, n, name).value for v, n in zip(vs, sizes)])
+        return ctypes.cast(arr, ctypes.c_void_p), arr
+
+    def vcycle(self, bs, xs):
+        """bh_batch_vcycle: xs[i] = MG_L(0, bs[i]) (Algorithm 1) for every problem,
+        by the batch's captured V-cycle graph in its precision."""
+        bp, keep_b = self._ptrs(bs, "b")
+        xp, keep_x = self._ptrs(xs, "x")
+        _check(load().bh_batch_vcycle(self._h, bp, xp))
+
+    def smooth_colors(self, xs, bs, first_color, end_color):
+        """bh_batch_smooth_colors: colors first_color .. end_color-1 of one
+        colored MVS step on every problem's finest level, xs in place."""
+        xp, keep_x = self._ptrs(xs, "x")
+        bp, keep_b = self._ptrs(bs, "b")
+        _check(load().bh_batch_smooth_colors(self._h, xp, bp, first_color, end_color))
+
     def launches(self):
         """bh_batch_stats: kernel and graph launches the batch has issued so far."""
         n = ctypes.c_longlong()
         _check(load().bh_batch_stats(self._h, ctypes.byref(n)))
         return n.value
 
-    def solve_host(self, bs, xs, rtol=1e-8, maxit=50):
+    def solve_host(self, bs, xs, rtol=1e-8, maxit=200):
         """bs, xs: contiguous float64 host arrays (numpy or CPU tensors)."""
         import numpy as np
         P = len(self.params)
@@ -399,7 +423,7 @@ class Batch:
                                           ctypes.cast(rr, ctypes.c_void_p)))
         return list(it), list(rr)
 
-    def solve(self, bs, xs, rtol=1e-8, maxit=50, raise_on_noconv=True):
+    def solve(self, bs, xs, rtol=1e-8, maxit=200, raise_on_noconv=True):
         """bh_batch_solve on device tensors; returns per-problem iterations and
         true relative residuals."""
         P = len(self.params)

@@ -53,13 +53,14 @@ def save_cache(c):
     os.replace(tmp, p)
 
 
-def tune_degree(k, level=None, problems=4, reps=5, verbose=False):
-    """Best patches-per-block for degree k; returns (best, {pb: ms})."""
+def tune_degree(k, level=None, problems=4, reps=5, verbose=False, precision=0):
+    """Best patches-per-block for degree k in the V-cycle precision `precision`
+    (FP64 or the FP32 V-cycle with FP64 defects); returns (best, {pb: ms})."""
     import torch
     import paper_2412_05082_gb300 as bh
     if level is None:  # about 2e5 unknowns per problem
         level = max(2, min(9, int(round(__import__("math").log2(450.0 / k)))))
-    params = [bh.default_params(2, k, level) for _ in range(problems)]
+    params = [bh.default_params(2, k, level, precision=precision) for _ in range(problems)]
     times = {}
     with bh.Batch(params) as batch:
         for pb in CANDIDATES:
@@ -75,15 +76,16 @@ def tune_degree(k, level=None, problems=4, reps=5, verbose=False):
     return best, times
 
 
-def tiles_for(degrees, refresh=False, verbose=False):
-    """{k: patches per block} for the 2D degrees, tuned once per device."""
+def tiles_for(degrees, refresh=False, verbose=False, precision=0):
+    """{k: patches per block} for the 2D degrees, tuned once per device and
+    V-cycle precision."""
     cache = load_cache()
     arch = _arch()
     out, dirty = {}, False
     for k in sorted(set(degrees)):
-        key = "d2_k%d_%s" % (k, arch)
+        key = "d2_k%d_p%d_%s" % (k, precision, arch)
         if refresh or key not in cache:
-            best, times = tune_degree(k, verbose=verbose)
+            best, times = tune_degree(k, verbose=verbose, precision=precision)
             cache[key] = {"patches_per_block": best, "ms": times}
             dirty = True
         out[k] = int(cache[key]["patches_per_block"])
@@ -102,14 +104,16 @@ def tune_batch(batch, problems, refresh=False, reps=5, verbose=False):
     (d, k, level)); applied to the batch before returning."""
     import paper_2412_05082_gb300 as bh
     degrees = sorted({k for _, k, _ in problems})
+    precision = batch.params[0].precision
     cache = load_cache()
-    key = "batch_%s_%s" % ("-".join("%d.%d.%d" % p for p in sorted(problems)), _arch())
+    key = "batch_p%d_%s_%s" % (precision, "-".join("%d.%d.%d" % p for p in sorted(problems)),
+                               _arch())
     if not refresh and key in cache:
         tiles = {int(k): int(v) for k, v in cache[key]["tiles"].items()}
         for k, pb in tiles.items():
             batch.set_tile(k, pb)
         return tiles
-    tiles = tiles_for(degrees)
+    tiles = tiles_for(degrees, precision=precision)
     for k, pb in tiles.items():
         batch.set_tile(k, pb)
     best = batch.vcycle_time(reps)

@@ -625,7 +625,7 @@ bh_status bh_default_params(int dim, int degree, int level, bh_params* out) {
   p.omega = 0.0;
   p.precision = BH_FP64;
   p.gmres_restart = 50;
-  p.gmres_side = BH_LEFT;
+  p.gmres_side = BH_RIGHT;
   p.coarse = BH_COARSE_EXACT;
   p.krylov = BH_GMRES;
   *out = p;

@@ -5,12 +5,17 @@
 // smoother's patch work of one color is one launch per degree present (one
 // block per tile, each launch with the shared memory of its own tile shape),
 // the launches forked into parallel branches of the graph; the tile shape
-// (patches per block) of each degree comes from the autotuner.  The V-cycle runs in lockstep by depth (depth t works on
-// level L_p - t of every problem p) and is captured once as a CUDA graph;
-// GMRES (left preconditioning, the paper's protocol) runs in lockstep with a
-// per-problem activity mask, one host synchronization per iteration for all
-// problems.  Every problem follows exactly the arithmetic of its own context,
-// so a result does not depend on the other problems of the batch.
+// (patches per block) of each degree comes from the autotuner.  The V-cycle
+// runs in lockstep by depth (depth t works on level L_p - t of every problem
+// p) and is captured once as a CUDA graph that maps b_L to x_L = MG(0, b_L)
+// for every problem.  It runs in FP64, or in FP32 with the defect before each
+// restriction evaluated and restricted in FP64 (BH_MIXED_FP32_R64).  GMRES(m)
+// runs in lockstep with a per-problem activity mask and one host
+// synchronization per iteration for all problems: left preconditioning
+// (preconditioned residual, the paper's tables), or right preconditioning in
+// the flexible form (true residual b - A x, required by the FP32 V-cycle),
+// with restarts.  Every problem follows exactly the arithmetic of its own
+// context, so a result does not depend on the other problems of the batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,8 +36,6 @@ void set_last_error(const std::string& msg);  // api.cu
 using namespace bh;
 
 namespace {
-
-using T = double;
 
 bh_status berr(bh_status s, const std::string& msg) {
   set_last_error(msg);
@@ -55,10 +58,10 @@ bh_status berr(bh_status s, const std::string& msg) {
 // ---------------------------------------------------------------------------
 // device side
 // ---------------------------------------------------------------------------
-struct Meta {          // per problem, indexed by problem id
-  const int* k;        // degree
-  const void* const* tabs;  // Tables<T, K>* (device)
-  const int* active;   // 0: problem finished, skip it
+struct Meta {                 // per problem, indexed by problem id
+  const int* k;               // degree
+  const void* const* tabs;    // Tables<T, K>* (device) of the launch's value type
+  const int* active;          // 0: problem finished, skip it
 };
 
 // first index p with prefix[p + 1] > tid (prefix[0] = 0, increasing)
@@ -84,7 +87,7 @@ __device__ __forceinline__ int find_seg(const int64_t* prefix, int n, int64_t ti
     case 7: CALL(7); break; \
   }
 
-template <int KIND>
+template <typename T, int KIND>
 __global__ void __launch_bounds__(128) sweep_batch_kernel(Meta m, const SweepArgs<T>* args,
                                                           const int64_t* prefix, const int* pid,
                                                           int n) {
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(128) sweep_batch_kernel(Meta m, const SweepArg
 #undef BH_CALL
 }
 
-template <bool PROLONG>
+template <typename T, bool PROLONG>
 __global__ void __launch_bounds__(128) xfer_batch_kernel(Meta m, const XferArgs<T>* args,
                                                          const int64_t* prefix, const int* pid,
                                                          int n) {
@@ -129,9 +132,10 @@ struct Tile {
 // kernel.  Its register count is the maximum over the degrees it dispatches:
 // with the folded path up to k = 4 it stays at 64 per thread and the 2D sweep's
 // batched solve ran 1 % faster than without it; up to k = 5 or 7 it needs
-// 80-128 registers and ran 3-17 % slower (measured on GB300).
+// 80-128 registers and ran 3-17 % slower (measured on GB300, FP64).
 constexpr int kBatchInteriorMaxK = 4;
 
+template <typename T>
 __global__ void __launch_bounds__(256) mvs2_batch_kernel(Meta m, const MvsArgs<T>* args,
                                                          const int* pid, const Tile* tiles,
                                                          int ntiles) {
@@ -154,7 +158,8 @@ __global__ void __launch_bounds__(256) mvs2_batch_kernel(Meta m, const MvsArgs<T
   }
 }
 
-struct Symv {    // coarse solve x = scale A b, A dense symmetric (n x n)
+template <typename T>
+struct Symv {  // coarse solve x = scale A b, A dense symmetric FP64 (n x n)
   const double* A;
   const T* b;
   T* x;
@@ -162,10 +167,11 @@ struct Symv {    // coarse solve x = scale A b, A dense symmetric (n x n)
   double scale;
 };
 
-__global__ void coarse_batch_kernel(Meta m, const Symv* ops, const int* pid, int count) {
+template <typename T>
+__global__ void coarse_batch_kernel(Meta m, const Symv<T>* ops, const int* pid, int count) {
   const int s = blockIdx.y;
   if (s >= count || !m.active[pid[s]]) return;
-  const Symv o = ops[s];
+  const Symv<T> o = ops[s];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= o.n) return;
   double acc = 0.0;
@@ -173,6 +179,7 @@ __global__ void coarse_batch_kernel(Meta m, const Symv* ops, const int* pid, int
   o.x[i] = (T)(o.scale * acc);
 }
 
+template <typename T>
 struct Vec {  // one problem's vector operands: y + yslot * ys, x + xslot * xs, n values
   T* y;
   const T* x;
@@ -183,7 +190,8 @@ struct Vec {  // one problem's vector operands: y + yslot * ys, x + xslot * xs, 
 // zero, copy, y += c x, y = x / sqrt(c): one launch over the concatenation
 enum VecOp { kZero = 0, kCopy = 1, kAxpyDev = 2, kScaleInvSqrt = 3 };
 
-__global__ void vec_batch_kernel(Meta m, const Vec* v, const int64_t* prefix, const int* pid,
+template <typename T>
+__global__ void vec_batch_kernel(Meta m, const Vec<T>* v, const int64_t* prefix, const int* pid,
                                  int n, int op, const double* coef, int cstride, int cslot,
                                  double sign, int yslot, int xslot) {
   const int64_t total = prefix[n];
@@ -193,32 +201,58 @@ __global__ void vec_batch_kernel(Meta m, const Vec* v, const int64_t* prefix, co
     const int p = pid[s];
     if (!m.active[p]) continue;
     const int64_t i = tid - prefix[s];
-    const Vec o = v[s];
+    const Vec<T> o = v[s];
     T* y = o.y + yslot * o.ys;
     const T* x = o.x + xslot * o.xs;
     switch (op) {
       case kZero: y[i] = T(0); break;
       case kCopy: y[i] = x[i]; break;
-      case kAxpyDev: y[i] = fma(sign * coef[p * cstride + cslot], x[i], y[i]); break;
-      default: y[i] = x[i] / sqrt(coef[p * cstride + cslot]); break;
+      case kAxpyDev: y[i] = T(fma(sign * coef[p * cstride + cslot], (double)x[i], (double)y[i])); break;
+      default: y[i] = T((double)x[i] / sqrt(coef[p * cstride + cslot])); break;
     }
+  }
+}
+
+// conversion between an FP64 vector (d + slot * ds) and an FP32 one
+struct Conv {
+  double* d;
+  float* f;
+  int64_t n;
+  int64_t ds;
+};
+enum ConvDir { kD2F = 0, kF2D = 1 };
+
+__global__ void conv_batch_kernel(Meta m, const Conv* v, const int64_t* prefix, const int* pid,
+                                  int n, int dir, int slot) {
+  const int64_t total = prefix[n];
+  for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
+       tid += (int64_t)gridDim.x * blockDim.x) {
+    const int s = find_seg(prefix, n, tid);
+    if (!m.active[pid[s]]) continue;
+    const int64_t i = tid - prefix[s];
+    const Conv o = v[s];
+    double* d = o.d + slot * o.ds;
+    if (dir == kD2F)
+      o.f[i] = (float)d[i];
+    else
+      d[i] = (double)o.f[i];
   }
 }
 
 // deterministic per-problem dot products: fixed chunks, then a fixed-order sum
 constexpr int kChunk = 8192;
 
-__global__ void dot_batch_partial(Meta m, const Vec* v, const int64_t* cprefix, const int* pid,
-                                  int n, double* partials, int yslot, int xslot) {
+__global__ void dot_batch_partial(Meta m, const Vec<double>* v, const int64_t* cprefix,
+                                  const int* pid, int n, double* partials, int yslot, int xslot) {
   const int64_t c = blockIdx.x;
   if (c >= cprefix[n]) return;
   const int s = find_seg(cprefix, n, c);
   const int p = pid[s];
   double acc = 0.0;
   if (m.active[p]) {
-    const Vec o = v[s];
-    const T* y = o.y + yslot * o.ys;
-    const T* x = o.x + xslot * o.xs;
+    const Vec<double> o = v[s];
+    const double* y = o.y + yslot * o.ys;
+    const double* x = o.x + xslot * o.xs;
     const int64_t i0 = (c - cprefix[s]) * kChunk;
     const int64_t i1 = min(o.n, i0 + kChunk);
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc = fma(y[i], x[i], acc);
@@ -253,13 +287,15 @@ struct DevArray {  // a device copy of a host vector
   int n = 0;
 };
 
-struct SweepOp {       // one batched sweep launch
+template <typename T>
+struct SweepOp {  // one batched sweep launch
   DevArray<SweepArgs<T>> args;
   DevArray<int64_t> prefix;
   DevArray<int> pid;
   int64_t total = 0;
 };
 
+template <typename T>
 struct XferOp {
   DevArray<XferArgs<T>> args;
   DevArray<int64_t> prefix;
@@ -267,6 +303,7 @@ struct XferOp {
   int64_t total = 0;
 };
 
+template <typename T>
 struct MvsOp {
   DevArray<MvsArgs<T>> args;
   DevArray<int> pid;
@@ -274,35 +311,56 @@ struct MvsOp {
   size_t smem = 0;
 };
 
+template <typename T>
 struct VecOpList {
-  DevArray<Vec> v;
+  DevArray<Vec<T>> v;
   DevArray<int64_t> prefix;   // element prefix
   DevArray<int64_t> cprefix;  // chunk prefix (dots)
   DevArray<int> pid;
   int64_t total = 0, chunks = 0;
 };
 
-struct Depth {  // operations at depth t of the lockstep V-cycle
-  bool smooth = false, coarse = false;
+struct ConvOpList {
+  DevArray<Conv> v;
+  DevArray<int64_t> prefix;
+  DevArray<int> pid;
+  int64_t total = 0;
+};
+
+// the operations of the V-cycle's own value type T at one depth
+template <typename T>
+struct VDepth {
   // per color, one MVS launch per degree present at this depth (each with the
   // shared memory its own tile needs); they run as parallel graph branches
-  std::vector<MvsOp> mvs[8];
-  SweepOp res_x, res_y;
-  XferOp restr[2], prol[2];
-  VecOpList zero_coarse;  // x at level - 1
-  DevArray<Symv> symv;
+  std::vector<MvsOp<T>> mvs[8];
+  XferOp<T> prol[2];
+  VecOpList<T> zero_coarse;  // x at level - 1
+  DevArray<Symv<T>> symv;
+};
+
+struct Depth {  // operations at depth t of the lockstep V-cycle
+  bool smooth = false, coarse = false;
+  VDepth<double> v64;  // FP64 V-cycle
+  VDepth<float> v32;   // FP32 V-cycle (BH_MIXED_FP32_R64)
+  // the defect b_l - A_l x before the restriction, always in FP64: of x64
+  // against b64 (FP64), or of the FP64 copy dx64 of x32 against the FP64
+  // right-hand side (b64 on the finest level, db64 below) (R64)
+  SweepOp<double> res_x, res_y;
+  XferOp<double> restr[2];  // FP64 restriction into b64 (FP64) / db64 (R64) of level l-1
+  ConvOpList x_f2d;         // R64: dx64 = x32 on level l
+  ConvOpList b_d2f;         // R64: b32 = db64 on level l-1
   DevArray<int> symv_pid;
   int nsymv = 0, maxn_symv = 0;
 };
 
 struct SolvePlan {  // GMRES work lists built once per batch
-  std::vector<SweepOp> apply_x;  // per j: V_j -> scratch
-  SweepOp apply_y;               // scratch -> b_L
-  SweepOp resid_x, resid_y;      // x -> scratch, b - A x -> r_L (pointers refreshed per call)
-  VecOpList ww, wV, Vw, rr;      // w.w, (w, V_i), V_i <- w, r.r
-  VecOpList zero_x, copy_b, bnorm, xV;  // caller vectors (refreshed per call)
-  std::vector<Vec> h_zero_x, h_copy_b, h_bnorm, h_xV;
-  std::vector<SweepArgs<T>> h_rx, h_ry;
+  std::vector<SweepOp<double>> apply_x;  // per j: (V_j left | Z_j right) -> scratch
+  SweepOp<double> apply_y;               // scratch -> w (b64_L left | r64_L right)
+  SweepOp<double> resid_x, resid_y;      // x -> scratch, b - A x -> r64_L (caller vectors)
+  VecOpList<double> ww, wV, Vw, Vr, rr, xcopyZ, Vcopy, rcopy, x64dot;
+  VecOpList<double> zero_x, copy_b, bnorm, xV;  // caller vectors (refreshed per call)
+  std::vector<Vec<double>> h_zero_x, h_copy_b, h_bnorm, h_xV;
+  std::vector<SweepArgs<double>> h_rx, h_ry;
   std::vector<double> hd, hcoef;
 };
 
@@ -315,16 +373,19 @@ struct bh_batch {
   cudaEvent_t ev = nullptr;
   std::vector<bh_ctx*> ctx;
   std::vector<int> k, L;
-  int m = 0;  // GMRES restart = max iterations
+  int m = 0;           // GMRES restart length
+  bool mixed = false;  // FP32 V-cycle with FP64 defects
+  bool right = false;  // right (flexible) preconditioning
+  int pre = 1, post = 1;
   int tile[8] = {0};  // patches per block per degree (0 = default)
   // device meta
   int* d_k = nullptr;
-  const void** d_tabs = nullptr;
+  const void** d_tabs64 = nullptr;
+  const void** d_tabs32 = nullptr;
   int* d_active = nullptr;
   double* d_dots = nullptr;      // [P][m + 2]
-  double* d_coef = nullptr;      // [P][m]
+  double* d_coef = nullptr;      // [P][m + 2]
   double* d_partials = nullptr;
-  int64_t max_chunks = 0;
   std::vector<Depth> depth;
   std::vector<void*> allocs;
   SolvePlan* plan = nullptr;
@@ -357,10 +418,14 @@ bh_status upload(bh_batch* b, const std::vector<A>& h, DevArray<A>& d) {
   return BH_OK;
 }
 
-Meta meta(const bh_batch* b) { return Meta{b->d_k, b->d_tabs, b->d_active}; }
+template <typename T>
+Meta meta(const bh_batch* b) {
+  return Meta{b->d_k, sizeof(T) == 8 ? b->d_tabs64 : b->d_tabs32, b->d_active};
+}
 
 unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
+template <typename T>
 SweepArgs<T> sweep_args(const Level& Lv, int axis, const T* in0, const T* in1, const T* in2,
                         T* o0, T* o1, T* o2, const T* bvec, int mode) {
   SweepArgs<T> a{};
@@ -383,8 +448,9 @@ SweepArgs<T> sweep_args(const Level& Lv, int axis, const T* in0, const T* in1, c
 }
 
 // build a sweep op over (problem id, args) pairs
+template <typename T>
 bh_status make_sweep(bh_batch* b, const std::vector<std::pair<int, SweepArgs<T>>>& items,
-                     SweepOp& op) {
+                     SweepOp<T>& op) {
   std::vector<SweepArgs<T>> args;
   std::vector<int64_t> prefix{0};
   std::vector<int> pid;
@@ -400,7 +466,7 @@ bh_status make_sweep(bh_batch* b, const std::vector<std::pair<int, SweepArgs<T>>
   return BH_OK;
 }
 
-template <bool PROLONG>
+template <typename T, bool PROLONG>
 XferArgs<T> xfer_args(int axis, const LevelGeom& fine, const T* in, T* out, bool add) {
   const int K = fine.k, Nc = fine.N / 2, nc = K * Nc - 1, nf = fine.n;
   XferArgs<T> a{};
@@ -432,7 +498,9 @@ XferArgs<T> xfer_args(int axis, const LevelGeom& fine, const T* in, T* out, bool
   return a;
 }
 
-bh_status make_xfer(bh_batch* b, const std::vector<std::pair<int, XferArgs<T>>>& items, XferOp& op) {
+template <typename T>
+bh_status make_xfer(bh_batch* b, const std::vector<std::pair<int, XferArgs<T>>>& items,
+                    XferOp<T>& op) {
   std::vector<XferArgs<T>> args;
   std::vector<int64_t> prefix{0};
   std::vector<int> pid;
@@ -449,17 +517,19 @@ bh_status make_xfer(bh_batch* b, const std::vector<std::pair<int, XferArgs<T>>>&
 }
 
 // per-call lists: same shape every call, pointers refreshed with an async copy
-bh_status refresh_vec(bh_batch* b, const std::vector<std::pair<int, Vec>>& items, VecOpList& op,
-                      std::vector<Vec>& host) {
+bh_status refresh_vec(bh_batch* b, const std::vector<std::pair<int, Vec<double>>>& items,
+                      VecOpList<double>& op, std::vector<Vec<double>>& host) {
   host.clear();
   for (auto& it : items) host.push_back(it.second);
-  BCK(cudaMemcpyAsync(op.v.d, host.data(), host.size() * sizeof(Vec), cudaMemcpyHostToDevice,
-                      b->st));
+  BCK(cudaMemcpyAsync(op.v.d, host.data(), host.size() * sizeof(Vec<double>),
+                      cudaMemcpyHostToDevice, b->st));
   return BH_OK;
 }
 
-bh_status make_vec(bh_batch* b, const std::vector<std::pair<int, Vec>>& items, VecOpList& op) {
-  std::vector<Vec> v;
+template <typename T>
+bh_status make_vec(bh_batch* b, const std::vector<std::pair<int, Vec<T>>>& items,
+                   VecOpList<T>& op) {
+  std::vector<Vec<T>> v;
   std::vector<int64_t> prefix{0}, cprefix{0};
   std::vector<int> pid;
   for (auto& it : items) {
@@ -477,11 +547,28 @@ bh_status make_vec(bh_batch* b, const std::vector<std::pair<int, Vec>>& items, V
   return BH_OK;
 }
 
+bh_status make_conv(bh_batch* b, const std::vector<std::pair<int, Conv>>& items, ConvOpList& op) {
+  std::vector<Conv> v;
+  std::vector<int64_t> prefix{0};
+  std::vector<int> pid;
+  for (auto& it : items) {
+    v.push_back(it.second);
+    pid.push_back(it.first);
+    prefix.push_back(prefix.back() + it.second.n);
+  }
+  op.total = prefix.back();
+  BCKS(upload(b, v, op.v));
+  BCKS(upload(b, prefix, op.prefix));
+  BCKS(upload(b, pid, op.pid));
+  return BH_OK;
+}
+
 int mvs_pb(const bh_batch* b, int k) {
   if (b->tile[k] > 0) return b->tile[k];
   return 4;  // default before tuning
 }
 
+template <typename T>
 size_t mvs_smem(int k, int pb) {
   switch (k) {
     case 2: return Mvs2Cfg<T, 2>::smem_bytes(pb);
@@ -493,7 +580,8 @@ size_t mvs_smem(int k, int pb) {
   }
 }
 
-int mvs_pb_max(int k) {
+template <typename T>
+int mvs_pb_max_t(int k) {
   switch (k) {
     case 2: return Mvs2Cfg<T, 2>::PB_MAX;
     case 3: return Mvs2Cfg<T, 3>::PB_MAX;
@@ -504,6 +592,105 @@ int mvs_pb_max(int k) {
   }
 }
 
+int mvs_pb_max(const bh_batch* b, int k) {
+  return b->mixed ? mvs_pb_max_t<float>(k) : mvs_pb_max_t<double>(k);
+}
+
+size_t mvs_smem_for(const bh_batch* b, int k, int pb) {
+  return b->mixed ? mvs_smem<float>(k, pb) : mvs_smem<double>(k, pb);
+}
+
+// typed level buffers of the V-cycle
+template <typename T> struct LvBuf;
+template <> struct LvBuf<double> {
+  static double* x(Level& l) { return l.x64; }
+  static double* b(Level& l) { return l.b64; }
+  static double* xs(bh_ctx* c) { return c->xs64[0]; }
+  static const void* tab(bh_ctx* c) { return c->tab64; }
+};
+template <> struct LvBuf<float> {
+  static float* x(Level& l) { return l.x32; }
+  static float* b(Level& l) { return l.b32; }
+  static float* xs(bh_ctx* c) { return c->xs32[0]; }
+  static const void* tab(bh_ctx* c) { return c->tab32; }
+};
+
+// the V-cycle ops of value type T at one depth (smoothing, prolongation,
+// zeroing of the coarse iterate, coarse solve) for the problems in `ps`
+template <typename T>
+bh_status build_vdepth(bh_batch* b, int t, VDepth<T>& V, Depth& D) {
+  std::vector<std::pair<int, XferArgs<T>>> p0, p1;
+  std::vector<std::pair<int, Vec<T>>> zc;
+  std::vector<Symv<T>> sv;
+  std::vector<int> svp;
+  // per color and degree (index k): patch-list arguments, problems, tiles
+  std::vector<std::vector<MvsArgs<T>>> margs(8 * (kMaxK + 1));
+  std::vector<std::vector<int>> mpid(8 * (kMaxK + 1));
+  std::vector<std::vector<Tile>> mtiles(8 * (kMaxK + 1));
+  size_t smem_k[kMaxK + 1] = {0};
+  for (int p = 0; p < b->P; ++p) {
+    const int l = b->L[p] - t;
+    if (l < 1) continue;
+    bh_ctx* c = b->ctx[p];
+    Level& Lv = c->lv[l];
+    if (l == 1) {
+      sv.push_back(Symv<T>{c->coarse_inv, LvBuf<T>::b(Lv), LvBuf<T>::x(Lv), c->coarse_n, Lv.pscale});
+      svp.push_back(p);
+      D.maxn_symv = std::max(D.maxn_symv, c->coarse_n);
+      continue;
+    }
+    Level& Lc = c->lv[l - 1];
+    p0.push_back({p, xfer_args<T, true>(0, Lv.g, LvBuf<T>::x(Lc), LvBuf<T>::xs(c), false)});
+    p1.push_back({p, xfer_args<T, true>(1, Lv.g, LvBuf<T>::xs(c), LvBuf<T>::x(Lv), true)});
+    zc.push_back({p, Vec<T>{LvBuf<T>::x(Lc), nullptr, Lc.g.nd, 0, 0}});
+    const int k = b->k[p];
+    const int pb = std::min(mvs_pb(b, k), mvs_pb_max_t<T>(k));
+    smem_k[k] = mvs_smem<T>(k, pb);
+    const DevTables dt = Ops<T>::device_tables(LvBuf<T>::tab(c), k);
+    for (int col = 0; col < 8; ++col) {
+      MvsArgs<T> a{};
+      a.x = LvBuf<T>::x(Lv);
+      a.b = LvBuf<T>::b(Lv);
+      a.verts = Lv.verts + Lv.coff[col];
+      a.count = Lv.coff[col + 1] - Lv.coff[col];
+      a.N = Lv.g.N;
+      a.n = Lv.g.n;
+      a.pb = pb;
+      a.ascale = Lv.ascale;
+      a.pscale = c->p.omega * Lv.pscale;
+      a.dinv = static_cast<const T*>(dt.dinv);
+      const int g = col * (kMaxK + 1) + k;
+      const int s = (int)margs[g].size();
+      margs[g].push_back(a);
+      mpid[g].push_back(p);
+      for (int f = 0; f < a.count; f += pb) mtiles[g].push_back(Tile{s, f, std::min(pb, a.count - f)});
+    }
+  }
+  if (!p0.empty()) {
+    BCKS(make_xfer(b, p0, V.prol[0]));
+    BCKS(make_xfer(b, p1, V.prol[1]));
+    BCKS(make_vec(b, zc, V.zero_coarse));
+    for (int col = 0; col < 8; ++col) {
+      for (int k = 0; k <= kMaxK; ++k) {
+        const int g = col * (kMaxK + 1) + k;
+        if (mtiles[g].empty()) continue;
+        V.mvs[col].emplace_back();
+        MvsOp<T>& op = V.mvs[col].back();
+        BCKS(upload(b, margs[g], op.args));
+        BCKS(upload(b, mpid[g], op.pid));
+        BCKS(upload(b, mtiles[g], op.tiles));
+        op.smem = smem_k[k];
+      }
+    }
+  }
+  if (!sv.empty()) {
+    BCKS(upload(b, sv, V.symv));
+    BCKS(upload(b, svp, D.symv_pid));
+    D.nsymv = (int)sv.size();
+  }
+  return BH_OK;
+}
+
 // the lockstep V-cycle's work lists (depends on the tile shapes)
 bh_status build_depths(bh_batch* b) {
   const int P = b->P;
@@ -511,160 +698,141 @@ bh_status build_depths(bh_batch* b) {
   b->depth.assign(T_, Depth());
   for (int t = 0; t < T_; ++t) {
     Depth& D = b->depth[t];
-    std::vector<std::pair<int, SweepArgs<T>>> rx, ry;
-    std::vector<std::pair<int, XferArgs<T>>> r0, r1, p0, p1;
-    std::vector<std::pair<int, Vec>> zc;
-    std::vector<Symv> sv;
-    std::vector<int> svp;
-    // per color and degree (index k): patch-list arguments, problems, tiles
-    std::vector<std::vector<MvsArgs<T>>> margs(8 * (kMaxK + 1));
-    std::vector<std::vector<int>> mpid(8 * (kMaxK + 1));
-    std::vector<std::vector<Tile>> mtiles(8 * (kMaxK + 1));
-    size_t smem_k[kMaxK + 1] = {0};
+    std::vector<std::pair<int, SweepArgs<double>>> rx, ry;
+    std::vector<std::pair<int, XferArgs<double>>> r0, r1;
+    std::vector<std::pair<int, Conv>> xf, bd;
     for (int p = 0; p < P; ++p) {
       const int l = b->L[p] - t;
       if (l < 1) continue;
-      bh_ctx* c = b->ctx[p];
-      Level& Lv = c->lv[l];
       if (l == 1) {
-        sv.push_back(Symv{c->coarse_inv, Lv.b64, Lv.x64, c->coarse_n, Lv.pscale});
-        svp.push_back(p);
-        D.maxn_symv = std::max(D.maxn_symv, c->coarse_n);
+        D.coarse = true;
         continue;
       }
+      D.smooth = true;
+      bh_ctx* c = b->ctx[p];
+      Level& Lv = c->lv[l];
       Level& Lc = c->lv[l - 1];
-      T* s0 = c->scr64;
-      T* s1 = c->scr64 + Lv.g.nd;
-      T* s2 = c->scr64 + 2 * Lv.g.nd;
-      rx.push_back({p, sweep_args(Lv, 0, Lv.x64, nullptr, nullptr, s0, s1, s2, nullptr, kStore)});
-      ry.push_back({p, sweep_args(Lv, 1, s0, s1, s2, Lv.r64, nullptr, nullptr, Lv.b64, kResidual)});
-      r0.push_back({p, xfer_args<false>(0, Lv.g, Lv.r64, c->xs64[0], false)});
-      r1.push_back({p, xfer_args<false>(1, Lv.g, c->xs64[0], Lc.b64, false)});
-      p0.push_back({p, xfer_args<true>(0, Lv.g, Lc.x64, c->xs64[0], false)});
-      p1.push_back({p, xfer_args<true>(1, Lv.g, c->xs64[0], Lv.x64, true)});
-      zc.push_back({p, Vec{Lc.x64, nullptr, Lc.g.nd, 0, 0}});
-      const int k = b->k[p];
-      const int pb = std::min(mvs_pb(b, k), mvs_pb_max(k));
-      smem_k[k] = mvs_smem(k, pb);
-      const DevTables dt = Ops<T>::device_tables(c->tab64, k);
-      for (int col = 0; col < 8; ++col) {
-        MvsArgs<T> a{};
-        a.x = Lv.x64;
-        a.b = Lv.b64;
-        a.verts = Lv.verts + Lv.coff[col];
-        a.count = Lv.coff[col + 1] - Lv.coff[col];
-        a.N = Lv.g.N;
-        a.n = Lv.g.n;
-        a.pb = pb;
-        a.ascale = Lv.ascale;
-        a.pscale = c->p.omega * Lv.pscale;
-        a.dinv = static_cast<const T*>(dt.dinv);
-        const int g = col * (kMaxK + 1) + k;
-        const int s = (int)margs[g].size();
-        margs[g].push_back(a);
-        mpid[g].push_back(p);
-        for (int f = 0; f < a.count; f += pb) mtiles[g].push_back(Tile{s, f, std::min(pb, a.count - f)});
+      double* s0 = c->scr64;
+      double* s1 = c->scr64 + Lv.g.nd;
+      double* s2 = c->scr64 + 2 * Lv.g.nd;
+      // defect in FP64: of x64 (FP64) or of dx64 = x32 (R64), against the FP64
+      // right-hand side of the level (R64: b64 on the finest level, db64 below)
+      const double* xin = b->mixed ? Lv.dx64 : Lv.x64;
+      const double* bin = (b->mixed && l != b->L[p]) ? Lv.db64 : Lv.b64;
+      double* bc = b->mixed ? Lc.db64 : Lc.b64;
+      rx.push_back({p, sweep_args<double>(Lv, 0, xin, nullptr, nullptr, s0, s1, s2, nullptr, kStore)});
+      ry.push_back({p, sweep_args<double>(Lv, 1, s0, s1, s2, Lv.r64, nullptr, nullptr, bin, kResidual)});
+      r0.push_back({p, xfer_args<double, false>(0, Lv.g, Lv.r64, c->xs64[0], false)});
+      r1.push_back({p, xfer_args<double, false>(1, Lv.g, c->xs64[0], bc, false)});
+      if (b->mixed) {
+        xf.push_back({p, Conv{Lv.dx64, Lv.x32, Lv.g.nd, 0}});
+        bd.push_back({p, Conv{Lc.db64, Lc.b32, Lc.g.nd, 0}});
       }
     }
-    D.smooth = !rx.empty();
-    D.coarse = !sv.empty();
     if (D.smooth) {
       BCKS(make_sweep(b, rx, D.res_x));
       BCKS(make_sweep(b, ry, D.res_y));
       BCKS(make_xfer(b, r0, D.restr[0]));
       BCKS(make_xfer(b, r1, D.restr[1]));
-      BCKS(make_xfer(b, p0, D.prol[0]));
-      BCKS(make_xfer(b, p1, D.prol[1]));
-      BCKS(make_vec(b, zc, D.zero_coarse));
-      for (int col = 0; col < 8; ++col) {
-        for (int k = 0; k <= kMaxK; ++k) {
-          const int g = col * (kMaxK + 1) + k;
-          if (mtiles[g].empty()) continue;
-          D.mvs[col].emplace_back();
-          MvsOp& op = D.mvs[col].back();
-          BCKS(upload(b, margs[g], op.args));
-          BCKS(upload(b, mpid[g], op.pid));
-          BCKS(upload(b, mtiles[g], op.tiles));
-          op.smem = smem_k[k];
-        }
+      if (b->mixed) {
+        BCKS(make_conv(b, xf, D.x_f2d));
+        BCKS(make_conv(b, bd, D.b_d2f));
       }
     }
-    if (D.coarse) {
-      BCKS(upload(b, sv, D.symv));
-      BCKS(upload(b, svp, D.symv_pid));
-      D.nsymv = (int)sv.size();
-    }
+    if (b->mixed)
+      BCKS(build_vdepth<float>(b, t, D.v32, D));
+    else
+      BCKS(build_vdepth<double>(b, t, D.v64, D));
   }
   return BH_OK;
 }
 
 // ---- launches (all on b->st, graph-capturable) ---------------------------------
-cudaError_t run_sweep(bh_batch* b, const SweepOp& op, int kind) {
+void count_launch(bh_batch* b, int n = 1) {
+  b->launches += n;
+  g_kernel_launches.fetch_add(n);
+}
+
+template <typename T>
+cudaError_t run_sweep(bh_batch* b, const SweepOp<T>& op, int kind) {
   if (op.total == 0) return cudaSuccess;
   const unsigned g = blocks_for(op.total, 128);
   if (kind == 0)
-    sweep_batch_kernel<0><<<g, 128, 0, b->st>>>(meta(b), op.args.d, op.prefix.d, op.pid.d, op.pid.n);
+    sweep_batch_kernel<T, 0><<<g, 128, 0, b->st>>>(meta<T>(b), op.args.d, op.prefix.d, op.pid.d,
+                                                   op.pid.n);
   else
-    sweep_batch_kernel<2><<<g, 128, 0, b->st>>>(meta(b), op.args.d, op.prefix.d, op.pid.d, op.pid.n);
-  b->launches++;
-  g_kernel_launches.fetch_add(1);
+    sweep_batch_kernel<T, 2><<<g, 128, 0, b->st>>>(meta<T>(b), op.args.d, op.prefix.d, op.pid.d,
+                                                   op.pid.n);
+  count_launch(b);
   return cudaGetLastError();
 }
 
-cudaError_t run_xfer(bh_batch* b, const XferOp& op, bool prolong) {
+template <typename T>
+cudaError_t run_xfer(bh_batch* b, const XferOp<T>& op, bool prolong) {
   if (op.total == 0) return cudaSuccess;
   const unsigned g = blocks_for(op.total, 128);
   if (prolong)
-    xfer_batch_kernel<true><<<g, 128, 0, b->st>>>(meta(b), op.args.d, op.prefix.d, op.pid.d, op.pid.n);
+    xfer_batch_kernel<T, true><<<g, 128, 0, b->st>>>(meta<T>(b), op.args.d, op.prefix.d, op.pid.d,
+                                                     op.pid.n);
   else
-    xfer_batch_kernel<false><<<g, 128, 0, b->st>>>(meta(b), op.args.d, op.prefix.d, op.pid.d, op.pid.n);
-  b->launches++;
-  g_kernel_launches.fetch_add(1);
+    xfer_batch_kernel<T, false><<<g, 128, 0, b->st>>>(meta<T>(b), op.args.d, op.prefix.d,
+                                                      op.pid.d, op.pid.n);
+  count_launch(b);
   return cudaGetLastError();
 }
 
-cudaError_t run_vec(bh_batch* b, const VecOpList& op, int kind, const double* coef, int cstride,
-                    int cslot, double sign, int yslot = 0, int xslot = 0) {
+template <typename T>
+cudaError_t run_vec(bh_batch* b, const VecOpList<T>& op, int kind, const double* coef,
+                    int cstride, int cslot, double sign, int yslot = 0, int xslot = 0) {
   if (op.total == 0) return cudaSuccess;
   int64_t g = blocks_for(op.total, 256);
   if (g > 152 * 16) g = 152 * 16;
-  vec_batch_kernel<<<(unsigned)g, 256, 0, b->st>>>(meta(b), op.v.d, op.prefix.d, op.pid.d,
-                                                   op.pid.n, kind, coef, cstride, cslot, sign,
-                                                   yslot, xslot);
-  b->launches++;
-  g_kernel_launches.fetch_add(1);
+  vec_batch_kernel<T><<<(unsigned)g, 256, 0, b->st>>>(meta<T>(b), op.v.d, op.prefix.d, op.pid.d,
+                                                      op.pid.n, kind, coef, cstride, cslot, sign,
+                                                      yslot, xslot);
+  count_launch(b);
   return cudaGetLastError();
 }
 
-cudaError_t run_dot(bh_batch* b, const VecOpList& op, int cslot, int yslot = 0, int xslot = 0) {
+cudaError_t run_conv(bh_batch* b, const ConvOpList& op, int dir, int slot = 0) {
+  if (op.total == 0) return cudaSuccess;
+  int64_t g = blocks_for(op.total, 256);
+  if (g > 152 * 16) g = 152 * 16;
+  conv_batch_kernel<<<(unsigned)g, 256, 0, b->st>>>(meta<double>(b), op.v.d, op.prefix.d,
+                                                    op.pid.d, op.pid.n, dir, slot);
+  count_launch(b);
+  return cudaGetLastError();
+}
+
+cudaError_t run_dot(bh_batch* b, const VecOpList<double>& op, int cslot, int yslot = 0,
+                    int xslot = 0) {
   if (op.chunks == 0) return cudaSuccess;
-  dot_batch_partial<<<(unsigned)op.chunks, 256, 0, b->st>>>(meta(b), op.v.d, op.cprefix.d,
-                                                          op.pid.d, op.pid.n, b->d_partials,
-                                                          yslot, xslot);
+  dot_batch_partial<<<(unsigned)op.chunks, 256, 0, b->st>>>(meta<double>(b), op.v.d,
+                                                            op.cprefix.d, op.pid.d, op.pid.n,
+                                                            b->d_partials, yslot, xslot);
   dot_batch_final<<<blocks_for(op.pid.n, 64), 64, 0, b->st>>>(op.cprefix.d, op.pid.d, op.pid.n,
                                                              b->d_partials, b->d_dots, b->m + 2,
                                                              cslot);
-  b->launches += 2;
-  g_kernel_launches.fetch_add(2);
+  count_launch(b, 2);
   return cudaGetLastError();
 }
 
 // one color: a launch per degree group, one block per tile, each with the
 // shared memory of its own tile shape; with several groups the launches fork
 // from b->st onto side streams and join back (parallel graph branches)
-cudaError_t run_mvs(bh_batch* b, const std::vector<MvsOp>& ops) {
+template <typename T>
+cudaError_t run_mvs(bh_batch* b, const std::vector<MvsOp<T>>& ops) {
   if (ops.empty()) return cudaSuccess;
   cudaError_t e;
   const bool fork = ops.size() > 1;
   if (fork && (e = cudaEventRecord(b->fork, b->st)) != cudaSuccess) return e;
   for (size_t i = 0; i < ops.size(); ++i) {
-    const MvsOp& op = ops[i];
+    const MvsOp<T>& op = ops[i];
     cudaStream_t st = fork ? b->side[i] : b->st;
     if (fork && (e = cudaStreamWaitEvent(st, b->fork, 0)) != cudaSuccess) return e;
-    mvs2_batch_kernel<<<op.tiles.n, 256, op.smem, st>>>(meta(b), op.args.d, op.pid.d, op.tiles.d,
-                                                        op.tiles.n);
-    b->launches++;
-    g_kernel_launches.fetch_add(1);
+    mvs2_batch_kernel<T><<<op.tiles.n, 256, op.smem, st>>>(meta<T>(b), op.args.d, op.pid.d,
+                                                           op.tiles.d, op.tiles.n);
+    count_launch(b);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (fork && (e = cudaEventRecord(b->join[i], st)) != cudaSuccess) return e;
   }
@@ -674,34 +842,53 @@ cudaError_t run_mvs(bh_batch* b, const std::vector<MvsOp>& ops) {
   return cudaSuccess;
 }
 
-// lockstep V-cycle from depth t: x_L = MG(b_L) with x_L zero on entry
-cudaError_t vcycle_from(bh_batch* b, int t) {
-  if (t >= (int)b->depth.size()) return cudaSuccess;
-  Depth& D = b->depth[t];
+template <typename T>
+cudaError_t run_colors(bh_batch* b, const VDepth<T>& V, int c0, int c1) {
   cudaError_t e;
-  if (D.coarse) {
-    dim3 grid(blocks_for(D.maxn_symv, 128), D.nsymv);
-    coarse_batch_kernel<<<grid, 128, 0, b->st>>>(meta(b), D.symv.d, D.symv_pid.d, D.nsymv);
-    b->launches++;
-    g_kernel_launches.fetch_add(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (!D.smooth) return cudaSuccess;
-  for (int col = 0; col < 8; ++col)
-    if ((e = run_mvs(b, D.mvs[col])) != cudaSuccess) return e;
-  if ((e = run_sweep(b, D.res_x, 0)) != cudaSuccess) return e;
-  if ((e = run_sweep(b, D.res_y, 2)) != cudaSuccess) return e;
-  if ((e = run_xfer(b, D.restr[0], false)) != cudaSuccess) return e;
-  if ((e = run_xfer(b, D.restr[1], false)) != cudaSuccess) return e;
-  if ((e = run_vec(b, D.zero_coarse, kZero, nullptr, 0, 0, 0.0)) != cudaSuccess) return e;
-  if ((e = vcycle_from(b, t + 1)) != cudaSuccess) return e;
-  if ((e = run_xfer(b, D.prol[0], true)) != cudaSuccess) return e;
-  if ((e = run_xfer(b, D.prol[1], true)) != cudaSuccess) return e;
-  for (int col = 0; col < 8; ++col)
-    if ((e = run_mvs(b, D.mvs[col])) != cudaSuccess) return e;
+  for (int col = c0; col < c1; ++col)
+    if ((e = run_mvs<T>(b, V.mvs[col])) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
+template <typename T> const VDepth<T>& vdepth(const Depth& D);
+template <> const VDepth<double>& vdepth<double>(const Depth& D) { return D.v64; }
+template <> const VDepth<float>& vdepth<float>(const Depth& D) { return D.v32; }
+
+// lockstep V-cycle from depth t in value type T: x_l = MG_l(0, b_l) on level
+// l = L_p - t of every problem (x_l zero on entry)
+template <typename T>
+cudaError_t vcycle_from(bh_batch* b, int t) {
+  if (t >= (int)b->depth.size()) return cudaSuccess;
+  Depth& D = b->depth[t];
+  const VDepth<T>& V = vdepth<T>(D);
+  cudaError_t e;
+  if (D.coarse) {
+    dim3 grid(blocks_for(D.maxn_symv, 128), D.nsymv);
+    coarse_batch_kernel<T><<<grid, 128, 0, b->st>>>(meta<T>(b), V.symv.d, D.symv_pid.d, D.nsymv);
+    count_launch(b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (!D.smooth) return cudaSuccess;
+  for (int s = 0; s < b->pre; ++s)
+    if ((e = run_colors<T>(b, V, 0, 8)) != cudaSuccess) return e;
+  if (b->mixed && (e = run_conv(b, D.x_f2d, kF2D)) != cudaSuccess) return e;
+  if ((e = run_sweep<double>(b, D.res_x, 0)) != cudaSuccess) return e;
+  if ((e = run_sweep<double>(b, D.res_y, 2)) != cudaSuccess) return e;
+  if ((e = run_xfer<double>(b, D.restr[0], false)) != cudaSuccess) return e;
+  if ((e = run_xfer<double>(b, D.restr[1], false)) != cudaSuccess) return e;
+  if (b->mixed && (e = run_conv(b, D.b_d2f, kD2F)) != cudaSuccess) return e;
+  if ((e = run_vec<T>(b, V.zero_coarse, kZero, nullptr, 0, 0, 0.0)) != cudaSuccess) return e;
+  if ((e = vcycle_from<T>(b, t + 1)) != cudaSuccess) return e;
+  if ((e = run_xfer<T>(b, V.prol[0], true)) != cudaSuccess) return e;
+  if ((e = run_xfer<T>(b, V.prol[1], true)) != cudaSuccess) return e;
+  for (int s = 0; s < b->post; ++s)
+    if ((e = run_colors<T>(b, V, 0, 8)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+// The captured graph: x64_L = MG(0, b64_L) for every problem.  FP64: zero
+// x64_L, V-cycle.  R64: zero x32_L, b32_L = b64_L, FP32 V-cycle (FP64 defects
+// against b64_L on the finest level), x64_L = x32_L.
 bh_status capture_vcycle(bh_batch* b) {
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
@@ -711,18 +898,38 @@ bh_status capture_vcycle(bh_batch* b) {
     cudaGraphDestroy(b->graph);
     b->graph = nullptr;
   }
-  // the V-cycle starts from x_L = 0 on the finest level of every problem
-  std::vector<std::pair<int, Vec>> zf;
+  std::vector<std::pair<int, Vec<double>>> zf64;
+  std::vector<std::pair<int, Vec<float>>> zf32;
+  std::vector<std::pair<int, Conv>> bin, xout;
   for (int p = 0; p < b->P; ++p) {
     Level& F = b->ctx[p]->lv[b->L[p]];
-    zf.push_back({p, Vec{F.x64, nullptr, F.g.nd, 0, 0}});
+    zf64.push_back({p, Vec<double>{F.x64, nullptr, F.g.nd, 0, 0}});
+    zf32.push_back({p, Vec<float>{F.x32, nullptr, F.g.nd, 0, 0}});
+    bin.push_back({p, Conv{F.b64, F.b32, F.g.nd, 0}});
+    xout.push_back({p, Conv{F.x64, F.x32, F.g.nd, 0}});
   }
-  VecOpList zero_fine;
-  BCKS(make_vec(b, zf, zero_fine));
+  VecOpList<double> zero64;
+  VecOpList<float> zero32;
+  ConvOpList cin, cout_;
+  if (b->mixed) {
+    BCKS(make_vec(b, zf32, zero32));
+    BCKS(make_conv(b, bin, cin));
+    BCKS(make_conv(b, xout, cout_));
+  } else {
+    BCKS(make_vec(b, zf64, zero64));
+  }
   const long long before = b->launches, before_g = g_kernel_launches.load();
   BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = run_vec(b, zero_fine, kZero, nullptr, 0, 0, 0.0);
-  if (e == cudaSuccess) e = vcycle_from(b, 0);
+  cudaError_t e;
+  if (b->mixed) {
+    e = run_vec<float>(b, zero32, kZero, nullptr, 0, 0, 0.0);
+    if (e == cudaSuccess) e = run_conv(b, cin, kD2F);
+    if (e == cudaSuccess) e = vcycle_from<float>(b, 0);
+    if (e == cudaSuccess) e = run_conv(b, cout_, kF2D);
+  } else {
+    e = run_vec<double>(b, zero64, kZero, nullptr, 0, 0, 0.0);
+    if (e == cudaSuccess) e = vcycle_from<double>(b, 0);
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
   // captured kernels run when the graph is replayed and are counted then
@@ -749,22 +956,36 @@ bh_status set_active(bh_batch* b, const std::vector<int>& act) {
   return BH_OK;
 }
 
+bh_status launch_graph(bh_batch* b) {
+  BCK(cudaGraphLaunch(b->gexec, b->st));
+  count_launch(b, (int)b->graph_kernels);
+  return BH_OK;
+}
+
+// only ever raise a kernel's shared-memory limit: graphs of other live batches
+// may launch it with more shared memory than this batch needs
+template <typename T>
+bh_status raise_smem_limit(size_t smem) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes fa{};
+  BCK(cudaFuncGetAttributes(&fa, mvs2_batch_kernel<T>));
+  if ((int)smem > fa.maxDynamicSharedSizeBytes)
+    BCK(cudaFuncSetAttribute(mvs2_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem));
+  return BH_OK;
+}
+
 bh_status prepare(bh_batch* b) {
   // mvs kernel: allow the largest dynamic shared memory any tile shape needs
   size_t smem = 0;
   for (int p = 0; p < b->P; ++p)
-    smem = std::max(smem, mvs_smem(b->k[p], std::min(mvs_pb(b, b->k[p]), mvs_pb_max(b->k[p]))));
-  {
-    // only ever raise the kernel's limit: graphs of other live batches may
-    // launch it with more shared memory than this batch needs
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lock(mu);
-    cudaFuncAttributes fa{};
-    BCK(cudaFuncGetAttributes(&fa, mvs2_batch_kernel));
-    if ((int)smem > fa.maxDynamicSharedSizeBytes)
-      BCK(cudaFuncSetAttribute(mvs2_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
-  }
+    smem = std::max(smem, mvs_smem_for(b, b->k[p],
+                                       std::min(mvs_pb(b, b->k[p]), mvs_pb_max(b, b->k[p]))));
+  if (b->mixed)
+    BCKS(raise_smem_limit<float>(smem));
+  else
+    BCKS(raise_smem_limit<double>(smem));
   // one side stream and join event per degree present (created once)
   int groups = 0;
   for (int k = 0; k <= kMaxK; ++k)
@@ -785,43 +1006,56 @@ bh_status prepare(bh_batch* b) {
 bh_status ensure_plan(bh_batch* b) {
   if (b->plan) return BH_OK;
   const int P = b->P, m = b->m;
-  for (int p = 0; p < P; ++p) {  // Krylov basis V_0..V_m per problem
+  for (int p = 0; p < P; ++p) {  // Krylov basis V_0..V_m (and Z_0..Z_{m-1} for right) per problem
     bh_ctx* c = b->ctx[p];
-    if (!c->V) {
-      const int64_t n = c->lv[b->L[p]].g.nd;
-      if (cudaMalloc(&c->V, (size_t)(m + 1) * n * sizeof(double)) != cudaSuccess) {
-        c->V = nullptr;
+    const int64_t n = c->lv[b->L[p]].g.nd;
+    double** bufs[2] = {&c->V, &c->Z};
+    const int64_t cnt[2] = {m + 1, b->right ? m : 0};
+    for (int i = 0; i < 2; ++i) {
+      if (*bufs[i] || cnt[i] == 0) continue;
+      if (cudaMalloc(bufs[i], (size_t)cnt[i] * n * sizeof(double)) != cudaSuccess) {
+        *bufs[i] = nullptr;
         cudaGetLastError();
         return berr(BH_ENOMEM, "Krylov basis allocation failed");
       }
-      c->dev_allocs.push_back(c->V);
+      c->dev_allocs.push_back(*bufs[i]);
     }
   }
   SolvePlan* S = new (std::nothrow) SolvePlan();
   if (!S) return berr(BH_ENOMEM, "host allocation failed");
   b->plan = S;
   S->apply_x.resize(m);
-  std::vector<std::pair<int, SweepArgs<T>>> ay, rx, ry;
-  std::vector<std::vector<std::pair<int, SweepArgs<T>>>> ax(m);
-  std::vector<std::pair<int, Vec>> ww, wV, Vw, rr, z;
+  std::vector<std::pair<int, SweepArgs<double>>> ay, rx, ry;
+  std::vector<std::vector<std::pair<int, SweepArgs<double>>>> ax(m);
+  std::vector<std::pair<int, Vec<double>>> ww, wV, Vw, Vr, rr, xz, vc, rc, x64, z;
   for (int p = 0; p < P; ++p) {
     bh_ctx* c = b->ctx[p];
     Level& F = c->lv[b->L[p]];
     const int64_t n = F.g.nd;
-    T* s0 = c->scr64;
-    T* s1 = s0 + n;
-    T* s2 = s1 + n;
+    double* s0 = c->scr64;
+    double* s1 = s0 + n;
+    double* s2 = s1 + n;
+    // w = A (Z_j | V_j): into r64_L (right; the graph's input b64_L carries V_j)
+    // or into b64_L (left; the graph then gives w = M^-1 A V_j in x64_L)
+    double* basis = b->right ? c->Z : c->V;
+    double* aout = b->right ? F.r64 : F.b64;
+    double* w = b->right ? F.r64 : F.x64;
     for (int j = 0; j < m; ++j)
-      ax[j].push_back({p, sweep_args(F, 0, c->V + (int64_t)j * n, nullptr, nullptr, s0, s1, s2,
-                                     nullptr, kStore)});
-    ay.push_back({p, sweep_args(F, 1, s0, s1, s2, F.b64, nullptr, nullptr, nullptr, kStore)});
-    rx.push_back({p, sweep_args(F, 0, F.x64, nullptr, nullptr, s0, s1, s2, nullptr, kStore)});
-    ry.push_back({p, sweep_args(F, 1, s0, s1, s2, F.r64, nullptr, nullptr, F.b64, kResidual)});
-    ww.push_back({p, Vec{F.x64, F.x64, n, 0, 0}});
-    wV.push_back({p, Vec{F.x64, c->V, n, 0, n}});
-    Vw.push_back({p, Vec{c->V, F.x64, n, n, 0}});
-    rr.push_back({p, Vec{F.r64, F.r64, n, 0, 0}});
-    z.push_back({p, Vec{F.x64, nullptr, n, 0, 0}});
+      ax[j].push_back({p, sweep_args<double>(F, 0, basis + (int64_t)j * n, nullptr, nullptr, s0,
+                                             s1, s2, nullptr, kStore)});
+    ay.push_back({p, sweep_args<double>(F, 1, s0, s1, s2, aout, nullptr, nullptr, nullptr, kStore)});
+    rx.push_back({p, sweep_args<double>(F, 0, F.x64, nullptr, nullptr, s0, s1, s2, nullptr, kStore)});
+    ry.push_back({p, sweep_args<double>(F, 1, s0, s1, s2, F.r64, nullptr, nullptr, F.b64, kResidual)});
+    ww.push_back({p, Vec<double>{w, w, n, 0, 0}});
+    wV.push_back({p, Vec<double>{w, c->V, n, 0, n}});
+    Vw.push_back({p, Vec<double>{c->V, w, n, n, 0}});
+    Vr.push_back({p, Vec<double>{c->V, F.r64, n, n, 0}});    // V_0 = r / sqrt(r.r)
+    rr.push_back({p, Vec<double>{F.r64, F.r64, n, 0, 0}});
+    xz.push_back({p, Vec<double>{c->Z, F.x64, n, n, 0}});    // Z_j = x64_L
+    vc.push_back({p, Vec<double>{F.b64, c->V, n, 0, n}});    // b64_L = V_j
+    rc.push_back({p, Vec<double>{F.b64, F.r64, n, 0, 0}});   // b64_L = r
+    x64.push_back({p, Vec<double>{F.x64, F.x64, n, 0, 0}});
+    z.push_back({p, Vec<double>{F.x64, nullptr, n, 0, 0}});
   }
   for (int j = 0; j < m; ++j) BCKS(make_sweep(b, ax[j], S->apply_x[j]));
   BCKS(make_sweep(b, ay, S->apply_y));
@@ -830,13 +1064,53 @@ bh_status ensure_plan(bh_batch* b) {
   BCKS(make_vec(b, ww, S->ww));
   BCKS(make_vec(b, wV, S->wV));
   BCKS(make_vec(b, Vw, S->Vw));
+  BCKS(make_vec(b, Vr, S->Vr));
   BCKS(make_vec(b, rr, S->rr));
+  BCKS(make_vec(b, xz, S->xcopyZ));
+  BCKS(make_vec(b, vc, S->Vcopy));
+  BCKS(make_vec(b, rc, S->rcopy));
+  BCKS(make_vec(b, x64, S->x64dot));
   BCKS(make_vec(b, z, S->zero_x));
   BCKS(make_vec(b, z, S->copy_b));
   BCKS(make_vec(b, z, S->bnorm));
   BCKS(make_vec(b, z, S->xV));
   S->hd.assign((size_t)P * (m + 2), 0.0);
   S->hcoef.assign((size_t)P * (m + 2), 0.0);
+  return BH_OK;
+}
+
+// inputs written on the caller's stream must be complete before the batch reads them
+bh_status wait_user(bh_batch* b) {
+  BCK(cudaEventRecord(b->ev, b->user));
+  BCK(cudaStreamWaitEvent(b->st, b->ev, 0));
+  return BH_OK;
+}
+
+// after a batch call: later work on the caller's stream sees its results
+bh_status signal_user(bh_batch* b) {
+  BCK(cudaEventRecord(b->ev, b->st));
+  BCK(cudaStreamWaitEvent(b->user, b->ev, 0));
+  return BH_OK;
+}
+
+// copies between the caller's vectors and the finest-level buffers of every
+// problem (one launch each; dst[p] = src[p])
+bh_status copy_lists(bh_batch* b, double* const* dst, const double* const* src) {
+  std::vector<std::pair<int, Vec<double>>> items;
+  for (int p = 0; p < b->P; ++p)
+    items.push_back({p, Vec<double>{dst[p], src[p], b->ctx[p]->lv[b->L[p]].g.nd, 0, 0}});
+  VecOpList<double> op;
+  BCKS(make_vec(b, items, op));
+  BCK(run_vec<double>(b, op, kCopy, nullptr, 0, 0, 0.0));
+  // make_vec's device lists are batch allocations; this one is used once
+  BCK(cudaStreamSynchronize(b->st));
+  for (void* ptr : {(void*)op.v.d, (void*)op.prefix.d, (void*)op.cprefix.d, (void*)op.pid.d}) {
+    auto it = std::find(b->allocs.begin(), b->allocs.end(), ptr);
+    if (it != b->allocs.end()) {
+      cudaFree(*it);
+      b->allocs.erase(it);
+    }
+  }
   return BH_OK;
 }
 
@@ -850,15 +1124,31 @@ bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_b
   for (int i = 0; i < count; ++i) {
     const bh_params& p = params[i];
     if (p.dim != 2) return berr(BH_EINVAL, "bh_batch_create: the batched form supports 2D problems");
-    if (p.smoother != BH_MVS_COLORED || p.local_solver != BH_FDM || p.precision != BH_FP64 ||
-        p.coarse != BH_COARSE_EXACT || p.gmres_side != BH_LEFT || p.krylov != BH_GMRES)
+    if (p.smoother != BH_MVS_COLORED || p.local_solver != BH_FDM || p.coarse != BH_COARSE_EXACT ||
+        p.krylov != BH_GMRES)
       return berr(BH_EINVAL, "bh_batch_create: the batched form runs colored MVS with FDM local "
-                             "solvers, FP64, the exact coarse solve and left-preconditioned GMRES");
+                             "solvers, the exact coarse solve and GMRES");
+    if (p.precision != BH_FP64 && p.precision != BH_MIXED_FP32_R64)
+      return berr(BH_EINVAL, "bh_batch_create: the batched form runs the FP64 V-cycle or the FP32 "
+                             "V-cycle with FP64 defects (BH_MIXED_FP32_R64)");
+    if (p.precision != params[0].precision || p.gmres_side != params[0].gmres_side ||
+        p.pre_steps != params[0].pre_steps || p.post_steps != params[0].post_steps)
+      return berr(BH_EINVAL, "bh_batch_create: precision, GMRES side and smoothing steps must be "
+                             "the same for every problem of a batch");
+    if (p.precision != BH_FP64 && p.gmres_side != BH_RIGHT)
+      return berr(BH_EINVAL, "bh_batch_create: the FP32 V-cycle needs the flexible right-"
+                             "preconditioned GMRES (gmres_side = BH_RIGHT)");
+    if (p.pre_steps < 0 || p.post_steps < 0 || p.pre_steps + p.post_steps > 8)
+      return berr(BH_EINVAL, "bh_batch_create: smoothing steps must be in 0..8 in total");
   }
   bh_batch* b = new (std::nothrow) bh_batch();
   if (!b) return berr(BH_ENOMEM, "host allocation failed");
   b->P = count;
   b->user = (cudaStream_t)stream;
+  b->mixed = params[0].precision == BH_MIXED_FP32_R64;
+  b->right = params[0].gmres_side == BH_RIGHT;
+  b->pre = params[0].pre_steps;
+  b->post = params[0].post_steps;
   if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -882,14 +1172,20 @@ bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_b
     b->k.push_back(p.degree);
     b->L.push_back(p.level);
   }
-  std::vector<const void*> tabs;
-  for (int p = 0; p < count; ++p) tabs.push_back(Ops<T>::device_tables(b->ctx[p]->tab64, b->k[p]).tables);
+  std::vector<const void*> tabs64, tabs32;
+  for (int p = 0; p < count; ++p) {
+    tabs64.push_back(Ops<double>::device_tables(b->ctx[p]->tab64, b->k[p]).tables);
+    tabs32.push_back(b->mixed ? Ops<float>::device_tables(b->ctx[p]->tab32, b->k[p]).tables
+                              : nullptr);
+  }
   DevArray<int> dk;
-  DevArray<const void*> dt;
+  DevArray<const void*> dt64, dt32;
   bh_status s;
-  if ((s = upload(b, b->k, dk)) || (s = upload(b, tabs, dt))) return bail(s);
+  if ((s = upload(b, b->k, dk)) || (s = upload(b, tabs64, dt64)) || (s = upload(b, tabs32, dt32)))
+    return bail(s);
   b->d_k = dk.d;
-  b->d_tabs = dt.d;
+  b->d_tabs64 = dt64.d;
+  b->d_tabs32 = dt32.d;
   std::vector<int> act(count, 1);
   DevArray<int> da;
   if ((s = upload(b, act, da))) return bail(s);
@@ -931,9 +1227,9 @@ bh_status bh_batch_destroy(bh_batch* b) {
 bh_status bh_batch_set_tile(bh_batch* b, int degree, int patches_per_block) {
   if (!b || degree < 2 || degree > 7 || patches_per_block < 1 || patches_per_block > 32)
     return berr(BH_EINVAL, "bh_batch_set_tile: bad arguments");
-  if (patches_per_block > mvs_pb_max(degree))
+  if (patches_per_block > mvs_pb_max(b, degree))
     return berr(BH_EINVAL, "bh_batch_set_tile: tile exceeds the shared-memory budget (max " +
-                               std::to_string(mvs_pb_max(degree)) + " patches for this degree)");
+                               std::to_string(mvs_pb_max(b, degree)) + " patches for this degree)");
   b->tile[degree] = patches_per_block;
   return prepare(b);
 }
@@ -942,8 +1238,7 @@ bh_status bh_batch_vcycle_time(bh_batch* b, int reps, double* ms) {
   if (!b || reps < 1 || !ms) return berr(BH_EINVAL, "bad arguments");
   std::vector<int> act(b->P, 1);
   BCKS(set_active(b, act));
-  BCK(cudaEventRecord(b->ev, b->user));
-  BCK(cudaStreamWaitEvent(b->st, b->ev, 0));
+  BCKS(wait_user(b));
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
@@ -960,28 +1255,94 @@ bh_status bh_batch_vcycle_time(bh_batch* b, int reps, double* ms) {
   return BH_OK;
 }
 
+bh_status bh_batch_vcycle(bh_batch* b, const double* const* b_dev, double* const* x_dev) {
+  if (!b || !b_dev || !x_dev) return berr(BH_EINVAL, "bh_batch_vcycle: bad arguments");
+  for (int p = 0; p < b->P; ++p)
+    if (!b_dev[p] || !x_dev[p] || b_dev[p] == x_dev[p])
+      return berr(BH_EINVAL, "bh_batch_vcycle: null or aliased vectors");
+  std::vector<int> act(b->P, 1);
+  BCKS(set_active(b, act));
+  BCKS(wait_user(b));
+  std::vector<double*> bl(b->P), xl(b->P);
+  for (int p = 0; p < b->P; ++p) {
+    Level& F = b->ctx[p]->lv[b->L[p]];
+    bl[p] = F.b64;
+    xl[p] = F.x64;
+  }
+  BCKS(copy_lists(b, bl.data(), b_dev));
+  BCKS(launch_graph(b));
+  BCKS(copy_lists(b, x_dev, xl.data()));
+  return signal_user(b);
+}
+
+bh_status bh_batch_smooth_colors(bh_batch* b, double* const* x_dev, const double* const* b_dev,
+                                 int first_color, int end_color) {
+  if (!b || !b_dev || !x_dev) return berr(BH_EINVAL, "bh_batch_smooth_colors: bad arguments");
+  if (first_color < 0 || end_color > 8 || first_color > end_color)
+    return berr(BH_EINVAL, "bh_batch_smooth_colors: color range outside 0..8");
+  for (int p = 0; p < b->P; ++p) {
+    if (!b_dev[p] || !x_dev[p] || (const double*)x_dev[p] == b_dev[p])
+      return berr(BH_EINVAL, "bh_batch_smooth_colors: null or aliased vectors");
+    if (b->L[p] < 2)
+      return berr(BH_EINVAL, "bh_batch_smooth_colors: a level-1 problem has no smoother");
+  }
+  std::vector<int> act(b->P, 1);
+  BCKS(set_active(b, act));
+  BCKS(wait_user(b));
+  std::vector<double*> bl(b->P), xl(b->P);
+  for (int p = 0; p < b->P; ++p) {
+    Level& F = b->ctx[p]->lv[b->L[p]];
+    bl[p] = F.b64;
+    xl[p] = F.x64;
+  }
+  BCKS(copy_lists(b, bl.data(), b_dev));
+  BCKS(copy_lists(b, xl.data(), x_dev));
+  if (b->mixed) {
+    std::vector<std::pair<int, Conv>> cb, cx;
+    for (int p = 0; p < b->P; ++p) {
+      Level& F = b->ctx[p]->lv[b->L[p]];
+      cb.push_back({p, Conv{F.b64, F.b32, F.g.nd, 0}});
+      cx.push_back({p, Conv{F.x64, F.x32, F.g.nd, 0}});
+    }
+    ConvOpList ob, ox;
+    BCKS(make_conv(b, cb, ob));
+    BCKS(make_conv(b, cx, ox));
+    BCK(run_conv(b, ob, kD2F));
+    BCK(run_conv(b, ox, kD2F));
+    BCK(run_colors<float>(b, b->depth[0].v32, first_color, end_color));
+    BCK(run_conv(b, ox, kF2D));
+  } else {
+    BCK(run_colors<double>(b, b->depth[0].v64, first_color, end_color));
+  }
+  BCKS(copy_lists(b, x_dev, xl.data()));
+  return signal_user(b);
+}
+
 bh_status bh_batch_solve(bh_batch* b, const double* const* b_dev, double* const* x_dev,
                          double rtol, int maxit, int* iters, double* relres) {
   if (!b || !b_dev || !x_dev || !iters || !relres || !(rtol > 0.0) || maxit < 1)
     return berr(BH_EINVAL, "bh_batch_solve: bad arguments");
-  const int P = b->P, m = std::min(b->m, maxit);
+  for (int p = 0; p < b->P; ++p)
+    if (!b_dev[p] || !x_dev[p] || (const double*)x_dev[p] == b_dev[p])
+      return berr(BH_EINVAL, "bh_batch_solve: null or aliased vectors");
+  const int P = b->P, m = b->m;
   const int cs = b->m + 2;  // stride of the dots and coefficient arrays
+  const bool right = b->right;
   BCKS(ensure_plan(b));
   SolvePlan& S = *b->plan;
-  // inputs written on the caller's stream must be complete before the batch reads them
-  BCK(cudaEventRecord(b->ev, b->user));
-  BCK(cudaStreamWaitEvent(b->st, b->ev, 0));
-  // caller vectors: x (zeroed, updated), b (copied to b_L, norm, residual)
+  BCKS(wait_user(b));
+  // caller vectors: x (zeroed, updated), b (norm; copied to b64_L for the left
+  // start and the residual)
   {
-    std::vector<std::pair<int, Vec>> lx, lb, lbb, lxv;
+    std::vector<std::pair<int, Vec<double>>> lx, lb, lbb, lxv;
     for (int p = 0; p < P; ++p) {
       bh_ctx* c = b->ctx[p];
       Level& F = c->lv[b->L[p]];
       const int64_t n = F.g.nd;
-      lx.push_back({p, Vec{x_dev[p], nullptr, n, 0, 0}});
-      lb.push_back({p, Vec{F.b64, b_dev[p], n, 0, 0}});
-      lbb.push_back({p, Vec{const_cast<double*>(b_dev[p]), b_dev[p], n, 0, 0}});
-      lxv.push_back({p, Vec{x_dev[p], c->V, n, 0, n}});
+      lx.push_back({p, Vec<double>{x_dev[p], nullptr, n, 0, 0}});
+      lb.push_back({p, Vec<double>{right ? F.r64 : F.b64, b_dev[p], n, 0, 0}});
+      lbb.push_back({p, Vec<double>{const_cast<double*>(b_dev[p]), b_dev[p], n, 0, 0}});
+      lxv.push_back({p, Vec<double>{x_dev[p], right ? c->Z : c->V, n, 0, n}});
     }
     BCKS(refresh_vec(b, lx, S.zero_x, S.h_zero_x));
     BCKS(refresh_vec(b, lb, S.copy_b, S.h_copy_b));
@@ -992,122 +1353,184 @@ bh_status bh_batch_solve(bh_batch* b, const double* const* b_dev, double* const*
     for (int p = 0; p < P; ++p) {
       bh_ctx* c = b->ctx[p];
       Level& F = c->lv[b->L[p]];
-      T* s0 = c->scr64;
-      T* s1 = s0 + F.g.nd;
-      T* s2 = s1 + F.g.nd;
-      S.h_rx.push_back(sweep_args(F, 0, x_dev[p], nullptr, nullptr, s0, s1, s2, nullptr, kStore));
-      S.h_ry.push_back(sweep_args(F, 1, s0, s1, s2, F.r64, nullptr, nullptr, b_dev[p], kResidual));
+      double* s0 = c->scr64;
+      double* s1 = s0 + F.g.nd;
+      double* s2 = s1 + F.g.nd;
+      S.h_rx.push_back(sweep_args<double>(F, 0, x_dev[p], nullptr, nullptr, s0, s1, s2, nullptr, kStore));
+      S.h_ry.push_back(sweep_args<double>(F, 1, s0, s1, s2, F.r64, nullptr, nullptr, b_dev[p], kResidual));
     }
-    BCK(cudaMemcpyAsync(S.resid_x.args.d, S.h_rx.data(), P * sizeof(SweepArgs<T>),
+    BCK(cudaMemcpyAsync(S.resid_x.args.d, S.h_rx.data(), P * sizeof(SweepArgs<double>),
                         cudaMemcpyHostToDevice, b->st));
-    BCK(cudaMemcpyAsync(S.resid_y.args.d, S.h_ry.data(), P * sizeof(SweepArgs<T>),
+    BCK(cudaMemcpyAsync(S.resid_y.args.d, S.h_ry.data(), P * sizeof(SweepArgs<double>),
                         cudaMemcpyHostToDevice, b->st));
   }
   std::vector<int> act(P, 1);
   BCKS(set_active(b, act));
-  BCK(run_vec(b, S.zero_x, kZero, nullptr, 0, 0, 0.0));
-  // r0 = M^-1 b: b_L = b, V-cycle into x_L; beta = ||x_L||, ||b||
-  BCK(run_vec(b, S.copy_b, kCopy, nullptr, 0, 0, 0.0));
-  BCK(cudaGraphLaunch(b->gexec, b->st));
-  b->launches += b->graph_kernels;
-  g_kernel_launches.fetch_add(b->graph_kernels);
-  BCK(run_dot(b, S.ww, 0));
+  BCK(run_vec<double>(b, S.zero_x, kZero, nullptr, 0, 0, 0.0));
+  // r0 = b (right, in r64_L) or M^-1 b (left, in x64_L); beta = ||r0||, ||b||
+  BCK(run_vec<double>(b, S.copy_b, kCopy, nullptr, 0, 0, 0.0));
+  if (right) {
+    BCK(run_dot(b, S.rr, 0));
+  } else {
+    BCKS(launch_graph(b));
+    BCK(run_dot(b, S.x64dot, 0));
+  }
   BCK(run_dot(b, S.bnorm, 1));
   std::vector<double>& hd = S.hd;
   BCK(cudaMemcpyAsync(hd.data(), b->d_dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st));
   BCK(cudaStreamSynchronize(b->st));
-  std::vector<double> beta(P), bnorm(P);
+  std::vector<double> beta(P), bnorm(P), ref(P);
   for (int p = 0; p < P; ++p) {
     beta[p] = std::sqrt(hd[(size_t)p * cs]);
     bnorm[p] = std::sqrt(hd[(size_t)p * cs + 1]);
-    if (!std::isfinite(bnorm[p])) return berr(BH_EINVAL, "right-hand side is not finite");
+    ref[p] = beta[p];
+    if (!std::isfinite(bnorm[p]) || !std::isfinite(beta[p]))
+      return berr(BH_EINVAL, "right-hand side is not finite");
     if (!(bnorm[p] > 0.0) || !(beta[p] > 0.0)) act[p] = 0;
   }
-  BCKS(set_active(b, act));
-  BCK(run_vec(b, S.Vw, kScaleInvSqrt, b->d_dots, cs, 0, 1.0, 0, 0));  // V_0 = x_L / beta
+  std::vector<int> total(P, 0), conv(P, 0), ran(P, 0);
+  std::vector<double> est_last(P, 0.0);
+  for (int p = 0; p < P; ++p) conv[p] = act[p] ? 0 : 1;
   std::vector<std::vector<double>> H(P, std::vector<double>((size_t)(m + 1) * m, 0.0));
   std::vector<std::vector<double>> cn(P, std::vector<double>(m)), sn(P, std::vector<double>(m)),
       g(P, std::vector<double>(m + 1, 0.0));
-  std::vector<int> done_j(P, 0), conv(P, 0);
-  for (int p = 0; p < P; ++p) g[p][0] = beta[p];
-  for (int j = 0; j < m; ++j) {
+  std::vector<int> done_j(P, 0);
+  std::vector<double>& coef = S.hcoef;
+  // restart cycles: V_0 = r / beta, Arnoldi until every active problem stops
+  while (true) {
     bool any = false;
     for (int p = 0; p < P; ++p) any |= act[p] != 0;
     if (!any) break;
-    BCK(run_sweep(b, S.apply_x[j], 0));  // b_L = A V_j
-    BCK(run_sweep(b, S.apply_y, 2));
-    BCK(cudaGraphLaunch(b->gexec, b->st));  // w = x_L = M^-1 b_L
-    b->launches += b->graph_kernels;
-    g_kernel_launches.fetch_add(b->graph_kernels);
-    for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
-      BCK(run_dot(b, S.wV, i, 0, i));
-      BCK(run_vec(b, S.wV, kAxpyDev, b->d_dots, cs, i, -1.0, 0, i));
+    BCKS(set_active(b, act));
+    BCK(run_vec<double>(b, right ? S.Vr : S.Vw, kScaleInvSqrt, b->d_dots, cs, 0, 1.0, 0, 0));
+    ran = act;
+    for (int p = 0; p < P; ++p) {
+      if (!act[p]) continue;
+      std::fill(g[p].begin(), g[p].end(), 0.0);
+      g[p][0] = beta[p];
+      done_j[p] = 0;
     }
-    BCK(run_dot(b, S.ww, j + 1));
+    for (int j = 0; j < m; ++j) {
+      any = false;
+      for (int p = 0; p < P; ++p) any |= act[p] != 0;
+      if (!any) break;
+      if (right) {  // z_j = M^-1 V_j (kept in Z_j), w = A z_j
+        BCK(run_vec<double>(b, S.Vcopy, kCopy, nullptr, 0, 0, 0.0, 0, j));
+        BCKS(launch_graph(b));
+        BCK(run_vec<double>(b, S.xcopyZ, kCopy, nullptr, 0, 0, 0.0, j, 0));
+        BCK(run_sweep<double>(b, S.apply_x[j], 0));
+        BCK(run_sweep<double>(b, S.apply_y, 2));
+      } else {  // w = M^-1 A V_j
+        BCK(run_sweep<double>(b, S.apply_x[j], 0));
+        BCK(run_sweep<double>(b, S.apply_y, 2));
+        BCKS(launch_graph(b));
+      }
+      for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
+        BCK(run_dot(b, S.wV, i, 0, i));
+        BCK(run_vec<double>(b, S.wV, kAxpyDev, b->d_dots, cs, i, -1.0, 0, i));
+      }
+      BCK(run_dot(b, S.ww, j + 1));
+      BCK(cudaMemcpyAsync(hd.data(), b->d_dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          b->st));
+      BCK(cudaStreamSynchronize(b->st));
+      bool changed = false;
+      for (int p = 0; p < P; ++p) {
+        if (!act[p]) continue;
+        auto Hij = [&](int i, int jj) -> double& { return H[p][(size_t)i * m + jj]; };
+        for (int i = 0; i <= j; ++i) Hij(i, j) = hd[(size_t)p * cs + i];
+        const double hn = std::sqrt(hd[(size_t)p * cs + j + 1]);
+        Hij(j + 1, j) = hn;
+        for (int i = 0; i < j; ++i) {
+          const double tt = cn[p][i] * Hij(i, j) + sn[p][i] * Hij(i + 1, j);
+          Hij(i + 1, j) = -sn[p][i] * Hij(i, j) + cn[p][i] * Hij(i + 1, j);
+          Hij(i, j) = tt;
+        }
+        const double rho = std::hypot(Hij(j, j), Hij(j + 1, j));
+        cn[p][j] = Hij(j, j) / rho;
+        sn[p][j] = Hij(j + 1, j) / rho;
+        Hij(j, j) = rho;
+        Hij(j + 1, j) = 0.0;
+        g[p][j + 1] = -sn[p][j] * g[p][j];
+        g[p][j] = cn[p][j] * g[p][j];
+        done_j[p] = j + 1;
+        total[p]++;
+        const double est = std::fabs(g[p][j + 1]);
+        est_last[p] = est;
+        if (!std::isfinite(est)) return berr(BH_ENOCONV, "batched GMRES: non-finite residual");
+        const bool ok = est <= rtol * ref[p] || hn == 0.0;
+        if (ok || total[p] >= maxit || j + 1 >= m) {
+          conv[p] = ok;
+          act[p] = 0;
+          changed = true;
+        }
+      }
+      if (changed) BCKS(set_active(b, act));
+      BCK(run_vec<double>(b, S.Vw, kScaleInvSqrt, b->d_dots, cs, j + 1, 1.0, j + 1, 0));  // V_{j+1}
+    }
+    // x += (Z | V) y for the problems of this cycle (back substitution on the
+    // host), then their true residual r = b - A x in r64_L
+    std::fill(coef.begin(), coef.end(), 0.0);
+    int jmax = 0;
+    for (int p = 0; p < P; ++p) {
+      if (!ran[p]) continue;
+      const int jd = done_j[p];
+      jmax = std::max(jmax, jd);
+      for (int i = jd - 1; i >= 0; --i) {
+        double sacc = g[p][i];
+        for (int jj = i + 1; jj < jd; ++jj) sacc -= H[p][(size_t)i * m + jj] * coef[(size_t)p * cs + jj];
+        coef[(size_t)p * cs + i] = sacc / H[p][(size_t)i * m + i];
+      }
+    }
+    BCKS(set_active(b, ran));
+    BCK(cudaMemcpyAsync(b->d_coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        b->st));
+    for (int i = 0; i < jmax; ++i) BCK(run_vec<double>(b, S.xV, kAxpyDev, b->d_coef, cs, i, 1.0, 0, i));
+    BCK(run_sweep<double>(b, S.resid_x, 0));
+    BCK(run_sweep<double>(b, S.resid_y, 2));
+    // restart the problems that stopped at the end of the cycle above the tolerance
+    std::vector<int> again(P, 0);
+    bool any_again = false;
+    for (int p = 0; p < P; ++p) {
+      again[p] = ran[p] && !conv[p] && total[p] < maxit;
+      any_again |= again[p] != 0;
+    }
+    if (!any_again) break;
+    BCKS(set_active(b, again));
+    if (right) {
+      BCK(run_dot(b, S.rr, 0));
+    } else {
+      BCK(run_vec<double>(b, S.rcopy, kCopy, nullptr, 0, 0, 0.0));
+      BCKS(launch_graph(b));
+      BCK(run_dot(b, S.x64dot, 0));
+    }
     BCK(cudaMemcpyAsync(hd.data(), b->d_dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost,
                         b->st));
     BCK(cudaStreamSynchronize(b->st));
-    bool changed = false;
     for (int p = 0; p < P; ++p) {
-      if (!act[p]) continue;
-      auto Hij = [&](int i, int jj) -> double& { return H[p][(size_t)i * m + jj]; };
-      for (int i = 0; i <= j; ++i) Hij(i, j) = hd[(size_t)p * cs + i];
-      const double hn = std::sqrt(hd[(size_t)p * cs + j + 1]);
-      Hij(j + 1, j) = hn;
-      for (int i = 0; i < j; ++i) {
-        const double tt = cn[p][i] * Hij(i, j) + sn[p][i] * Hij(i + 1, j);
-        Hij(i + 1, j) = -sn[p][i] * Hij(i, j) + cn[p][i] * Hij(i + 1, j);
-        Hij(i, j) = tt;
-      }
-      const double rho = std::hypot(Hij(j, j), Hij(j + 1, j));
-      cn[p][j] = Hij(j, j) / rho;
-      sn[p][j] = Hij(j + 1, j) / rho;
-      Hij(j, j) = rho;
-      Hij(j + 1, j) = 0.0;
-      g[p][j + 1] = -sn[p][j] * g[p][j];
-      g[p][j] = cn[p][j] * g[p][j];
-      done_j[p] = j + 1;
-      const double est = std::fabs(g[p][j + 1]);
-      if (!std::isfinite(est)) return berr(BH_ENOCONV, "batched GMRES: non-finite residual");
-      if (est <= rtol * beta[p] || hn == 0.0 || j + 1 >= m) {
-        conv[p] = est <= rtol * beta[p] || hn == 0.0;
+      act[p] = again[p];
+      if (!again[p]) continue;
+      beta[p] = std::sqrt(hd[(size_t)p * cs]);
+      if (!std::isfinite(beta[p])) return berr(BH_ENOCONV, "batched GMRES: non-finite residual");
+      if (!(beta[p] > 0.0)) {
+        conv[p] = 1;
         act[p] = 0;
-        changed = true;
       }
     }
-    if (changed) BCKS(set_active(b, act));
-    BCK(run_vec(b, S.Vw, kScaleInvSqrt, b->d_dots, cs, j + 1, 1.0, j + 1, 0));  // V_{j+1}
   }
-  // x = V y (back substitution on the host), then the true residuals
-  std::vector<double>& coef = S.hcoef;
-  std::fill(coef.begin(), coef.end(), 0.0);
-  int jmax = 0;
-  for (int p = 0; p < P; ++p) {
-    const int jd = done_j[p];
-    jmax = std::max(jmax, jd);
-    for (int i = jd - 1; i >= 0; --i) {
-      double sacc = g[p][i];
-      for (int jj = i + 1; jj < jd; ++jj) sacc -= H[p][(size_t)i * m + jj] * coef[(size_t)p * cs + jj];
-      coef[(size_t)p * cs + i] = sacc / H[p][(size_t)i * m + i];
-    }
-  }
+  // true relative residuals of every problem that ran (r64_L holds b - A x)
   for (int p = 0; p < P; ++p) act[p] = bnorm[p] > 0.0 ? 1 : 0;
   BCKS(set_active(b, act));
-  BCK(cudaMemcpyAsync(b->d_coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice,
-                      b->st));
-  for (int i = 0; i < jmax; ++i) BCK(run_vec(b, S.xV, kAxpyDev, b->d_coef, cs, i, 1.0, 0, i));
-  BCK(run_sweep(b, S.resid_x, 0));
-  BCK(run_sweep(b, S.resid_y, 2));
   BCK(run_dot(b, S.rr, 0));
   BCK(cudaMemcpyAsync(hd.data(), b->d_dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st));
   BCK(cudaStreamSynchronize(b->st));
   bool all_conv = true;
-  b->last_iters = done_j;
+  b->last_iters = total;
   for (int p = 0; p < P; ++p) {
-    iters[p] = done_j[p];
+    iters[p] = total[p];
     relres[p] = bnorm[p] > 0.0 ? std::sqrt(hd[(size_t)p * cs]) / bnorm[p] : 0.0;
     if (bnorm[p] > 0.0 && !conv[p]) all_conv = false;
   }
+  BCKS(signal_user(b));
   if (!all_conv) return berr(BH_ENOCONV, "batched GMRES: some problems did not reach the tolerance");
   return BH_OK;
 }
@@ -1131,15 +1554,16 @@ bh_status bh_batch_solve_host(bh_batch* b, const double* const* b_host, double* 
       b->stage_x.push_back(dx);
     }
   }
+  // the copies run on the caller's stream, which bh_batch_solve waits for
   for (int p = 0; p < b->P; ++p)
     BCK(cudaMemcpyAsync(b->stage_b[p], b_host[p], b->ctx[p]->lv[b->L[p]].g.nd * sizeof(double),
-                        cudaMemcpyHostToDevice, b->st));
+                        cudaMemcpyHostToDevice, b->user));
   bh_status s = bh_batch_solve(b, b->stage_b.data(), b->stage_x.data(), rtol, maxit, iters, relres);
   if (s != BH_OK && s != BH_ENOCONV) return s;
   for (int p = 0; p < b->P; ++p)
     BCK(cudaMemcpyAsync(x_host[p], b->stage_x[p], b->ctx[p]->lv[b->L[p]].g.nd * sizeof(double),
-                        cudaMemcpyDeviceToHost, b->st));
-  BCK(cudaStreamSynchronize(b->st));
+                        cudaMemcpyDeviceToHost, b->user));
+  BCK(cudaStreamSynchronize(b->user));
   return s;
 }
 

@@ -50,7 +50,7 @@ def test_default_params_and_validation(lib):
     p = lib.default_params(2, 3, 4)
     assert (p.dim, p.degree, p.level, p.smoother, p.local_solver) == (2, 3, 4, lib.MVS_COLORED, lib.FDM)
     assert p.pre_steps == 1 and p.post_steps == 1 and p.gmres_restart == 50
-    assert p.gmres_side == lib.LEFT
+    assert p.gmres_side == lib.RIGHT
     assert p.krylov == lib.GMRES
     for bad in [(1, 3, 4), (2, 1, 4), (2, 8, 4), (3, 2, 0)]:
         with pytest.raises(lib.BiharmError):

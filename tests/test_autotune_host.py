@@ -2,6 +2,7 @@
 V-cycle time is a known function of its tiles: the coordinate-descent pass
 of tune_batch, the candidates the library refuses, and the JSON cache."""
 import json
+import types
 
 import pytest
 
@@ -14,8 +15,9 @@ class FakeBatch:
     tiles above `limit[k]` the way the library refuses a tile that does not
     fit in shared memory."""
 
-    def __init__(self, best, limit):
+    def __init__(self, best, limit, precision=0):
         self.best, self.limit = best, limit
+        self.params = [types.SimpleNamespace(precision=precision)]
         self.tiles = {}
         self.timings = 0
 
@@ -34,8 +36,8 @@ def tuner(tmp_path, monkeypatch):
     monkeypatch.setenv("BIHARM_TUNE_CACHE", str(tmp_path / "tiles.json"))
     monkeypatch.setattr(autotune, "_arch", lambda: "sm_103_fake")
     # per-degree starting tiles, as tiles_for would measure them
-    monkeypatch.setattr(autotune, "tiles_for", lambda degrees, refresh=False, verbose=False:
-                        {k: 4 for k in degrees})
+    monkeypatch.setattr(autotune, "tiles_for", lambda degrees, refresh=False, verbose=False,
+                        precision=0: {k: 4 for k in degrees})
     return tmp_path / "tiles.json"
 
 
@@ -58,8 +60,12 @@ def test_cache_is_keyed_by_the_problem_list_and_reused(tuner):
     tiles = autotune.tune_batch(first, problems)
     assert tiles == {3: 8, 4: 2}
     cache = json.load(open(tuner))
-    key = "batch_2.3.5-2.4.4_sm_103_fake"
+    key = "batch_p0_2.3.5-2.4.4_sm_103_fake"
     assert cache[key]["tiles"] == {"3": 8, "4": 2}
+    # the FP32 V-cycle's kernels are tuned apart from the FP64 ones
+    mixed = FakeBatch(best={3: 2, 4: 16}, limit={}, precision=2)
+    assert autotune.tune_batch(mixed, problems) == {3: 2, 4: 16}
+    assert "batch_p2_2.3.5-2.4.4_sm_103_fake" in json.load(open(tuner))
     # same problems in another order: no timing, cached tiles applied
     again = FakeBatch(best={3: 1, 4: 1}, limit={})
     assert autotune.tune_batch(again, list(reversed(problems))) == tiles

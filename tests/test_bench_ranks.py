@@ -138,3 +138,18 @@ def test_table_entries_cover_every_printed_value():
         assert d == (3 if name.startswith("tab3") else 2)
     # the paper's caption: only levels with 5e4 to 1e7 DoFs (2D) were computed
     assert min(e[0] for e in entries if e[4] == 2) >= 5e4
+
+
+def test_cpu_baseline_on_all_degrees_with_a_small_budget():
+    """The CPU baseline leg: the six degrees solved concurrently by spawned
+    oracle processes; with a budget of a second it stops after the first
+    size, and reports that size, its cores and the sizes it did not run."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.cpu_baseline(budget_s=1.0, reps=1)
+    assert r["kind"] == "oracle" and r["value"] > 0
+    assert r["largest_cells"] == 8 and len(r["sizes"]) == 1
+    assert r["cores"] >= 6 and r["host_cpus"] == os.cpu_count()
+    top = r["sizes"][0]
+    assert top["dofs"] == sum((k * 8 + 1) ** 2 for k in range(2, 8))
+    assert top["true_relres_max"] <= 1.0001e-8 and "512^2" in r["not_run"]

@@ -1,5 +1,16 @@
-"""Batched form: every problem's result equals its own single-context solve
-(same iterations, same solution to 1e-9 relative), in any mix."""
+"""Batched form, through the C ABI.
+
+Oracle parity of the kernels the batch runs (the batched sweeps, transfers,
+patch kernels, coarse solve and vector kernels): one batched V-cycle of a
+mixed-degree batch against the oracle's Algorithm 1 per problem (1e-10),
+batched GMRES (right and left) against the oracle's GMRES (iterations +-1,
+1e-8 true residual, solution to 1e-6), the FP32 V-cycle with FP64 defects
+against the FP64 oracle, and one color of the batched MVS kernel inside a
+batch that holds the 2D Q4 problem on 512^2 cells on sampled patches.  At
+the benchmark's sizes the batched solves are checked by a property that holds
+at any size: the true residual evaluated by the oracle's Kronecker operator.
+Further: a problem's result does not depend on the mix, and equals its own
+single-context solve."""
 import numpy as np
 import pytest
 
@@ -7,7 +18,10 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+import oracle_samples  # noqa: E402
 import workload  # noqa: E402
+from oracle import assemble, kron, krylov, mg, smoothers  # noqa: E402
+from oracle.patches import color as color_of  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -17,6 +31,167 @@ def bh():
     import paper_2412_05082_gb300 as m
     m.load()
     return m
+
+
+def cuda(v):
+    return torch.tensor(np.asarray(v), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# a mixed-degree batch small enough for the oracle: every degree, levels 1..4
+MIX = [(2, 2, 4), (2, 3, 3), (2, 4, 3), (2, 5, 2), (2, 6, 2), (2, 7, 2), (2, 3, 1), (2, 2, 2)]
+
+
+def hierarchies():
+    return [mg.Hierarchy(d, k, L) for d, k, L in MIX]
+
+
+def rhs_rough_solution(A, seed):
+    """b = A x* for a seeded x* ~ U[-1, 1]: the right-hand side of the
+    benchmark's solves (the FP64 rounding floor of the true residual is O(eps))."""
+    xs = workload.vector_uniform(A.shape[0], seed)
+    return A @ xs, xs
+
+
+def test_batched_vcycle_matches_oracle_per_problem(bh):
+    Hs = hierarchies()
+    bs = [workload.rhs_uniform(H.A[H.L].shape[0], 200 + i) for i, H in enumerate(Hs)]
+    refs = [H.vcycle(H.L, np.zeros_like(b), b) for H, b in zip(Hs, bs)]
+    with bh.Batch([bh.default_params(d, k, L) for d, k, L in MIX]) as batch:
+        B = [cuda(b) for b in bs]
+        X = [torch.full_like(v, float("nan")) for v in B]
+        batch.vcycle(B, X)
+        for (d, k, L), x, ref in zip(MIX, X, refs):
+            assert relerr(host(x), ref) <= 1e-10, (k, L, relerr(host(x), ref))
+
+
+@pytest.mark.parametrize("side", ["right", "left"])
+def test_batched_solve_matches_oracle_gmres(bh, side):
+    Hs = hierarchies()
+    bs = [rhs_rough_solution(H.A[H.L], 300 + i)[0] if i % 2 == 0 else
+          workload.rhs_uniform(H.A[H.L].shape[0], 300 + i) for i, H in enumerate(Hs)]
+    refs = [krylov.gmres(H.A[H.L], b, H.preconditioner, 1e-8, side=side) for H, b in zip(Hs, bs)]
+    params = [bh.default_params(d, k, L, gmres_side=bh.RIGHT if side == "right" else bh.LEFT)
+              for d, k, L in MIX]
+    with bh.Batch(params) as batch:
+        B = [cuda(b) for b in bs]
+        X = [torch.empty_like(v) for v in B]
+        its, rrs = batch.solve(B, X, 1e-8, 100)
+        for (d, k, L), x, it, rr, (xr, it_ref, hist, rr_ref), H, b in zip(MIX, X, its, rrs, refs,
+                                                                          Hs, bs):
+            assert abs(it - it_ref) <= 1, (k, L, it, it_ref)
+            xg = host(x)
+            assert relerr(xg, xr) <= 1e-6, (k, L)
+            true = np.linalg.norm(b - H.A[H.L] @ xg) / np.linalg.norm(b)
+            assert abs(true - rr) <= 1e-3 * rr + 1e-15, (k, L, true, rr)
+            if side == "right":
+                assert rr <= 1.0001e-8, (k, L, rr)
+
+
+def test_batched_solve_restarts(bh):
+    """GMRES(4) on problems that need more than four iterations: the restarted
+    batch reaches the tolerance like the oracle's restarted GMRES (iterations
+    +-1), and a problem that would need more than maxit iterations reports
+    non-convergence without stopping the others."""
+    probs = [(2, 2, 4), (2, 4, 3), (2, 6, 2)]
+    Hs = [mg.Hierarchy(d, k, L) for d, k, L in probs]
+    bs = [rhs_rough_solution(H.A[H.L], 400 + i)[0] for i, H in enumerate(Hs)]
+    refs = [krylov.gmres(H.A[H.L], b, H.preconditioner, 1e-8, restart=4) for H, b in zip(Hs, bs)]
+    params = [bh.default_params(d, k, L, gmres_restart=4) for d, k, L in probs]
+    with bh.Batch(params) as batch:
+        B = [cuda(b) for b in bs]
+        X = [torch.empty_like(v) for v in B]
+        its, rrs = batch.solve(B, X, 1e-8, 100)
+        for (d, k, L), it, rr, x, (xr, it_ref, _, _) in zip(probs, its, rrs, X, refs):
+            assert it_ref > 4 and abs(it - it_ref) <= 1, (k, L, it, it_ref)
+            assert rr <= 1.0001e-8
+            assert relerr(host(x), xr) <= 1e-6
+        its2, rrs2 = batch.solve(B, X, 1e-8, 3, raise_on_noconv=False)
+        assert its2 == [3, 3, 3] and min(rrs2) > 1e-8
+        with pytest.raises(bh.BiharmError):
+            batch.solve(B, X, 1e-8, 3)
+
+
+def test_batched_mixed_precision_vcycle_and_solve(bh):
+    """The FP32 V-cycle with FP64 defects (BH_MIXED_FP32_R64) in the batch:
+    one V-cycle within 1e-4 of the FP64 oracle's, and flexible GMRES to the
+    1e-8 true residual with at most one iteration more than the oracle's FP64
+    GMRES, the solution within 1e-6 of it."""
+    Hs = hierarchies()
+    bs = [rhs_rough_solution(H.A[H.L], 500 + i)[0] for i, H in enumerate(Hs)]
+    params = [bh.default_params(d, k, L, precision=bh.MIXED_FP32_R64) for d, k, L in MIX]
+    with bh.Batch(params) as batch:
+        B = [cuda(b) for b in bs]
+        X = [torch.empty_like(v) for v in B]
+        batch.vcycle(B, X)
+        for (d, k, L), H, b, x in zip(MIX, Hs, bs, X):
+            ref = H.vcycle(H.L, np.zeros_like(b), b)
+            assert relerr(host(x), ref) <= 1e-4, (k, L, relerr(host(x), ref))
+        its, rrs = batch.solve(B, X, 1e-8, 100)
+        for (d, k, L), H, b, x, it, rr in zip(MIX, Hs, bs, X, its, rrs):
+            xr, it_ref, _, _ = krylov.gmres(H.A[H.L], b, H.preconditioner, 1e-8)
+            assert rr <= 1.0001e-8 and it <= it_ref + 1, (k, L, it, it_ref, rr)
+            assert relerr(host(x), xr) <= 1e-6
+
+
+@pytest.mark.parametrize("color", [0, 5])
+def test_batched_color_with_the_512_cell_problem(bh, color):
+    """One color of the batched MVS kernel in a batch of 2D Q4 on 512^2 cells
+    (checked on 24 sampled patches) with two small problems of other degrees
+    (checked completely against the oracle's sequential MVS over the color)."""
+    probs = [(2, 4, 9), (2, 7, 3), (2, 2, 4)]
+    xs, bs = [], []
+    for i, (d, k, L) in enumerate(probs):
+        n = (k * 2 ** L - 1) ** d
+        xs.append(workload.vector_uniform(n, 60 + i))
+        bs.append(workload.rhs_uniform(n, 70 + i))
+    with bh.Batch([bh.default_params(d, k, L) for d, k, L in probs]) as batch:
+        X = [cuda(x) for x in xs]
+        batch.smooth_colors(X, [cuda(b) for b in bs], color, color + 1)
+        got = [host(x) for x in X]
+    d, k, L = probs[0]
+    oracle_samples.check_color_on_sampled_patches(d, k, 2 ** L, color, xs[0], bs[0], got[0], 1.0)
+    for (d, k, L), x, b, g in zip(probs[1:], xs[1:], bs[1:], got[1:]):
+        N = 2 ** L
+        A = assemble.c0ip_matrix(d, k, N)
+        from oracle.patches import LocalSolvers
+        loc = LocalSolvers(assemble.c0ip_matrix(d, k, N, mixed=False), d, k, N)
+        order = [v for v in smoothers.mvs_order(d, N) if color_of(v) == color]
+        ref = smoothers.mvs_step(A, loc, b, x, 1.0, order=order)
+        assert relerr(g - x, ref - x) <= 1e-10, (k, L)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "r64"])
+def test_batched_sweep_solve_reaches_true_residual(bh, precision):
+    """The benchmark's workload (2D Q2-Q4 on 512^2 and Q5-Q7 on 256^2 cells,
+    b = A x* with x* ~ U[-1, 1]) solved as one batch by right-preconditioned
+    GMRES: the true residual of every returned solution, evaluated by the
+    oracle's Kronecker operator, is at most 1e-8 (plus the rounding of its own
+    evaluation), and equals the residual the batch reports."""
+    probs = workload.SWEEP_2D
+    ops = [kron.KronOperator(d, k, N) for d, k, N in probs]
+    xstar = [workload.vector_uniform((k * N - 1) ** d, k) for d, k, N in probs]
+    bs = [A @ xs for A, xs in zip(ops, xstar)]
+    prec = bh.FP64 if precision == "fp64" else bh.MIXED_FP32_R64
+    params = [bh.default_params(d, k, workload.level_of(N), precision=prec) for d, k, N in probs]
+    with bh.Batch(params) as batch:
+        B = [cuda(b) for b in bs]
+        X = [torch.empty_like(v) for v in B]
+        its, rrs = batch.solve(B, X, 1e-8, 100)
+        got = [host(x) for x in X]
+    for (d, k, N), A, b, x, it, rr in zip(probs, ops, bs, got, its, rrs):
+        true = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert rr <= 1.0001e-8 and true <= 1.01e-8, (k, N, rr, true)
+        assert abs(true - rr) <= 1e-2 * rr, (k, N, true, rr)
+        assert 1 <= it <= 40, (k, N, it)
 
 
 def single(bh, d, k, L, b):
@@ -82,6 +257,11 @@ def test_batch_tiles_and_graph(bh):
             batch.set_tile(7, 33)
     with pytest.raises(bh.BiharmError):
         bh.Batch([bh.default_params(3, 2, 3)])      # batched form is 2D
+    with pytest.raises(bh.BiharmError):              # one precision per batch
+        bh.Batch([bh.default_params(2, 2, 3),
+                  bh.default_params(2, 3, 3, precision=bh.MIXED_FP32_R64)])
+    with pytest.raises(bh.BiharmError):              # FP32 V-cycle needs right GMRES
+        bh.Batch([bh.default_params(2, 2, 3, precision=bh.MIXED_FP32_R64, gmres_side=bh.LEFT)])
 
 
 def test_batch_autotuner_keeps_results(bh, tmp_path, monkeypatch):

@@ -4,7 +4,6 @@ arithmetic: FP64 sums of O(100) terms each carry ~1e-15 relative rounding):
 apply_A and transfers 1e-12, one smoothing step and one V-cycle 1e-10, solves
 reach the same 1e-8 relative residual with iteration counts within +-1."""
 import functools
-import itertools
 
 import numpy as np
 import pytest
@@ -13,6 +12,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+import oracle_samples  # noqa: E402
 import workload  # noqa: E402
 from oracle import assemble, kron, krylov, mg, smoothers  # noqa: E402
 from oracle.patches import LocalSolvers  # noqa: E402
@@ -476,13 +476,6 @@ def test_full_size_apply_and_sampled_avs(bh):
         assert abs(got[idx] - expect) <= 1e-10 * max(abs(expect), np.abs(r).max() * 1e-3)
 
 
-def along(P, X, a):
-    """Rectangular 1D matrix P applied along method axis a of X (axis 0 = x,
-    numpy's last axis)."""
-    ax = X.ndim - 1 - a
-    return np.moveaxis(np.moveaxis(X, ax, -1) @ P.T, -1, ax)
-
-
 @pytest.mark.parametrize("d,k,N", [(3, 7, 64), (3, 3, 128), (2, 7, 256)])
 def test_full_size_apply_on_sampled_rows(bh, d, k, N):
     """apply_A at the largest sweep sizes (3D Q7 on 64^3 cells: 89 M unknowns;
@@ -514,7 +507,7 @@ def test_full_size_apply_on_sampled_rows(bh, d, k, N):
         for cf, ops in terms:
             T = xw
             for a, P in enumerate(ops):
-                T = along(P[np.ix_([c[a]], win[a])], T, a)
+                T = oracle_samples.along(P[np.ix_([c[a]], win[a])], T, a)
             y += cf * T.item()
         assert abs(got[idx] - y) <= 1e-12 * scale, (idx, got[idx], y)
 
@@ -528,9 +521,7 @@ def test_full_size_mvs_color_on_sampled_patches(bh, d, k, N, color):
     color, x_v + omega A~_v^-1 R_v (b - A x) from the oracle's Kronecker
     factors, patch by patch; every node outside the color's patches
     unchanged, bit for bit."""
-    from oracle.patches import color as color_of
     L = workload.level_of(N)
-    n1 = k * N - 1
     omega = smoothers.default_omega("mvs", d, "inexact")
     with make_ctx(bh, d, k, L) as ctx:
         n = ctx.num_unknowns(L)
@@ -539,42 +530,7 @@ def test_full_size_mvs_color_on_sampled_patches(bh, d, k, N, color):
         X = cuda(x)
         ctx.smooth_colors(L, X, cuda(b), color, color + 1)
         got = host(X)
-    M1, L1, B1 = (np.asarray(m.todense()) if hasattr(m, "todense") else np.asarray(m)
-                  for m in kron.global_1d(k, N))
-    terms = ([(1.0, (B1, M1)), (1.0, (M1, B1)), (2.0, (L1, L1))] if d == 2 else
-             [(1.0, (B1, M1, M1)), (1.0, (M1, B1, M1)), (1.0, (M1, M1, B1)),
-              (2.0, (L1, L1, M1)), (2.0, (M1, L1, L1)), (2.0, (L1, M1, L1))])
-    X0 = x.reshape((n1,) * d)          # numpy axes: slowest first, axis 0 = x is last
-    G = got.reshape((n1,) * d)
-    # which nodes the color's patches cover
-    covered = np.zeros((n1,) * d, dtype=bool)
-    verts = [v for v in itertools.product(range(1, N), repeat=d) if color_of(v) == color]
-    for v in verts:
-        covered[tuple(slice(k * (v[a] - 1), k * (v[a] + 1) - 1) for a in reversed(range(d)))] = True
-    assert np.array_equal(G[~covered], X0[~covered])
-    rng = np.random.default_rng(11)
-    for vi in rng.choice(len(verts), 24, replace=False):
-        v = verts[vi]
-        rows = [np.arange(k * (v[a] - 1), k * (v[a] + 1) - 1) for a in range(d)]
-        # the band of every patch row stays inside k(v-3) .. k(v+3) (zeros beyond its reach)
-        win = [np.arange(max(0, k * (v[a] - 3)), min(n1, k * (v[a] + 3))) for a in range(d)]
-        xw = X0[np.ix_(*[win[a] for a in reversed(range(d))])]
-        Ax = np.zeros([len(rows[a]) for a in reversed(range(d))])
-        At = 0.0
-        for c, ops in terms:
-            T = xw
-            for a, P in enumerate(ops):
-                T = along(P[np.ix_(rows[a], win[a])], T, a)
-            Ax = Ax + c * T
-            if c == 1.0:       # the separable local matrix drops the mixed terms
-                blk = np.ones((1, 1))
-                for a in reversed(range(d)):
-                    blk = np.kron(blk, ops[a][np.ix_(rows[a], rows[a])])
-                At = At + blk
-        sel = np.ix_(*[rows[a] for a in reversed(range(d))])
-        r = (b.reshape((n1,) * d)[sel] - Ax).ravel()
-        expect = X0[sel].ravel() + omega * np.linalg.solve(At, r)
-        assert relerr(G[sel].ravel() - X0[sel].ravel(), expect - X0[sel].ravel()) <= 1e-10, v
+    oracle_samples.check_color_on_sampled_patches(d, k, N, color, x, b, got, omega)
 
 
 def test_edge_cases(bh):
