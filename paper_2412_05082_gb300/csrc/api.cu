@@ -122,12 +122,11 @@ bh_status patches_t(bh_ctx* c, int l, const T* r, T* x, int lo, int hi, bool ato
   const double sc = c->p.omega * L.pscale;
   if (c->p.local_solver == BH_EXACT && c->exact_gemm) {
     // per color in [lo, hi) and run of one type combination: gather the patch
-    // tensors as columns, Y = sc Ainv R (cuBLAS), scatter-add Y
+    // tensors as columns, Y = sc Ainv R (dense product, gemm.cuh), scatter-add Y
     const int md = (int)std::lround(std::pow(2 * c->p.degree - 1, c->p.dim));
     const size_t msz = (size_t)md * md;
     T* R = TypeOf<T>::gR(c);
     T* Y = TypeOf<T>::gY(c);
-    const T alpha = (T)sc, beta = T(0);
     for (int col = 0; col < c->ncolors(); ++col) {
       if (L.coff[col] < lo || L.coff[col + 1] > hi) continue;
       for (const auto& run : L.runs[col]) {
@@ -135,16 +134,7 @@ bh_status patches_t(bh_ctx* c, int l, const T* r, T* x, int lo, int hi, bool ato
         const int cnt = run[1];
         const T* Ainv = TypeOf<T>::ainv(c) + (size_t)run[2] * msz;
         CK(Ops<T>::patch_gather(L.g, r, vs, cnt, R, c->st));
-        cublasStatus_t bs;
-        if constexpr (std::is_same<T, double>::value)
-          bs = cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, md, cnt, md, &alpha, Ainv, md, R,
-                           md, &beta, Y, md);
-        else
-          bs = cublasSgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, md, cnt, md, &alpha, Ainv, md, R,
-                           md, &beta, Y, md);
-        if (bs != CUBLAS_STATUS_SUCCESS)
-          return fail(BH_ECUDA, "cuBLAS GEMM of the exact local solver failed (status " +
-                                    std::to_string((int)bs) + ")");
+        CK(Ops<T>::gemm(md, cnt, sc, Ainv, R, Y, c->st));
         CK(Ops<T>::patch_scatter(L.g, Y, vs, cnt, x, atomic, c->st));
       }
     }
@@ -311,7 +301,6 @@ void destroy_ctx(bh_ctx* c) {
   if (c->hdots) cudaFreeHost(c->hdots);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
-  if (c->blas) cublasDestroy(c->blas);
   if (c->tab64) Ops<double>::free_tables(c->tab64, c->p.degree);
   if (c->tab32) Ops<float>::free_tables(c->tab32, c->p.degree);
   delete c;
@@ -800,9 +789,6 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
       return bail(status);
     if (mx && ((status = dmalloc(c, &c->gR32, cols)) || (status = dmalloc(c, &c->gY32, cols))))
       return bail(status);
-    if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetStream(c->blas, c->st) != CUBLAS_STATUS_SUCCESS)
-      return bail(fail(BH_ECUDA, "cuBLAS handle for the exact local solver"));
   }
   if (p.local_solver == BH_EXACT) {
     const int slots = d == 2 ? 16 : 64;

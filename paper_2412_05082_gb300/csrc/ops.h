@@ -70,6 +70,11 @@ struct Ops {
   static cudaError_t patch_scatter(const LevelGeom& g, const T* Y, const int* verts, int count,
                                    T* x, bool atomic, cudaStream_t st);
 
+  // Y = alpha A R: A md x md, R and Y md x cnt, all column-major (the dense
+  // product of the exact local solver on a run of gathered patch tensors).
+  static cudaError_t gemm(int md, int cnt, double alpha, const T* A, const T* R, T* Y,
+                          cudaStream_t st);
+
   // xf += P xc (embedding), fine geometry given; s0, s1 scratch of fine nd each.
   static cudaError_t prolongate_add(const void* tab, const LevelGeom& fine, const T* xc, T* xf,
                                     T* s0, T* s1, cudaStream_t st);

@@ -34,10 +34,12 @@ def color_vertices(d, N, color):
 
 
 def check_color_on_sampled_patches(d, k, N, color, x, b, got, omega, samples=24, seed=11,
-                                   tol=1e-10):
+                                   tol=1e-10, exact=False):
     """One color of the colored MVS (Sec. 3) applied to x gave `got`: every node
     outside the color's patches is unchanged bit for bit, and on `samples`
-    sampled patches x_v + omega A~_v^-1 R_v (b - A x) matches to `tol`."""
+    sampled patches x_v + omega A~_v^-1 R_v (b - A x) matches to `tol`, with
+    the separable local matrix A~_v of Eq. (localsolverbila), or with the exact
+    A_v = R_v A R_v^T (all terms) when exact is set."""
     n1 = k * N - 1
     terms = factors(d, k, N)
     X0 = x.reshape((n1,) * d)          # numpy axes: slowest first, axis 0 = x is last
@@ -61,11 +63,11 @@ def check_color_on_sampled_patches(d, k, N, color, x, b, got, omega, samples=24,
             for a, P in enumerate(ops):
                 T = along(P[np.ix_(rows[a], win[a])], T, a)
             Ax = Ax + c * T
-            if c == 1.0:       # the separable local matrix drops the mixed terms
+            if c == 1.0 or exact:   # the separable local matrix drops the mixed terms
                 blk = np.ones((1, 1))
                 for a in reversed(range(d)):
                     blk = np.kron(blk, ops[a][np.ix_(rows[a], rows[a])])
-                At = At + blk
+                At = At + c * blk
         sel = np.ix_(*[rows[a] for a in reversed(range(d))])
         r = (b.reshape((n1,) * d)[sel] - Ax).ravel()
         expect = X0[sel].ravel() + omega * np.linalg.solve(At, r)

@@ -115,7 +115,10 @@ SMOOTH_CASES = [
     (2, 3, 16, "mvs", "inexact"), (2, 5, 8, "mvs", "inexact"), (2, 7, 8, "mvs", "inexact"),
     # exact local solvers: per-patch products (3D k = 4) and, for patches of
     # m^3 >= 512 unknowns, one dense product per run of a type combination
+    # (the library's own FP64 tensor-core GEMM, gemm.cuh)
     (3, 4, 4, "mvs", "exact"), (3, 5, 4, "avs", "exact"), (3, 5, 2, "mvs", "exact"),
+    (3, 5, 4, "mvs", "exact"), (3, 6, 2, "mvs", "exact"), (3, 6, 4, "mvs", "exact"),
+    (3, 7, 2, "mvs", "exact"),
 ]
 
 
@@ -268,7 +271,7 @@ def test_solve_resumes_from_a_guess(bh, kw):
 
 def test_mixed_precision_exact_local_solver_3d(bh):
     """3D k = 5 with exact local solvers (one dense product per run of a type
-    combination, cuBLAS DGEMM / SGEMM): FP64 and the FP32 V-cycle with FP64
+    combination, the library's FP64 and FP32 GEMM): FP64 and the FP32 V-cycle with FP64
     defects reach the 1e-8 true residual, at most one iteration apart, both
     within 1e-6 of the dense solve."""
     d, k, L = 3, 5, 2
@@ -531,6 +534,28 @@ def test_full_size_mvs_color_on_sampled_patches(bh, d, k, N, color):
         ctx.smooth_colors(L, X, cuda(b), color, color + 1)
         got = host(X)
     oracle_samples.check_color_on_sampled_patches(d, k, N, color, x, b, got, omega)
+
+
+@pytest.mark.parametrize("k,color,samples", [(5, 0, 24), (6, 9, 12), (7, 3, 8)])
+def test_full_size_exact_mvs_color_on_sampled_patches(bh, k, color, samples):
+    """One color of the colored MVS with exact local solvers at the 3D sweep
+    size (64^3 cells, m^3 = 729 .. 2197 unknowns per patch: one dense product
+    per run of patches of a type combination, by the library's FP64 GEMM):
+    on sampled patches x_v + omega A_v^-1 R_v (b - A x) with the exact local
+    matrix from the oracle's Kronecker factors; every other node unchanged."""
+    d, N = 3, 64
+    L = workload.level_of(N)
+    omega = smoothers.default_omega("mvs", d, "exact")
+    with make_ctx(bh, d, k, L, local_solver=bh.EXACT) as ctx:
+        n = ctx.num_unknowns(L)
+        x = workload.vector_uniform(n, 5)
+        b = workload.rhs_uniform(n, 6)
+        X = cuda(x)
+        ctx.smooth_colors(L, X, cuda(b), color, color + 1)
+        got = host(X)
+        del X
+    oracle_samples.check_color_on_sampled_patches(d, k, N, color, x, b, got, omega,
+                                                  samples=samples, exact=True)
 
 
 def test_edge_cases(bh):
