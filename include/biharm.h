@@ -375,8 +375,9 @@ bh_status bh_server_destroy(bh_server* server);
  * and forbids allocation while it executes, or a latency-critical loop that
  * cannot afford the synchronization of cudaMalloc.  The paper has no
  * counterpart; it is a deployment variant of the apply_A kernel.
- *  - Needs no context and allocates nothing: the operator tables are built on
- *    the host stack per call and the sweep intermediates live in one static
+ *  - Needs no context and allocates nothing, on the device or on the host
+ *    heap: the operator tables are built once per (degree, gamma) into static
+ *    host storage and reused, and the sweep intermediates live in one static
  *    device array of 64 MiB (8 Mi doubles) that every GPU loading the library
  *    holds until the process exits.
  *  - Size limit: 3 (2D) or 6 (3D) times n^d must fit in that array, i.e. at
@@ -389,7 +390,9 @@ bh_status bh_server_destroy(bh_server* server);
  *    (other streams, other host threads) race and must be serialized by the
  *    caller.  Nothing in the array needs to start at zero.
  *  - The first call on a device resolves the array's device address (with
- *    that device current); make that first call before any stream capture. */
+ *    that device current); make that first call before any stream capture.
+ *    A cudaDeviceReset of the device invalidates the resolved address without
+ *    the library noticing: do not reset a device between calls. */
 bh_status bh_apply_A_noalloc(int dim, int degree, int level, double gamma,
                              const double* x_dev, double* y_dev, void* stream);
 

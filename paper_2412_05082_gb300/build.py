@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbiharm.so")
 SOURCES = ["inst_f64.cu", "inst_f32.cu", "vec.cu", "api.cu", "setup.cpp", "noalloc.cu", "batch.cu",
-           "serve.cpp", "probe.cu"]
+           "serve.cpp", "probe.cu", "gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -122,7 +122,7 @@ bh_status patches_t(bh_ctx* c, int l, const T* r, T* x, int lo, int hi, bool ato
   const double sc = c->p.omega * L.pscale;
   if (c->p.local_solver == BH_EXACT && c->exact_gemm) {
     // per color in [lo, hi) and run of one type combination: gather the patch
-    // tensors as columns, Y = sc Ainv R (dense product, gemm.cuh), scatter-add Y
+    // tensors as columns, Y = sc Ainv R (dense product, gemm.cu), scatter-add Y
     const int md = (int)std::lround(std::pow(2 * c->p.degree - 1, c->p.dim));
     const size_t msz = (size_t)md * md;
     T* R = TypeOf<T>::gR(c);

@@ -13,7 +13,7 @@
 namespace bh {
 
 // Patch size m^d from which the exact local solver multiplies the patches of a
-// run with its dense inverse as one matrix product (gemm.cuh): the per-patch
+// run with its dense inverse as one matrix product (gemm.cu): the per-patch
 // product streams the whole inverse from L2 for every few patches.  Measured
 // on one 3D MVS step: at m^d = 343 (k = 4) the per-patch kernel is still 15 %
 // faster; at 729 and above the product is the only usable form.
@@ -53,7 +53,7 @@ struct bh_ctx {
   double* ainv64 = nullptr;
   float* ainv32 = nullptr;
   // exact local solver on large patches (m^d >= kExactGemmMin): the patch
-  // tensors of one run as matrix columns, multiplied by the inverse (gemm.cuh)
+  // tensors of one run as matrix columns, multiplied by the inverse (gemm.cu)
   bool exact_gemm = false;
   int gemm_cols = 0;  // largest run
   double *gR64 = nullptr, *gY64 = nullptr;

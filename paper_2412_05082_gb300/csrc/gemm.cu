@@ -19,14 +19,15 @@
 // Out-of-range rows, columns and k are zero-filled in shared memory, so any
 // m^d and cnt work; element-wise 4- or 8-byte copies need no alignment beyond
 // the value's own (m^d is odd).
-#pragma once
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "ops.h"
 
 namespace bh {
+namespace {
 
 __device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
@@ -200,6 +201,30 @@ __global__ void __launch_bounds__(GemmF32Cfg::THREADS) gemm_f32_kernel(int md, i
       if (gn < cnt) Y[(int64_t)gn * md + gm] = alpha * acc[i][j];
     }
   }
+}
+
+}  // namespace
+
+cudaError_t gemm_f64(int md, int cnt, double alpha, const double* A, const double* R, double* Y,
+                     cudaStream_t st) {
+  if (md <= 0 || cnt <= 0) return cudaSuccess;
+  using C = GemmF64Cfg;
+  const dim3 grid((unsigned)((md + C::BM - 1) / C::BM), (unsigned)((cnt + C::BN - 1) / C::BN));
+  if (grid.y > 65535u) return cudaErrorInvalidValue;
+  gemm_f64_kernel<<<grid, C::THREADS, 0, st>>>(md, cnt, alpha, A, R, Y);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_f32(int md, int cnt, float alpha, const float* A, const float* R, float* Y,
+                     cudaStream_t st) {
+  if (md <= 0 || cnt <= 0) return cudaSuccess;
+  using C = GemmF32Cfg;
+  const dim3 grid((unsigned)((md + C::BM - 1) / C::BM), (unsigned)((cnt + C::BN - 1) / C::BN));
+  if (grid.y > 65535u) return cudaErrorInvalidValue;
+  gemm_f32_kernel<<<grid, C::THREADS, 0, st>>>(md, cnt, alpha, A, R, Y);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
 }
 
 }  // namespace bh

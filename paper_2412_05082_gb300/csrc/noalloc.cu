@@ -4,8 +4,9 @@
 // operator: a plugin running inside a host framework that owns every device
 // allocation and forbids its plugins to allocate while executing, or a
 // latency-critical loop that cannot afford cudaMalloc's implicit device
-// synchronization.  This entry point serves them.  It needs no context: the
-// kernel-parameter tables are built on the host stack for every call, and the
+// synchronization.  This entry point serves them.  It needs no context and no
+// heap: the kernel-parameter tables are built by the heap-free 1D core into
+// static host storage (once per degree and penalty, then reused), and the
 // sweep intermediates (three arrays of n^d values in 2D, six in 3D) live in
 // the file-scope device array below, which every GPU that loads the library
 // holds (64 MiB) until the process exits.
@@ -21,6 +22,8 @@
 // with cudaGetSymbolAddress while that device is current (the host-side name
 // of the array is only a stand-in, not a device address) and keeps it for the
 // later calls on that device.  Make that first call before any stream capture.
+// A cudaDeviceReset of that device invalidates the kept address, and the
+// library does not notice it: do not reset a device between calls.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,6 +34,7 @@
 
 #include "biharm.h"
 #include "kernels.cuh"
+#include "line1d.h"
 
 namespace bh {
 void set_last_error(const std::string& msg);  // api.cu
@@ -54,168 +58,41 @@ bh_status err(bh_status s, const char* msg) {
 }
 
 // ---- host tables without heap allocation (cells of size 1) ------------------
-constexpr int kMaxNodes = 7 * kMaxK + 1;
-
-void legendre(int n, double x, double& pn, double& pm) {
-  double p0 = 1.0, p1 = x;
-  if (n == 0) { pn = 1.0; pm = 0.0; return; }
-  for (int m = 1; m < n; ++m) {
-    const double p2 = ((2.0 * m + 1.0) * x * p1 - m * p0) / (m + 1.0);
-    p0 = p1;
-    p1 = p2;
-  }
-  pn = p1;
-  pm = p0;
-}
-
-void gll(int k, double* z) {  // Gauss-Lobatto-Legendre points on [0, 1]
-  z[0] = -1.0;
-  z[k] = 1.0;
-  for (int j = 1; j < k; ++j) {
-    double t = -std::cos(M_PI * j / k);
-    for (int it = 0; it < 100; ++it) {
-      double pn, pm;
-      legendre(k, t, pn, pm);
-      const double d1 = k * (t * pn - pm) / (t * t - 1.0);
-      const double d2 = (2.0 * t * d1 - k * (k + 1.0) * pn) / (1.0 - t * t);
-      const double dt = d1 / d2;
-      t -= dt;
-      if (std::fabs(dt) < 1e-17) break;
-    }
-    z[j] = t;
-  }
-  for (int j = 0; j <= k; ++j) z[j] = 0.5 * (z[j] + 1.0);
-  z[0] = 0.0;
-  z[k] = 1.0;
-}
-
-void gauss(int q, double* x, double* w) {  // Gauss-Legendre on [0, 1]
-  for (int j = 0; j < q; ++j) {
-    double t = std::cos(M_PI * (j + 0.75) / (q + 0.5)), d1 = 1.0, pn, pm;
-    for (int it = 0; it < 100; ++it) {
-      legendre(q, t, pn, pm);
-      d1 = q * (t * pn - pm) / (t * t - 1.0);
-      const double dt = pn / d1;
-      t -= dt;
-      if (std::fabs(dt) < 1e-17) break;
-    }
-    legendre(q, t, pn, pm);
-    d1 = q * (t * pn - pm) / (t * t - 1.0);
-    x[j] = 0.5 * (t + 1.0);
-    w[j] = 1.0 / ((1.0 - t * t) * d1 * d1);
-  }
-}
-
-double lag(const double* z, int n, int i, double x, int deriv) {  // Lagrange basis derivative
-  auto fac = [&](int j) { return (x - z[j]) / (z[i] - z[j]); };
-  double s = 0.0;
-  if (deriv == 0) {
-    s = 1.0;
-    for (int j = 0; j < n; ++j)
-      if (j != i) s *= fac(j);
-  } else if (deriv == 1) {
-    for (int m = 0; m < n; ++m) {
-      if (m == i) continue;
-      double p = 1.0 / (z[i] - z[m]);
-      for (int j = 0; j < n; ++j)
-        if (j != i && j != m) p *= fac(j);
-      s += p;
-    }
-  } else {
-    for (int m = 0; m < n; ++m) {
-      if (m == i) continue;
-      for (int l = 0; l < n; ++l) {
-        if (l == i || l == m) continue;
-        double p = 1.0 / ((z[i] - z[m]) * (z[i] - z[l]));
-        for (int j = 0; j < n; ++j)
-          if (j != i && j != m && j != l) p *= fac(j);
-        s += p;
-      }
-    }
-  }
-  return s;
-}
-
-// Global 1D M, L, B on a line of `cells` unit cells (Eq. (matrix1d) plus the
-// face points of Eq. (ev)), nodes 0..k*cells, leading dimension kMaxNodes.
-void line_1d(int k, double gamma, int cells, double (*M)[kMaxNodes], double (*L)[kMaxNodes],
-             double (*B)[kMaxNodes]) {
-  double z[kMaxK + 1], x[kMaxK + 2], w[kMaxK + 2];
-  gll(k, z);
-  gauss(k + 2, x, w);
-  const int c1 = k + 1, n = k * cells + 1;
-  double cM[kMaxK + 1][kMaxK + 1] = {}, cL[kMaxK + 1][kMaxK + 1] = {}, cB[kMaxK + 1][kMaxK + 1] = {};
-  for (int q = 0; q < k + 2; ++q)
-    for (int i = 0; i < c1; ++i)
-      for (int j = 0; j < c1; ++j) {
-        cM[i][j] += w[q] * lag(z, c1, i, x[q], 0) * lag(z, c1, j, x[q], 0);
-        cL[i][j] += w[q] * lag(z, c1, i, x[q], 1) * lag(z, c1, j, x[q], 1);
-        cB[i][j] += w[q] * lag(z, c1, i, x[q], 2) * lag(z, c1, j, x[q], 2);
-      }
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) M[i][j] = L[i][j] = B[i][j] = 0.0;
-  for (int c = 0; c < cells; ++c)
-    for (int i = 0; i < c1; ++i)
-      for (int j = 0; j < c1; ++j) {
-        M[k * c + i][k * c + j] += cM[i][j];
-        L[k * c + i][k * c + j] += cL[i][j];
-        B[k * c + i][k * c + j] += cB[i][j];
-      }
-  for (int f = 0; f <= cells; ++f) {  // jump = sum of outward derivatives, mean = half sum
-    int ids[2 * kMaxK + 2], cnt = 0;
-    double J[2 * kMaxK + 2], Mu[2 * kMaxK + 2];
-    const bool interior = f > 0 && f < cells;
-    if (f > 0)
-      for (int i = 0; i < c1; ++i, ++cnt) {
-        ids[cnt] = k * (f - 1) + i;
-        J[cnt] = lag(z, c1, i, 1.0, 1);
-        Mu[cnt] = lag(z, c1, i, 1.0, 2) * (interior ? 0.5 : 1.0);
-      }
-    if (f < cells)
-      for (int i = 0; i < c1; ++i, ++cnt) {
-        ids[cnt] = k * f + i;
-        J[cnt] = -lag(z, c1, i, 0.0, 1);
-        Mu[cnt] = lag(z, c1, i, 0.0, 2) * (interior ? 0.5 : 1.0);
-      }
-    for (int a = 0; a < cnt; ++a)
-      for (int b = 0; b < cnt; ++b)
-        B[ids[a]][ids[b]] += gamma * J[a] * J[b] - J[a] * Mu[b] - Mu[a] * J[b];
-  }
-}
-
-// band row t = -2k..2k of row g of a line of `cells` cells; ghost columns zero
-template <int K>
-void class_row(double (*P)[kMaxNodes], int cells, int g, double* row) {
-  for (int t = -2 * K; t <= 2 * K; ++t) {
-    const int col = g + t;
-    row[t + 2 * K] = (col >= 1 && col <= K * cells - 1) ? P[g][col] : 0.0;
-  }
-}
+// Built by the heap-free 1D core (line1d.h) into static host storage, and
+// cached per degree for the last penalty gamma: both are guarded by
+// g_scratch_mutex, so a call reuses the table of the previous call with the
+// same (degree, gamma) and only a change of gamma rebuilds it.
+constexpr int kLineNodes = line1d::kMaxLineNodes;
+double g_line[6][kLineNodes * kLineNodes];  // M, L, B of the 7-cell and the 2-cell line
+double g_class[3][(3 * kMaxK + 1) * (4 * kMaxK + 1)];
 
 template <int K>
-void build_optab(double gamma, OpTab<double, K>& tab) {
-  static_assert(7 * K + 1 <= kMaxNodes, "line too long");
-  double M[kMaxNodes][kMaxNodes], L[kMaxNodes][kMaxNodes], B[kMaxNodes][kMaxNodes];
-  line_1d(K, gamma, 7, M, L, B);  // canonical rows 3K..4K-1, left 1..K, right 6K..7K-1
-  for (int q = 0; q < K; ++q) {
-    class_row<K>(M, 7, 3 * K + q, tab.M[q]);
-    class_row<K>(L, 7, 3 * K + q, tab.L[q]);
-    class_row<K>(B, 7, 3 * K + q, tab.B[q]);
+struct CachedTab {
+  double gamma = 0.0;  // 0: not built yet
+  OpTab<double, K> tab;
+};
+template <int K>
+CachedTab<K> g_tab;
+
+// The operator's row-class tables for (K, gamma); g_scratch_mutex held.
+template <int K>
+const OpTab<double, K>& optab(double gamma) {
+  CachedTab<K>& c = g_tab<K>;
+  if (c.gamma != gamma) {
+    const int n7 = 7 * K + 1, n2 = 2 * K + 1, bw = 4 * K + 1;
+    line1d::line_matrices(K, gamma, 7, g_line[0], g_line[1], g_line[2], n7);
+    line1d::line_matrices(K, gamma, 2, g_line[3], g_line[4], g_line[5], n2);
+    line1d::class_tables(K, g_line[0], g_line[1], g_line[2], n7, g_line[3], g_line[4], g_line[5],
+                         n2, g_class[0], g_class[1], g_class[2]);
+    for (int cl = 0; cl < 3 * K + 1; ++cl)
+      for (int t = 0; t < bw; ++t) {
+        c.tab.M[cl][t] = g_class[0][cl * bw + t];
+        c.tab.L[cl][t] = g_class[1][cl * bw + t];
+        c.tab.B[cl][t] = g_class[2][cl * bw + t];
+      }
+    c.gamma = gamma;
   }
-  for (int g = 1; g <= K; ++g) {
-    class_row<K>(M, 7, g, tab.M[K + g - 1]);
-    class_row<K>(L, 7, g, tab.L[K + g - 1]);
-    class_row<K>(B, 7, g, tab.B[K + g - 1]);
-  }
-  for (int g = 6 * K; g <= 7 * K - 1; ++g) {
-    class_row<K>(M, 7, g, tab.M[2 * K + g - 6 * K]);
-    class_row<K>(L, 7, g, tab.L[2 * K + g - 6 * K]);
-    class_row<K>(B, 7, g, tab.B[2 * K + g - 6 * K]);
-  }
-  line_1d(K, gamma, 2, M, L, B);  // N = 2: the middle vertex touches both faces
-  class_row<K>(M, 2, K, tab.M[3 * K]);
-  class_row<K>(L, 2, K, tab.L[3 * K]);
-  class_row<K>(B, 2, K, tab.B[3 * K]);
+  return c.tab;
 }
 
 template <int K, int KIND>
@@ -227,11 +104,11 @@ cudaError_t sweep(const OpTab<double, K>& tab, const SweepArgs<double>& a, cudaS
   return cudaGetLastError();
 }
 
+// the sweeps of y = A_l x; g_scratch_mutex held (the cached table)
 template <int K>
 cudaError_t apply_static(int d, int N, double gamma, const double* x, double* y, double* scr,
                          cudaStream_t st) {
-  OpTab<double, K> tab;
-  build_optab<K>(gamma, tab);
+  const OpTab<double, K>& tab = optab<K>(gamma);
   const int n = K * N - 1;
   const int64_t nd = d == 2 ? (int64_t)n * n : (int64_t)n * n * n;
   SweepArgs<double> a{};
@@ -302,20 +179,19 @@ extern "C" bh_status bh_apply_A_noalloc(int dim, int degree, int level, double g
     cudaGetLastError();
     return err(BH_ECUDA, "bh_apply_A_noalloc: no usable current CUDA device");
   }
-  double* scr;
-  {
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_dev[dev]) {  // once per device, with that device current
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-      if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        return err(BH_ECUDA, "bh_apply_A_noalloc: cudaGetSymbolAddress of the scratch array failed");
-      }
-      g_scratch_dev[dev] = static_cast<double*>(p);
+  // one lock for the device address, the cached host table and the launches
+  // (the launch copies the table into its kernel parameters)
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_dev[dev]) {  // once per device, with that device current
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return err(BH_ECUDA, "bh_apply_A_noalloc: cudaGetSymbolAddress of the scratch array failed");
     }
-    scr = g_scratch_dev[dev];
+    g_scratch_dev[dev] = static_cast<double*>(p);
   }
+  double* scr = g_scratch_dev[dev];
   const cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaErrorInvalidValue;
   switch (degree) {

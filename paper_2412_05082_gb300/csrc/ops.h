@@ -91,6 +91,13 @@ struct Ops {
                                 cudaStream_t st);
 };
 
+// ---- dense products of the exact local solver (gemm.cu) ----------------------
+// Y = alpha A R: A md x md, R and Y md x cnt, all column-major.
+cudaError_t gemm_f64(int md, int cnt, double alpha, const double* A, const double* R, double* Y,
+                     cudaStream_t st);
+cudaError_t gemm_f32(int md, int cnt, float alpha, const float* A, const float* R, float* Y,
+                     cudaStream_t st);
+
 // ---- vector kernels (FP64 unless noted) -------------------------------------
 // Deterministic dot product: partial sums per block, then one block in fixed order.
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs

@@ -6,7 +6,6 @@
 #include <new>
 #include <vector>
 
-#include "gemm.cuh"
 #include "kernels.cuh"
 #include "mvs.cuh"
 #include "mvs3.cuh"
@@ -453,20 +452,10 @@ cudaError_t Ops<T>::patch_scatter(const LevelGeom& g, const T* Y, const int* ver
 template <typename T>
 cudaError_t Ops<T>::gemm(int md, int cnt, double alpha, const T* A, const T* R, T* Y,
                          cudaStream_t st) {
-  if (md <= 0 || cnt <= 0) return cudaSuccess;
-  if constexpr (sizeof(T) == 8) {
-    using C = GemmF64Cfg;
-    const dim3 grid((unsigned)((md + C::BM - 1) / C::BM), (unsigned)((cnt + C::BN - 1) / C::BN));
-    if (grid.y > 65535u) return cudaErrorInvalidValue;
-    gemm_f64_kernel<<<grid, C::THREADS, 0, st>>>(md, cnt, alpha, A, R, Y);
-  } else {
-    using C = GemmF32Cfg;
-    const dim3 grid((unsigned)((md + C::BM - 1) / C::BM), (unsigned)((cnt + C::BN - 1) / C::BN));
-    if (grid.y > 65535u) return cudaErrorInvalidValue;
-    gemm_f32_kernel<<<grid, C::THREADS, 0, st>>>(md, cnt, (float)alpha, A, R, Y);
-  }
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 8)
+    return gemm_f64(md, cnt, alpha, A, R, Y, st);
+  else
+    return gemm_f32(md, cnt, (float)alpha, A, R, Y, st);
 }
 
 // one transfer pass along `axis`; shapes per axis given for input and output

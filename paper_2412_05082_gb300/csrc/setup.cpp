@@ -5,6 +5,8 @@
 // local and coarse solvers.
 #include "setup.h"
 
+#include "line1d.h"
+
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -12,187 +14,38 @@
 
 namespace bh {
 
-namespace {
-
-// Legendre P_n(x) and P_{n-1}(x) by the three-term recurrence.
-void legendre(int n, double x, double& pn, double& pnm1) {
-  double p0 = 1.0, p1 = x;
-  if (n == 0) { pn = 1.0; pnm1 = 0.0; return; }
-  for (int m = 1; m < n; ++m) {
-    double p2 = ((2.0 * m + 1.0) * x * p1 - m * p0) / (m + 1.0);
-    p0 = p1;
-    p1 = p2;
-  }
-  pn = p1;
-  pnm1 = p0;
-}
-
-}  // namespace
-
 std::vector<double> gll_points(int k) {
-  // end points and the roots of P_k', found by Newton's method from the
-  // Chebyshev-Gauss-Lobatto points; P_k' and P_k'' from the Legendre ODE.
-  std::vector<double> x(k + 1);
-  x[0] = -1.0;
-  x[k] = 1.0;
-  for (int j = 1; j < k; ++j) {
-    double t = -std::cos(M_PI * j / k);
-    for (int it = 0; it < 100; ++it) {
-      double pn, pm;
-      legendre(k, t, pn, pm);
-      double d1 = k * (t * pn - pm) / (t * t - 1.0);
-      double d2 = (2.0 * t * d1 - k * (k + 1.0) * pn) / (1.0 - t * t);
-      double dt = d1 / d2;
-      t -= dt;
-      if (std::fabs(dt) < 1e-17) break;
-    }
-    x[j] = t;
-  }
-  std::sort(x.begin(), x.end());
-  for (double& v : x) v = 0.5 * (v + 1.0);
-  x[0] = 0.0;
-  x[k] = 1.0;
-  return x;
+  std::vector<double> z(k + 1);
+  line1d::gll(k, z.data());
+  return z;
 }
 
 void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w) {
   x.assign(q, 0.0);
   w.assign(q, 0.0);
-  for (int j = 0; j < q; ++j) {
-    double t = std::cos(M_PI * (j + 0.75) / (q + 0.5));
-    double d1 = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double pn, pm;
-      legendre(q, t, pn, pm);
-      d1 = q * (t * pn - pm) / (t * t - 1.0);
-      double dt = pn / d1;
-      t -= dt;
-      if (std::fabs(dt) < 1e-17) break;
-    }
-    double pn, pm;
-    legendre(q, t, pn, pm);
-    d1 = q * (t * pn - pm) / (t * t - 1.0);
-    x[j] = 0.5 * (t + 1.0);
-    w[j] = 1.0 / ((1.0 - t * t) * d1 * d1);  // 2/((1-t^2)P'^2), halved for [0,1]
-  }
+  line1d::gauss(q, x.data(), w.data());
 }
 
 double lagrange(const std::vector<double>& z, int i, double x, int deriv) {
-  // l_i = prod_{j != i} (x - z_j)/(z_i - z_j); derivatives by the product rule.
-  const int n = (int)z.size();
-  auto fac = [&](int j) { return (x - z[j]) / (z[i] - z[j]); };
-  if (deriv == 0) {
-    double p = 1.0;
-    for (int j = 0; j < n; ++j)
-      if (j != i) p *= fac(j);
-    return p;
-  }
-  if (deriv == 1) {
-    double s = 0.0;
-    for (int m = 0; m < n; ++m) {
-      if (m == i) continue;
-      double p = 1.0 / (z[i] - z[m]);
-      for (int j = 0; j < n; ++j)
-        if (j != i && j != m) p *= fac(j);
-      s += p;
-    }
-    return s;
-  }
-  double s = 0.0;
-  for (int m = 0; m < n; ++m) {
-    if (m == i) continue;
-    for (int l = 0; l < n; ++l) {
-      if (l == i || l == m) continue;
-      double p = 1.0 / ((z[i] - z[m]) * (z[i] - z[l]));
-      for (int j = 0; j < n; ++j)
-        if (j != i && j != m && j != l) p *= fac(j);
-      s += p;
-    }
-  }
-  return s;
+  return line1d::lagrange(z.data(), (int)z.size(), i, x, deriv);
 }
 
 static void cell_matrices(int k, const std::vector<double>& z, std::vector<double>& M,
                           std::vector<double>& L, std::vector<double>& B) {
-  std::vector<double> x, w;
-  gauss_rule(k + 2, x, w);
   const int n = k + 1;
   M.assign(n * n, 0.0);
   L.assign(n * n, 0.0);
   B.assign(n * n, 0.0);
-  for (size_t q = 0; q < x.size(); ++q) {
-    double v0[kMaxK + 1], v1[kMaxK + 1], v2[kMaxK + 1];
-    for (int i = 0; i < n; ++i) {
-      v0[i] = lagrange(z, i, x[q], 0);
-      v1[i] = lagrange(z, i, x[q], 1);
-      v2[i] = lagrange(z, i, x[q], 2);
-    }
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        M[i * n + j] += w[q] * v0[i] * v0[j];
-        L[i * n + j] += w[q] * v1[i] * v1[j];
-        B[i * n + j] += w[q] * v2[i] * v2[j];
-      }
-  }
+  line1d::cell_matrices(k, z.data(), M.data(), L.data(), B.data());
 }
 
 void global_1d(int k, double gamma, int cells, std::vector<double>& M, std::vector<double>& L,
                std::vector<double>& B) {
-  const std::vector<double> z = gll_points(k);
-  std::vector<double> cM, cL, cB;
-  cell_matrices(k, z, cM, cL, cB);
-  const int n = k * cells + 1, c1 = k + 1;
+  const int n = k * cells + 1;
   M.assign((size_t)n * n, 0.0);
   L.assign((size_t)n * n, 0.0);
   B.assign((size_t)n * n, 0.0);
-  for (int c = 0; c < cells; ++c)
-    for (int i = 0; i < c1; ++i)
-      for (int j = 0; j < c1; ++j) {
-        size_t o = (size_t)(k * c + i) * n + (k * c + j);
-        M[o] += cM[i * c1 + j];
-        L[o] += cL[i * c1 + j];
-        B[o] += cB[i * c1 + j];
-      }
-  // derivative traces at the cell end points (cell size 1)
-  std::vector<double> d1l(c1), d1r(c1), d2l(c1), d2r(c1);
-  for (int i = 0; i < c1; ++i) {
-    d1l[i] = lagrange(z, i, 0.0, 1);
-    d1r[i] = lagrange(z, i, 1.0, 1);
-    d2l[i] = lagrange(z, i, 0.0, 2);
-    d2r[i] = lagrange(z, i, 1.0, 2);
-  }
-  // face points f = 0..cells: jump = sum of outward derivatives, mean = half sum
-  // (one-sided on the boundary); gamma/h [[.]][[.]] - {.}[[.]] - [[.]]{.}, h = 1
-  for (int f = 0; f <= cells; ++f) {
-    std::vector<int> ids;
-    std::vector<double> J, Mu;
-    const bool interior = (f > 0 && f < cells);
-    if (f > 0) {  // cell f-1 on the left, outward normal +x
-      for (int i = 0; i < c1; ++i) {
-        ids.push_back(k * (f - 1) + i);
-        J.push_back(d1r[i]);
-        Mu.push_back(d2r[i] * (interior ? 0.5 : 1.0));
-      }
-    }
-    if (f < cells) {  // cell f on the right, outward normal -x
-      for (int i = 0; i < c1; ++i) {
-        ids.push_back(k * f + i);
-        J.push_back(-d1l[i]);
-        Mu.push_back(d2l[i] * (interior ? 0.5 : 1.0));
-      }
-    }
-    for (size_t a = 0; a < ids.size(); ++a)
-      for (size_t b = 0; b < ids.size(); ++b)
-        B[(size_t)ids[a] * n + ids[b]] += gamma * J[a] * J[b] - J[a] * Mu[b] - Mu[a] * J[b];
-  }
-}
-
-static void fill_class(const std::vector<double>& full, int n, int k, int cells, int g, double* row) {
-  const int last = k * cells - 1;  // last interior node
-  for (int t = -2 * k; t <= 2 * k; ++t) {
-    int col = g + t;
-    row[t + 2 * k] = (col >= 1 && col <= last) ? full[(size_t)g * n + col] : 0.0;
-  }
+  line1d::line_matrices(k, gamma, cells, M.data(), L.data(), B.data(), n);
 }
 
 static void cholesky_lower(int n, double* A) {
@@ -401,30 +254,8 @@ void build_setup(int k, double gamma, Setup1D& s) {
   global_1d(k, gamma, 7, M7, L7, B7);
   global_1d(k, gamma, 2, M2, L2, B2);
   const int n7 = 7 * k + 1, n2 = 2 * k + 1;
-  for (int q = 0; q < k; ++q) {  // canonical rows: band -2k..2k away from both faces
-    const int g = 3 * k + q;
-    fill_class(M7, n7, k, 7, g, &s.tabM[q * bw]);
-    fill_class(L7, n7, k, 7, g, &s.tabL[q * bw]);
-    fill_class(B7, n7, k, 7, g, &s.tabB[q * bw]);
-  }
-  for (int g = 1; g <= k; ++g) {  // rows touching x = 0
-    const int c = k + g - 1;
-    fill_class(M7, n7, k, 7, g, &s.tabM[c * bw]);
-    fill_class(L7, n7, k, 7, g, &s.tabL[c * bw]);
-    fill_class(B7, n7, k, 7, g, &s.tabB[c * bw]);
-  }
-  for (int g = 6 * k; g <= 7 * k - 1; ++g) {  // rows touching x = 1
-    const int c = 2 * k + (g - 6 * k);
-    fill_class(M7, n7, k, 7, g, &s.tabM[c * bw]);
-    fill_class(L7, n7, k, 7, g, &s.tabL[c * bw]);
-    fill_class(B7, n7, k, 7, g, &s.tabB[c * bw]);
-  }
-  {  // N = 2, middle vertex g = k touches both faces
-    const int c = 3 * k;
-    fill_class(M2, n2, k, 2, k, &s.tabM[c * bw]);
-    fill_class(L2, n2, k, 2, k, &s.tabL[c * bw]);
-    fill_class(B2, n2, k, 2, k, &s.tabB[c * bw]);
-  }
+  line1d::class_tables(k, M7.data(), L7.data(), B7.data(), n7, M2.data(), L2.data(), B2.data(),
+                       n2, s.tabM.data(), s.tabL.data(), s.tabB.data());
   // patch submatrices: nodes (first .. first + m - 1) of the reference line;
   // patch vertices v = 3 (interior), 1 (left), 6 (right) of 7 cells, 1 of 2 cells
   struct Src { const std::vector<double>* M; const std::vector<double>* L; const std::vector<double>* B; int n; int first; };

@@ -115,7 +115,7 @@ SMOOTH_CASES = [
     (2, 3, 16, "mvs", "inexact"), (2, 5, 8, "mvs", "inexact"), (2, 7, 8, "mvs", "inexact"),
     # exact local solvers: per-patch products (3D k = 4) and, for patches of
     # m^3 >= 512 unknowns, one dense product per run of a type combination
-    # (the library's own FP64 tensor-core GEMM, gemm.cuh)
+    # (the library's own FP64 tensor-core GEMM, gemm.cu)
     (3, 4, 4, "mvs", "exact"), (3, 5, 4, "avs", "exact"), (3, 5, 2, "mvs", "exact"),
     (3, 5, 4, "mvs", "exact"), (3, 6, 2, "mvs", "exact"), (3, 6, 4, "mvs", "exact"),
     (3, 7, 2, "mvs", "exact"),
