@@ -41,8 +41,9 @@ typedef enum {
   BH_ENOMEM = -2,    /* device or host allocation failed */
   BH_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
   BH_ENOCONV = -4,   /* the Krylov solver did not reach the tolerance */
-  BH_ETIMEOUT = -5,  /* a bounded device-side wait ran out */
-  BH_EBUSY = -6      /* resource in use (server queue full) */
+  BH_ETIMEOUT = -5,  /* a bounded wait ran out (server: a request's deadline passed) */
+  BH_EBUSY = -6,     /* resource in use (server queue full) */
+  BH_ECANCELED = -7  /* the request was cancelled before it started */
 } bh_status;
 
 /* smoother (Sec. 3): additive vertex-patch smoother with atomic or colored
@@ -214,6 +215,13 @@ const char* bh_last_error(void);
  * (all contexts).  Host only; never fails. */
 long long bh_kernel_launches(void);
 
+/* Host-side fault injection, for testing failure handling without a device
+ * fault: after `skip` more device allocations by the library succeed, the next
+ * `fail` ones fail with BH_ENOMEM as if cudaMalloc had returned an out-of-memory
+ * error (cudaMalloc is not called for them).  (0, 0) switches it off.  Global
+ * to the process; host only.  The paper has no counterpart. */
+bh_status bh_fault_inject_alloc(long long skip, long long fail);
+
 /* Measured FP64 fused-multiply-add rate of the current device in TFLOP/s:
  * 4 blocks per SM of 128 threads, each running four independent chains of
  * dependent FMAs on registers, timed with CUDA events on `stream` (a
@@ -359,12 +367,28 @@ bh_status bh_server_create(const bh_server_config* cfg, bh_server** out);
 bh_status bh_server_submit(bh_server* server, int dim, int degree, int level,
                            const double* b_host, double* x_host, int64_t* ticket);
 
+/* bh_server_submit with a deadline: a request not started deadline_s seconds
+ * after its submission (0: no deadline) is dropped when a slot reaches it, its
+ * result status BH_ETIMEOUT; the server goes on with the next request. */
+bh_status bh_server_submit_deadline(bh_server* server, int dim, int degree, int level,
+                                    const double* b_host, double* x_host, double deadline_s,
+                                    int64_t* ticket);
+
+/* Cancel a queued request: it is removed from the queue and its result status
+ * is BH_ECANCELED (the ticket must still be released by bh_server_wait).
+ * BH_EBUSY if it has already started or finished (a running solve is not
+ * interrupted), BH_EINVAL for an unknown ticket. */
+bh_status bh_server_cancel(bh_server* server, int64_t ticket);
+
 /* Wait up to timeout_s seconds (< 0: forever) for a ticket; fills *result and
- * releases the ticket.  BH_ETIMEOUT if still running. */
+ * releases the ticket.  BH_ETIMEOUT if still running.  Tickets that are never
+ * waited for (a client that went away) do not hold up other requests; they
+ * are released by bh_server_destroy. */
 bh_status bh_server_wait(bh_server* server, int64_t ticket, double timeout_s,
                          bh_server_result* result);
 
-/* Queue, slot and memory counters as a JSON object. */
+/* Queue, slot and memory counters as a JSON object, with the requests dropped
+ * at their deadline, cancelled, and failed (allocation or solve errors). */
 bh_status bh_server_stats(bh_server* server, char* buf, size_t len);
 
 /* Finish the queued requests, stop the workers, free every hierarchy. */

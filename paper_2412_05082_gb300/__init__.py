@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libbiharm.so")
 
 # enums of biharm.h
 BH_OK, BH_EINVAL, BH_ENOMEM, BH_ECUDA, BH_ENOCONV, BH_ETIMEOUT, BH_EBUSY = 0, -1, -2, -3, -4, -5, -6
+BH_ECANCELED = -7
 AVS_ATOMIC, AVS_COLORED, MVS_COLORED = 0, 1, 2
 FDM, EXACT = 0, 1
 FP64, MIXED_FP32, MIXED_FP32_R64 = 0, 1, 2
@@ -24,7 +25,7 @@ GMRES, CG = 0, 1
 RHS_MANUFACTURED, RHS_PAPER_SINE = 0, 1
 
 STATUS_NAMES = {0: "BH_OK", -1: "BH_EINVAL", -2: "BH_ENOMEM", -3: "BH_ECUDA",
-                -4: "BH_ENOCONV", -5: "BH_ETIMEOUT", -6: "BH_EBUSY"}
+                -4: "BH_ENOCONV", -5: "BH_ETIMEOUT", -6: "BH_EBUSY", -7: "BH_ECANCELED"}
 
 
 class BiharmError(RuntimeError):
@@ -65,6 +66,7 @@ SIGNATURES = {
     "bh_stats": (_I, [_P, _c.c_char_p, _c.c_size_t]),
     "bh_last_error": (_c.c_char_p, []),
     "bh_kernel_launches": (_c.c_longlong, []),
+    "bh_fault_inject_alloc": (_I, [_c.c_longlong, _c.c_longlong]),
     "bh_fp64_fma_rate": (_I, [_P, _c.POINTER(_D)]),
     "bh_fp64_mma_rate": (_I, [_P, _c.POINTER(_D)]),
     "bh_setup_1d": (_I, [_I, _D, _I, _I, _P]),
@@ -98,6 +100,8 @@ SIGNATURES.update({
     "bh_server_default_config": (_I, [_c.POINTER(ServerConfig)]),
     "bh_server_create": (_I, [_c.POINTER(ServerConfig), _c.POINTER(_P)]),
     "bh_server_submit": (_I, [_P, _I, _I, _I, _P, _P, _c.POINTER(_I64)]),
+    "bh_server_submit_deadline": (_I, [_P, _I, _I, _I, _P, _P, _D, _c.POINTER(_I64)]),
+    "bh_server_cancel": (_I, [_P, _I64]),
     "bh_server_wait": (_I, [_P, _I64, _D, _c.POINTER(ServerResult)]),
     "bh_server_stats": (_I, [_P, _c.c_char_p, _c.c_size_t]),
     "bh_server_destroy": (_I, [_P]),
@@ -139,6 +143,12 @@ def default_params(dim, degree, level, **overrides):
 
 def kernel_launches():
     return int(load().bh_kernel_launches())
+
+
+def fault_inject_alloc(skip, fail):
+    """bh_fault_inject_alloc: after `skip` more device allocations, make the
+    next `fail` ones fail with BH_ENOMEM (host-side; (0, 0) switches it off)."""
+    _check(load().bh_fault_inject_alloc(int(skip), int(fail)))
 
 
 def fp64_fma_rate(stream=None):
@@ -457,8 +467,10 @@ class Server:
         self._h = h
         self._keep = {}
 
-    def submit(self, dim, degree, level, b, x):
-        """b, x: contiguous float64 numpy arrays (kept alive until wait)."""
+    def submit(self, dim, degree, level, b, x, deadline=0.0):
+        """b, x: contiguous float64 numpy arrays (kept alive until wait);
+        deadline: seconds after which a request that has not started is
+        dropped (bh_server_submit_deadline; 0: none)."""
         import numpy as np
         n = (degree * 2 ** level - 1) ** dim
         for a in (b, x):
@@ -466,10 +478,15 @@ class Server:
                     or not a.flags.c_contiguous:
                 raise ValueError("b and x must be contiguous float64 arrays with %d values" % n)
         t = ctypes.c_int64()
-        _check(load().bh_server_submit(self._h, dim, degree, level, b.ctypes.data, x.ctypes.data,
-                                       ctypes.byref(t)))
+        _check(load().bh_server_submit_deadline(self._h, dim, degree, level, b.ctypes.data,
+                                                x.ctypes.data, float(deadline), ctypes.byref(t)))
         self._keep[t.value] = (b, x)
         return t.value
+
+    def cancel(self, ticket):
+        """bh_server_cancel: drop a queued request (BiharmError BH_EBUSY once it
+        has started)."""
+        _check(load().bh_server_cancel(self._h, ticket))
 
     def wait(self, ticket, timeout=-1.0):
         """bh_server_wait: the request's status, iterations, relres and latencies

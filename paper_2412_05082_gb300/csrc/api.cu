@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -45,6 +46,18 @@ bh_status fail(bh_status s, const std::string& msg) {
 namespace bh {
 // message returned by bh_last_error() on this thread (used by noalloc.cu, batch.cu)
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+// Host-side fault injection (bh_fault_inject_alloc): after g_alloc_skip more
+// device allocations, the next g_alloc_fail ones fail as if cudaMalloc had
+// returned cudaErrorMemoryAllocation, without calling it.
+std::atomic<long long> g_alloc_skip{0}, g_alloc_fail{0};
+
+bool alloc_fault() {
+  if (g_alloc_fail.load() <= 0) return false;
+  if (g_alloc_skip.fetch_sub(1) > 0) return false;
+  g_alloc_skip.store(0);
+  return g_alloc_fail.fetch_sub(1) > 0;
+}
 }  // namespace bh
 
 namespace {
@@ -53,7 +66,7 @@ template <typename T>
 bh_status dmalloc(bh_ctx* c, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return BH_OK;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  cudaError_t e = alloc_fault() ? cudaErrorMemoryAllocation : cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
@@ -1112,6 +1125,14 @@ bh_status bh_stats(const bh_ctx* ctx, char* buf, size_t len) {
 }
 
 long long bh_kernel_launches(void) { return g_kernel_launches.load(); }
+
+bh_status bh_fault_inject_alloc(long long skip, long long count) {
+  if (skip < 0 || count < 0) return fail(BH_EINVAL, "bh_fault_inject_alloc: negative count");
+  g_alloc_fail.store(0);
+  g_alloc_skip.store(skip);
+  g_alloc_fail.store(count);
+  return BH_OK;
+}
 
 bh_status bh_setup_1d(int degree, double gamma, int cells, int which, double* out) {
   if (degree < 2 || degree > kMaxK || cells < 1 || which < 0 || which > 2 || !out)

@@ -31,6 +31,7 @@
 
 namespace bh {
 void set_last_error(const std::string& msg);  // api.cu
+bool alloc_fault();                           // api.cu: host-side fault injection
 }
 
 using namespace bh;
@@ -409,7 +410,8 @@ bh_status upload(bh_batch* b, const std::vector<A>& h, DevArray<A>& d) {
   d.n = (int)h.size();
   d.d = nullptr;
   if (h.empty()) return BH_OK;
-  if (cudaMalloc(&d.d, h.size() * sizeof(A)) != cudaSuccess) {
+  if (alloc_fault() || cudaMalloc(&d.d, h.size() * sizeof(A)) != cudaSuccess) {
+    d.d = nullptr;
     cudaGetLastError();
     return berr(BH_ENOMEM, "cudaMalloc failed in batch setup");
   }
@@ -1013,7 +1015,7 @@ bh_status ensure_plan(bh_batch* b) {
     const int64_t cnt[2] = {m + 1, b->right ? m : 0};
     for (int i = 0; i < 2; ++i) {
       if (*bufs[i] || cnt[i] == 0) continue;
-      if (cudaMalloc(bufs[i], (size_t)cnt[i] * n * sizeof(double)) != cudaSuccess) {
+      if (alloc_fault() || cudaMalloc(bufs[i], (size_t)cnt[i] * n * sizeof(double)) != cudaSuccess) {
         *bufs[i] = nullptr;
         cudaGetLastError();
         return berr(BH_ENOMEM, "Krylov basis allocation failed");

@@ -56,6 +56,7 @@ struct Request {
   const double* b = nullptr;  // host, owned by the caller until completion
   double* x = nullptr;
   Clock::time_point submitted;
+  Clock::time_point deadline = Clock::time_point::max();  // dropped if not started by then
   // results
   bool done = false;
   int status = BH_OK, iters = 0;
@@ -104,7 +105,8 @@ struct bh_server {
   bool stop = false;
   int64_t next_ticket = 1;
   int running = 0;
-  long long admitted = 0, evictions = 0, created = 0, completed = 0;
+  long long admitted = 0, evictions = 0, created = 0, completed = 0, dropped = 0, cancelled = 0,
+            failed = 0;
   double busy_seconds = 0;
   Clock::time_point t0;
 };
@@ -185,11 +187,21 @@ void worker(bh_server* s) {
     if (s->queue.empty() && s->stop) return;
     Request* r = s->queue.front();
     s->queue.pop_front();
+    if (Clock::now() > r->deadline) {  // not started before its deadline: dropped
+      r->status = BH_ETIMEOUT;
+      r->done = true;
+      r->latency = std::chrono::duration<double>(Clock::now() - r->submitted).count();
+      s->completed++;
+      s->dropped++;
+      s->cv_done.notify_all();
+      continue;
+    }
     const int precision = (s->cfg.mixed_max_degree >= r->degree) ? BH_MIXED_FP32_R64 : BH_FP64;
     bh_status st = BH_OK;
     Pooled* p = acquire(s, lk, *r, precision, &st);
     if (!p) {
       r->status = st;
+      s->failed++;
       r->done = true;
       r->latency = std::chrono::duration<double>(Clock::now() - r->submitted).count();
       s->completed++;
@@ -210,6 +222,7 @@ void worker(bh_server* s) {
     p->busy = false;
     p->last_used = t_end;
     r->status = st;
+    if (st != BH_OK) s->failed++;
     r->iters = it;
     r->relres = rr;
     r->service = std::chrono::duration<double>(t_end - t_start).count();
@@ -271,7 +284,14 @@ bh_status bh_server_create(const bh_server_config* cfg, bh_server** out) {
 
 bh_status bh_server_submit(bh_server* s, int dim, int degree, int level, const double* b_host,
                            double* x_host, int64_t* ticket) {
-  if (!s || !b_host || !x_host || !ticket) return serr(BH_EINVAL, "bh_server_submit: bad arguments");
+  return bh_server_submit_deadline(s, dim, degree, level, b_host, x_host, 0.0, ticket);
+}
+
+bh_status bh_server_submit_deadline(bh_server* s, int dim, int degree, int level,
+                                    const double* b_host, double* x_host, double deadline_s,
+                                    int64_t* ticket) {
+  if (!s || !b_host || !x_host || !ticket || !(deadline_s >= 0.0))
+    return serr(BH_EINVAL, "bh_server_submit: bad arguments");
   bh_params tmp;
   bh_status v = bh_default_params(dim, degree, level, &tmp);
   if (v != BH_OK) return v;
@@ -283,6 +303,9 @@ bh_status bh_server_submit(bh_server* s, int dim, int degree, int level, const d
   r->b = b_host;
   r->x = x_host;
   r->submitted = Clock::now();
+  if (deadline_s > 0.0)
+    r->deadline = r->submitted +
+                  std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(deadline_s));
   {
     std::lock_guard<std::mutex> g(s->mu);
     if (s->stop) {
@@ -323,6 +346,24 @@ bh_status bh_server_wait(bh_server* s, int64_t ticket, double timeout_s, bh_serv
   return BH_OK;
 }
 
+bh_status bh_server_cancel(bh_server* s, int64_t ticket) {
+  if (!s) return serr(BH_EINVAL, "null server");
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return serr(BH_EINVAL, "unknown ticket");
+  Request* r = it->second;
+  auto q = std::find(s->queue.begin(), s->queue.end(), r);
+  if (q == s->queue.end()) return serr(BH_EBUSY, "request already started or finished");
+  s->queue.erase(q);
+  r->status = BH_ECANCELED;
+  r->done = true;
+  r->latency = std::chrono::duration<double>(Clock::now() - r->submitted).count();
+  s->completed++;
+  s->cancelled++;
+  s->cv_done.notify_all();
+  return BH_OK;
+}
+
 bh_status bh_server_stats(bh_server* s, char* buf, size_t len) {
   if (!s || !buf || len == 0) return serr(BH_EINVAL, "bad arguments");
   std::lock_guard<std::mutex> g(s->mu);
@@ -331,10 +372,11 @@ bh_status bh_server_stats(bh_server* s, char* buf, size_t len) {
                 "{\"slots\": %d, \"queued\": %zu, \"running\": %d, \"admitted\": %lld, "
                 "\"completed\": %lld, \"resident_contexts\": %zu, \"created\": %lld, "
                 "\"evictions\": %lld, \"reserved_bytes\": %.0f, \"budget_bytes\": %.0f, "
-                "\"busy_slot_seconds\": %.6f, \"uptime_s\": %.6f}",
+                "\"busy_slot_seconds\": %.6f, \"uptime_s\": %.6f, \"dropped\": %lld, "
+                "\"cancelled\": %lld, \"failed\": %lld}",
                 s->cfg.slots, s->queue.size(), s->running, s->admitted, s->completed,
                 s->pool.size(), s->created, s->evictions, s->used, s->cfg.mem_budget_bytes,
-                s->busy_seconds, up);
+                s->busy_seconds, up, s->dropped, s->cancelled, s->failed);
   return BH_OK;
 }
 

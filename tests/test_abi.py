@@ -124,3 +124,13 @@ def test_no_cpu_fallback(lib):
     assert e.value.status == lib.BH_ECUDA
     with pytest.raises(TypeError):
         lib._dev(torch.zeros(3, dtype=torch.float64), 3, "x")
+
+
+def test_fault_injection_switch_on_the_host(lib):
+    """bh_fault_inject_alloc is host-only: it takes non-negative counts and can
+    be switched off again without a device."""
+    lib.fault_inject_alloc(3, 1)
+    lib.fault_inject_alloc(0, 0)
+    with pytest.raises(lib.BiharmError) as e:
+        lib.fault_inject_alloc(-1, 1)
+    assert e.value.status == lib.BH_EINVAL
