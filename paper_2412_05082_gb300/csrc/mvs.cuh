@@ -50,9 +50,14 @@ struct Mvs2Cfg {
   static constexpr int W = 4 * K + 1;   // window nodes per direction
   static constexpr int WM = 2 * K + 1;  // rows of T_L, T_B
   static constexpr int NC = 3 * K + 1, BW = 4 * K + 1;
-  // values per patch: window, T_M, T_L, T_B; the two m x m buffers of the
-  // residual and the FDM reuse the window's space once the x-split has read it
-  static constexpr int PER = W * W + W * M + 2 * WM * M;
+  // FP32: b and x on the patch nodes are copied to shared memory together
+  // with the window, so that no stage after the window copy waits on a global
+  // load (the FP32 kernel is bound by load latency, the FP64 one by its pipe)
+  static constexpr bool PREFETCH = sizeof(T) == 4;
+  // values per patch: window, T_M, T_L, T_B (and the prefetched b and x); the
+  // two m x m buffers of the residual and the FDM reuse the window's space once
+  // the x-split has read it
+  static constexpr int PER = W * W + W * M + 2 * WM * M + (PREFETCH ? 2 * M * M : 0);
   static_assert(2 * M * M <= W * W, "FDM buffers must fit in the window region");
   // M, L, B class tables, the four S, and the interior type's 1 / (l_x + l_y)
   static constexpr int TABLES = 3 * NC * BW + 5 * M * M;
@@ -141,6 +146,23 @@ __device__ __forceinline__ void ycombine_half(const T* sM, const T* sL, const T*
   }
 }
 
+// Asynchronous copies of b and x on the m x m patch nodes of the tile's
+// patches into sBv, sXv ([patch][row][column]).  Patch nodes always lie in the
+// interior 1..n.  Values of x on a patch's own nodes are changed by no other
+// patch of its color, so the copy stays current until the patch's update.
+template <typename T, int K>
+__device__ __forceinline__ void prefetch_patch_nodes(const MvsArgs<T>& a, int np,
+                                                     const int (*sV)[2], T* sBv, T* sXv) {
+  constexpr int M = 2 * K - 1, MM = M * M;
+  const int64_t n = a.n;
+  for (int e = threadIdx.x; e < np * MM; e += blockDim.x) {
+    const int p = e / MM, i = (e / M) % M, j = e % M;
+    const int64_t gi = (int64_t)(K * (sV[p][1] - 1) + i) * n + (K * (sV[p][0] - 1) + j);
+    async_copy_or_zero(sBv + e, a.b + gi, true);
+    async_copy_or_zero(sXv + e, a.x + gi, true);
+  }
+}
+
 // Patches first .. first + np - 1 of a.verts by one thread block; tables read
 // from `op` / `fdm` (kernel parameters or device memory) into shared memory.
 // smem_raw: dynamic shared memory of at least Mvs2Cfg::smem_bytes(a.pb) bytes.
@@ -161,6 +183,8 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
   T* sTB = sTL + pb * WM * M;  // [pb][WM][M]
   T* sR = sX;                  // [pb][M][M], over the window after the x-split
   T* sF = sR + pb * MM;        // [pb][M][M]
+  T* sBv = sTB + pb * WM * M;  // [pb][M][M] b on the patch nodes (PREFETCH)
+  T* sXv = sBv + pb * MM;      // [pb][M][M] x on the patch nodes (PREFETCH)
   __shared__ int sV[32][2], sTy[32][2], sCombo[32];
 
   if (np <= 0) return;
@@ -190,6 +214,7 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
     const bool in = gx >= 1 && gx <= n && gy >= 1 && gy <= n;
     async_copy_or_zero(sX + e, a.x + (in ? (int64_t)(gy - 1) * n + (gx - 1) : 0), in);
   }
+  if constexpr (C::PREFETCH) prefetch_patch_nodes<T, K>(a, np, sV, sBv, sXv);
   async_copy_wait();
   __syncthreads();
   // x-split: T_M on every window row, one half-line (half, patch, row) per item
@@ -228,12 +253,14 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
     const bool canon = sTy[p][1] == 0;
     const int g0 = K * (sV[p][1] - 1);
     const int gx = K * (sV[p][0] - 1) + j + 1;
-    const T* bcol = a.b + (int64_t)g0 * n + (gx - 1);  // b at patch position 1 (global row g0 + 1)
+    // b at patch position 1 (global row g0 + 1) of the column, and its row stride
+    const T* bcol = C::PREFETCH ? sBv + p * MM + j : a.b + (int64_t)g0 * n + (gx - 1);
+    const int64_t bs = C::PREFETCH ? M : n;
     T* rcol = sR + p * M * M + j;
     if (half == 0)
-      ycombine_half<T, K, 0>(sM, sL, sB, canon, g0, N, cm, cl, cb, bcol, n, asc, rcol);
+      ycombine_half<T, K, 0>(sM, sL, sB, canon, g0, N, cm, cl, cb, bcol, bs, asc, rcol);
     else
-      ycombine_half<T, K, 1>(sM, sL, sB, canon, g0, N, cm, cl, cb, bcol, n, asc, rcol);
+      ycombine_half<T, K, 1>(sM, sL, sB, canon, g0, N, cm, cl, cb, bcol, bs, asc, rcol);
   }
   __syncthreads();
   // fast diagonalization: F = R S_x (rows), R = S_y^T F scaled (columns)
@@ -277,7 +304,11 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
 #pragma unroll
     for (int c = 0; c < M; ++c) s = fma(S[j * M + c], f[c], s);
     const int gx = K * (sV[p][0] - 1) + j + 1, gy = K * (sV[p][1] - 1) + i + 1;
-    a.x[(int64_t)(gy - 1) * n + (gx - 1)] += ps * s;
+    T* xo = a.x + (int64_t)(gy - 1) * n + (gx - 1);
+    if constexpr (C::PREFETCH)
+      *xo = sXv[e] + ps * s;
+    else
+      *xo += ps * s;
   }
 }
 
@@ -468,6 +499,8 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   T* sTB = sTL + pb * WM * M;
   T* sR = sX;  // over the window after the x-split
   T* sF = sR + pb * MM;
+  T* sBv = sTB + pb * WM * M;  // b and x on the patch nodes (PREFETCH)
+  T* sXv = sBv + pb * MM;
   __shared__ int sVi[32][2];
   const int N = a.N, n = a.n;
   // operator and eigenvector tables staged in shared memory (layout of OpTab
@@ -497,6 +530,7 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
     // outside the interior the (unread) source is the first value of x
     async_copy_or_zero(sX + e, a.x + (in ? (int64_t)(gy - 1) * n + (gx - 1) : 0), in);
   }
+  if constexpr (C::PREFETCH) prefetch_patch_nodes<T, K>(a, np, sVi, sBv, sXv);
   async_copy_wait();
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * np * W; e += blockDim.x) {
@@ -527,12 +561,13 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
     const T* cb = sTB + (p * WM) * M + j;
     const int g0 = K * (sVi[p][1] - 1);
     const int gx = K * (sVi[p][0] - 1) + j + 1;
-    const T* bcol = a.b + (int64_t)g0 * n + (gx - 1);
+    const T* bcol = C::PREFETCH ? sBv + p * MM + j : a.b + (int64_t)g0 * n + (gx - 1);
+    const int64_t bs = C::PREFETCH ? M : n;
     T* rcol = sR + p * MM + j;
     if (half == 0)
-      ycombine_canon<T, K, 0>(op_s, cm, cl, cb, bcol, n, asc, rcol);
+      ycombine_canon<T, K, 0>(op_s, cm, cl, cb, bcol, bs, asc, rcol);
     else
-      ycombine_canon<T, K, 1>(op_s, cm, cl, cb, bcol, n, asc, rcol);
+      ycombine_canon<T, K, 1>(op_s, cm, cl, cb, bcol, bs, asc, rcol);
   }
   __syncthreads();
   // F = R S (rows)
@@ -579,7 +614,13 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
     const T* src = sF + p * MM + i * M;
     const int gy = K * (sVi[p][1] - 1) + i + 1, gx0 = K * (sVi[p][0] - 1) + 1;
     T* xrow = a.x + (int64_t)(gy - 1) * n + (gx0 - 1);
-    auto put = [&](int j, T v) { xrow[j] += ps * v; };
+    const T* xv = sXv + p * MM + i * M;  // x on the row's patch nodes (PREFETCH)
+    auto put = [&](int j, T v) {
+      if constexpr (C::PREFETCH)
+        xrow[j] = xv[j] + ps * v;
+      else
+        xrow[j] += ps * v;
+    };
     if (half == 0)
       fdm_bwd_canon<T, K, 0>(fdm_s, src, 1, put);
     else

@@ -124,11 +124,12 @@ def test_batched_mixed_precision_vcycle_and_solve(bh):
     """The FP32 V-cycle with FP64 defects (BH_MIXED_FP32_R64) in the batch.
     One V-cycle: within 1e-3 of the FP64 oracle's -- FP32 rounding (eps 6e-8)
     amplified by the condition numbers of the patch problems, which grow with
-    the degree (1.5e-4 measured at k = 6) -- and within 1e-5 of the same
-    V-cycle of a single FP32 context (the same arithmetic per patch up to the
-    order of rounding).  Then flexible GMRES to the 1e-8 true residual with at
-    most one iteration more than the oracle's FP64 GMRES, the solution within
-    1e-6 of it."""
+    the degree (1.5e-4 measured at k = 6) -- and no farther from the same
+    V-cycle of a single FP32 context than twice that context's own FP32
+    rounding error (the same arithmetic per patch, in another rounding order:
+    2.7e-5 measured at k = 4 against an FP32 error of 2e-5).  Then flexible
+    GMRES to the 1e-8 true residual with at most one iteration more than the
+    oracle's FP64 GMRES, the solution within 1e-6 of it."""
     Hs = hierarchies()
     bs = [rhs_rough_solution(H.A[H.L], 500 + i)[0] for i, H in enumerate(Hs)]
     params = [bh.default_params(d, k, L, precision=bh.MIXED_FP32_R64) for d, k, L in MIX]
@@ -142,7 +143,8 @@ def test_batched_mixed_precision_vcycle_and_solve(bh):
             with bh.Context(p) as c:
                 xc = torch.zeros_like(x)
                 c.vcycle(L, xc, cuda(b))
-                assert relerr(host(x), host(xc)) <= 1e-5, (k, L)
+                own = relerr(host(xc), ref)          # the single context's FP32 error
+                assert relerr(host(x), host(xc)) <= 2.0 * own + 1e-7, (k, L, own)
         its, rrs = batch.solve(B, X, 1e-8, 100)
         for (d, k, L), H, b, x, it, rr in zip(MIX, Hs, bs, X, its, rrs):
             xr, it_ref, _, _ = krylov.gmres(H.A[H.L], b, H.preconditioner, 1e-8)
@@ -233,7 +235,7 @@ def test_batch_matches_single_solves(bh):
         assert np.abs(x - x1).max() <= 1e-9 * np.abs(x1).max(), (k, L)
         # the true residuals of two iterates that agree to 1e-9 relative differ by
         # up to ||A|| 1e-9 ||x|| / ||b||: compare them to 1e-3 relative
-        assert abs(rr - rr1) <= 1e-3 * rr1
+        assert abs(rr - rr1) <= 1e-3 * rr1 + 1e-14   # 1e-14: the level-1 exact solve
 
 
 def test_batch_result_independent_of_the_mix(bh):
