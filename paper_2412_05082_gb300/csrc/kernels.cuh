@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(256) patch_fdm_kernel(const __grid_constant__ 
     const int ax = pass < D ? pass : pass - D;
     const int st = ipow(M, ax);
     for (int e = threadIdx.x; e < 2 * np * NL; e += blockDim.x) {
-      const int half = e / (np * NL), p = (e / NL) % np, q = e % NL;
+      const int q_ = e / (NL), q = e - q_ * (NL);  // item (half, patch, q)
+      const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
       const int l0 = (q / st) * st * M + q % st;  // first element of line q
       const int t = sType[p][ax];
       const T* S = &sS[t][0][0];

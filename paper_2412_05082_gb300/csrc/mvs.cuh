@@ -219,7 +219,8 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
   __syncthreads();
   // x-split: T_M on every window row, one half-line (half, patch, row) per item
   for (int e = threadIdx.x; e < 2 * np * W; e += blockDim.x) {
-    const int half = e / (np * W), p = (e / W) % np, wy = e % W;
+    const int q_ = e / (W), wy = e - q_ * (W);  // item (half, patch, wy)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* xr = sX + (p * W + wy) * W + K;  // xr[j] = window column K + j
     T* tm = sTM + (p * W + wy) * M;
     const bool canon = sTy[p][0] == 0;
@@ -231,7 +232,8 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
   }
   // T_L and T_B on the 2k+1 middle window rows
   for (int e = threadIdx.x; e < 2 * np * WM; e += blockDim.x) {
-    const int half = e / (np * WM), p = (e / WM) % np, r = e % WM;
+    const int q_ = e / (WM), r = e - q_ * (WM);  // item (half, patch, r)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* xr = sX + (p * W + K + r) * W + K;
     T* tl = sTL + (p * WM + r) * M;
     T* tb = sTB + (p * WM + r) * M;
@@ -246,7 +248,8 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
   // y-combination and residual r = b - A x on the patch nodes, one half-column per item
   const T asc = (T)a.ascale;
   for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
-    const int half = e / (np * M), p = (e / M) % np, j = e % M;
+    const int q_ = e / (M), j = e - q_ * (M);  // item (half, patch, j)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* cm = sTM + (p * W + K) * M + j;
     const T* cl = sTL + (p * WM) * M + j;
     const T* cb = sTB + (p * WM) * M + j;
@@ -534,7 +537,8 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   async_copy_wait();
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * np * W; e += blockDim.x) {
-    const int half = e / (np * W), p = (e / W) % np, wy = e % W;
+    const int q_ = e / (W), wy = e - q_ * (W);  // item (half, patch, wy)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* xr = sX + (p * W + wy) * W + K;
     T* tm = sTM + (p * W + wy) * M;
     if (half == 0)
@@ -543,7 +547,8 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
       xsplit_m_canon<T, K, 1>(op_s, xr, tm);
   }
   for (int e = threadIdx.x; e < 2 * np * WM; e += blockDim.x) {
-    const int half = e / (np * WM), p = (e / WM) % np, r = e % WM;
+    const int q_ = e / (WM), r = e - q_ * (WM);  // item (half, patch, r)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* xr = sX + (p * W + K + r) * W + K;
     T* tl = sTL + (p * WM + r) * M;
     T* tb = sTB + (p * WM + r) * M;
@@ -555,7 +560,8 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   __syncthreads();
   const T asc = (T)a.ascale;
   for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
-    const int half = e / (np * M), p = (e / M) % np, j = e % M;
+    const int q_ = e / (M), j = e - q_ * (M);  // item (half, patch, j)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* cm = sTM + (p * W + K) * M + j;
     const T* cl = sTL + (p * WM) * M + j;
     const T* cb = sTB + (p * WM) * M + j;
@@ -572,7 +578,8 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   __syncthreads();
   // F = R S (rows)
   for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
-    const int half = e / (np * M), p = (e / M) % np, i = e % M;
+    const int q_ = e / (M), i = e - q_ * (M);  // item (half, patch, i)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* src = sR + p * MM + i * M;
     T* dst = sF + p * MM + i * M;
     auto put = [&](int c, T v) { dst[c] = v; };
@@ -584,7 +591,8 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   __syncthreads();
   // G = D^-1 S^T F (columns), into sR
   for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
-    const int half = e / (np * M), p = (e / M) % np, c0 = e % M;
+    const int q_ = e / (M), c0 = e - q_ * (M);  // item (half, patch, c0)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* src = sF + p * MM + c0;
     T* dst = sR + p * MM + c0;
     const T* dv = sDinv + c0;  // type combination 0 (interior x interior)
@@ -597,7 +605,8 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   __syncthreads();
   // F = S G (columns)
   for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
-    const int half = e / (np * M), p = (e / M) % np, c0 = e % M;
+    const int q_ = e / (M), c0 = e - q_ * (M);  // item (half, patch, c0)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* src = sR + p * MM + c0;
     T* dst = sF + p * MM + c0;
     auto put = [&](int i, T v) { dst[i * M] = v; };
@@ -610,7 +619,8 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   // x_v += pscale F S^T (rows)
   const T ps = (T)a.pscale;
   for (int e = threadIdx.x; e < 2 * np * M; e += blockDim.x) {
-    const int half = e / (np * M), p = (e / M) % np, i = e % M;
+    const int q_ = e / (M), i = e - q_ * (M);  // item (half, patch, i)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const T* src = sF + p * MM + i * M;
     const int gy = K * (sVi[p][1] - 1) + i + 1, gx0 = K * (sVi[p][0] - 1) + 1;
     T* xrow = a.x + (int64_t)(gy - 1) * n + (gx0 - 1);

@@ -124,7 +124,8 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
   // ---- x-split: T_M on the cross rows, T_L and T_B on the middle rows --------
   // items (half, patch, row); x read from global memory, zero outside 1..n
   for (int e = threadIdx.x; e < 2 * np * C::CROSS; e += blockDim.x) {
-    const int half = e / (np * C::CROSS), p = (e / C::CROSS) % np, row = e % C::CROSS;
+    const int q_ = e / (C::CROSS), row = e - q_ * (C::CROSS);  // item (half, patch, row)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     int y, z;
     if (row < WM * W) {
       z = K + row / W;
@@ -152,7 +153,8 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
       line_half<T, K, 1, 0, 0, false>(sM, canon, gx0, N, w, 1, tm, 1, one);
   }
   for (int e = threadIdx.x; e < 2 * np * WM * WM; e += blockDim.x) {
-    const int half = e / (np * WM * WM), p = (e / (WM * WM)) % np, r = e % (WM * WM);
+    const int q_ = e / (WM * WM), r = e - q_ * (WM * WM);  // item (half, patch, r)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const int y = K + r % WM, z = K + r / WM;
     const int gx0 = K * (sV[p][0] - 1);
     const int gy = K * (sV[p][1] - 2) + y, gz = K * (sV[p][2] - 2) + z;
@@ -179,7 +181,8 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
   // ---- y-mix: lines along y for a fixed (z, x position j) ---------------------
   // U_B[z][i][j] = (M_y T_M)(i) for every window z (T_M rows y = K..3K)
   for (int e = threadIdx.x; e < 2 * np * W * M; e += blockDim.x) {
-    const int half = e / (np * W * M), p = (e / (W * M)) % np, r = e % (W * M);
+    const int q_ = e / (W * M), r = e - q_ * (W * M);  // item (half, patch, r)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const int z = r / M, j = r % M;
     const T* A = regA + p * C::RA;
     // T_M column at (y = K + pos, z): rows of the cross are not evenly spaced in
@@ -197,7 +200,8 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
   }
   // U_M and U_L on the middle z
   for (int e = threadIdx.x; e < 2 * np * WM * M; e += blockDim.x) {
-    const int half = e / (np * WM * M), p = (e / (WM * M)) % np, r = e % (WM * M);
+    const int q_ = e / (WM * M), r = e - q_ * (WM * M);  // item (half, patch, r)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
     const int zr = r / M, j = r % M, z = K + zr;
     const T* A = regA + p * C::RA;
     T cm[W], cl[WM], cb[WM];
@@ -231,7 +235,8 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
   // ---- z-combination and residual on the patch nodes (region A) ---------------
   const T asc = (T)a.ascale;
   for (int e = threadIdx.x; e < 2 * np * MM; e += blockDim.x) {
-    const int half = e / (np * MM), p = (e / MM) % np, r = e % MM;  // r = i (y) * M + j (x)
+    const int q_ = e / (MM), r = e - q_ * (MM);  // item (half, patch, r)
+    const int half = q_ >= np ? 1 : 0, p = q_ - half * np;  // r = i (y) * M + j (x)
     const T* Bp = regB + p * C::RB;
     T cub[W], cum[WM], cul[WM];
 #pragma unroll
@@ -309,7 +314,8 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
       const int istride = (stage % 2 == 0) ? C::RA : C::RB;
       const int ostride = (stage % 2 == 0) ? C::RB : C::RA;
       for (int e = threadIdx.x; e < 2 * np * MM; e += blockDim.x) {
-        const int half = e / (np * MM), p = (e / MM) % np, q = e % MM;
+        const int q_ = e / (MM), q = e - q_ * (MM);  // item (half, patch, q)
+        const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
         // first element of line q (the two other coordinates) in [z][y][x] order
         const int l0 = ax == 0 ? q * M : (ax == 1 ? (q / M) * MM + q % M : q);
         const int t = INTERIOR ? 0 : sTy[p][ax];
