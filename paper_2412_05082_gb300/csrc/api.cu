@@ -147,7 +147,15 @@ bh_status patches_t(bh_ctx* c, int l, const T* r, T* x, int lo, int hi, bool ato
         const int cnt = run[1];
         const T* Ainv = TypeOf<T>::ainv(c) + (size_t)run[2] * msz;
         CK(Ops<T>::patch_gather(L.g, r, vs, cnt, R, c->st));
-        CK(Ops<T>::gemm(md, cnt, sc, Ainv, R, Y, c->st));
+        if constexpr (std::is_same<T, double>::value) {
+          // FP64 by FP16 slices: slice the run's columns, then the sliced product
+          const size_t sl = (size_t)kSlices * md * slice_ld(md);
+          CK(slice_cols(R, md, cnt, c->gRs, c->gRe, c->st));
+          CK(gemm_f64_sliced(md, cnt, sc, c->ainv_sl + (size_t)run[2] * sl,
+                             c->ainv_ex + (size_t)run[2] * md, c->gRs, c->gRe, Y, c->st));
+        } else {
+          CK(gemm_f32(md, cnt, (float)sc, Ainv, R, Y, c->st));
+        }
         CK(Ops<T>::patch_scatter(L.g, Y, vs, cnt, x, atomic, c->st));
       }
     }
@@ -800,6 +808,12 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
     const size_t cols = (size_t)md * c->gemm_cols;
     if ((status = dmalloc(c, &c->gR64, cols)) || (status = dmalloc(c, &c->gY64, cols)))
       return bail(status);
+    const size_t slices = (size_t)kSlices * slice_ld(md);
+    if ((status = dmalloc(c, &c->gRs, slices * c->gemm_cols)) ||
+        (status = dmalloc(c, &c->gRe, (size_t)c->gemm_cols)) ||
+        (status = dmalloc(c, &c->ainv_sl, slices * md * (d == 2 ? 16 : 64))) ||
+        (status = dmalloc(c, &c->ainv_ex, (size_t)md * (d == 2 ? 16 : 64))))
+      return bail(status);
     if (mx && ((status = dmalloc(c, &c->gR32, cols)) || (status = dmalloc(c, &c->gY32, cols))))
       return bail(status);
   }
@@ -867,6 +881,12 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
       if (cudaMemcpy(c->ainv64 + slot * msz, A.data(), msz * sizeof(double),
                      cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(fail(BH_ECUDA, "upload of local inverses failed"));
+      if (gemm_exact) {  // slices of the rows (= columns: the inverse is symmetric)
+        const size_t sl = (size_t)kSlices * md * slice_ld(md);
+        if (slice_cols(c->ainv64 + slot * msz, md, md, c->ainv_sl + slot * sl,
+                       c->ainv_ex + (size_t)slot * md, c->st) != cudaSuccess)
+          return bail(fail(BH_ECUDA, "slicing of the local inverses failed"));
+      }
       if (mx) {
         Af.assign(A.begin(), A.end());
         if (cudaMemcpy(c->ainv32 + slot * msz, Af.data(), msz * sizeof(float),

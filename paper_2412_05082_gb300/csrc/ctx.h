@@ -58,6 +58,13 @@ struct bh_ctx {
   int gemm_cols = 0;  // largest run
   double *gR64 = nullptr, *gY64 = nullptr;
   float *gR32 = nullptr, *gY32 = nullptr;
+  // FP64 product by FP16 slices (gemm.cu): the slices of every inverse slot
+  // ([slot][kSlices][m^d][ld]) with their row exponents ([slot][m^d]), and the
+  // slices of one run's gathered patch tensors with their column exponents
+  uint16_t* ainv_sl = nullptr;
+  int* ainv_ex = nullptr;
+  uint16_t* gRs = nullptr;
+  int* gRe = nullptr;
   // GMRES workspace (allocated on first solve)
   int m = 0;
   double* V = nullptr;

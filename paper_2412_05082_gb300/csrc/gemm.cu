@@ -3,23 +3,31 @@
 // patches sharing one boundary-type combination, the patch tensors gathered as
 // the columns of R (m^d x cnt) are multiplied by the dense inverse,
 //
-//   Y = alpha * A R,   A: m^d x m^d, column-major;  R, Y: m^d x cnt, column-major,
+//   Y = alpha * A R,   A: m^d x m^d symmetric;  R, Y: m^d x cnt, column-major,
 //
-// with m^d = 729, 1331, 2197 for 3D k = 5, 6, 7.  The product is bound by the
-// arithmetic pipe, never by memory: FP64 on GB300 issues about 2 DFMA per clock
-// and SM, FP32 128 FFMA.
-//  - FP64: the FP64 tensor-core instruction (mma.sync m8n8k4, 256 FMAs per warp
-//    instruction, the rate of the FMA pipe or slightly above on this part);
-//    a 64 x 64 tile per block of four warps, each warp 32 x 32 (16 MMAs per
-//    k-step of 4), k-panels of 16 staged in shared memory by asynchronous
-//    copies, double-buffered.
-//  - FP32: FFMA with 8 x 8 outputs per thread, a 128 x 128 tile per block of
-//    256 threads, 128-bit shared-memory operand loads (one byte of shared
-//    memory per FMA), k-panels of 8, double-buffered.
-// Out-of-range rows, columns and k are zero-filled in shared memory, so any
-// m^d and cnt work; element-wise 4- or 8-byte copies need no alignment beyond
-// the value's own (m^d is odd).
+// with m^d = 729, 1331, 2197 for 3D k = 5, 6, 7.
+//
+// FP64: emulated on the FP16 tensor cores by splitting the operands into
+// integer slices (an error-free splitting of the Ozaki type).  Every row of A
+// and every column of R is scaled by a power of two into (-1, 1) and split into
+// kSlices slices of kSliceBits bits: x = 2^e sum_i x_i 2^(-6 (i+1)), x_i an
+// integer with |x_i| <= 63, exact in FP16.  A slice product sum_k a_i r_j is an
+// integer below K 63^2 < 2^24 for K <= 4,227, so the tensor cores' FP32
+// accumulation over the whole inner dimension is exact; the products of the
+// slice pairs (i, j) with i + j < kSlices are scaled by 2^(-6 (i + j + 2)) and
+// summed in FP64.  The dropped pairs and the split's remainder are below
+// 2^(-6 kSlices) relative to the row and column maxima: 2^-48 for 8 slices,
+// the rounding level of an FP64 product with an inner dimension of 2,197.
+// FP16 mma.sync runs at 600 TFLOP/s on GB300 against 1.1 for the FP64 tensor
+// instruction (measured), so the 36 slice products of the emulation beat the
+// FP64 product several times over.
+//
+// FP32 (the mixed forms): FFMA with 8 x 8 outputs per thread, a 128 x 128 tile
+// per block of 256 threads, 128-bit shared-memory operand loads, k-panels of 8,
+// double-buffered.
 #include <cuda_runtime.h>
+
+#include <cuda_fp16.h>
 
 #include <cstdint>
 
@@ -36,110 +44,177 @@ __device__ __forceinline__ void async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// ---- FP64: DMMA ------------------------------------------------------------
-// Block tile (WM_ x 32) x (WN_ x 32): WM_ x WN_ warps, each warp a 32 x 32 tile
-// (4 x 4 DMMA tiles of 8 x 8, 16 accumulating MMAs per k-step of 4); k-panels
-// of BK values.
-template <int WM_, int WN_, int BK_>
-struct GemmF64Cfg {
-  static constexpr int WM = WM_, WN = WN_, BK = BK_;
-  static constexpr int BM = 32 * WM, BN = 32 * WN, PAD = 8, THREADS = 32 * WM * WN;
-  static constexpr int LDA = BM + PAD, LDB = BN + PAD;
-};
-// one warp row by two warp columns (a 32 x 64 tile of 64 threads): the fastest of
-// the shapes measured on GB300 at m^d = 729, 1331, 2197 (0.99, 1.02, 1.08 TFLOP/s;
-// cuBLAS DGEMM on the same products: 1.06, 1.07, 1.08)
-using GemmF64 = GemmF64Cfg<1, 2, 16>;
-
-__device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, double b) {
-  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
-               : "+d"(d0), "+d"(d1)
-               : "d"(a), "d"(b));
+// ---- FP64 by FP16 slices ----------------------------------------------------
+// One warp per column n of X (rows x cols, column-major, leading dimension
+// rows): F[n] = e with max_k |X(k, n)| < 2^e, slices Xs[i][n][k] (leading
+// dimension ldk >= rows, a multiple of 8; zero for k in [rows, ldk)).
+__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ X, int rows,
+                                                         int cols, int ldk, __half* __restrict__ Xs,
+                                                         int* __restrict__ F) {
+  const int col = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= cols) return;
+  const double* x = X + (int64_t)col * rows;
+  double mx = 0.0;
+  for (int k = lane; k < rows; k += 32) mx = fmax(mx, fabs(x[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
+  if (lane == 0) F[col] = e;
+  const int64_t plane = (int64_t)cols * ldk;
+  for (int k = lane; k < ldk; k += 32) {
+    double t = k < rows ? ldexp(x[k], -e) : 0.0;  // |t| < 1, exact
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i) {
+      t *= (double)(1 << kSliceBits);  // exact
+      const double q = trunc(t);       // |q| <= 63
+      t -= q;                          // exact
+      Xs[i * plane + (int64_t)col * ldk + k] = __float2half_rn((float)q);
+    }
+  }
 }
 
-template <typename C>
-__global__ void __launch_bounds__(C::THREADS) gemm_f64_kernel(int md, int cnt, double alpha,
-                                                              const double* __restrict__ A,
-                                                              const double* __restrict__ R,
-                                                              double* __restrict__ Y) {
-  __shared__ __align__(16) double As[2][C::BK][C::LDA];  // As[s][k][m] = A(m, k)
-  __shared__ __align__(16) double Bs[2][C::BK][C::LDB];  // Bs[s][k][n] = R(k, n)
+struct SlicedCfg {
+  static constexpr int BM = 128, BN = 64, BK = 32, PADK = 8, THREADS = 256;
+  static constexpr int LD = BK + PADK;  // halves per shared-memory row (80 bytes)
+  static constexpr int PAIRS = kSlices * (kSlices + 1) / 2;
+};
+
+__device__ __forceinline__ void async_copy16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void hmma_16x8x16(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Y = alpha A R from the slices: As[i][m][k] and Ea[m] of the rows of A, Rs[j][n][k] and
+// Fr[n] of the columns of R (leading dimension ldk).  A block computes a 128 x 64
+// tile with 8 warps of 32 x 32 (2 x 4 MMA tiles of 16 x 8); the (pair, k-panel)
+// sequence is one stream of 16-byte asynchronous copies, double-buffered.
+__global__ void __launch_bounds__(SlicedCfg::THREADS, 2) gemm_sliced_kernel(
+    int md, int cnt, int ldk, double alpha, const __half* __restrict__ As,
+    const int* __restrict__ Ea, const __half* __restrict__ Rs, const int* __restrict__ Fr,
+    double* __restrict__ Y) {
+  using C = SlicedCfg;
+  __shared__ __align__(16) __half sA[2][C::BM][C::LD];
+  __shared__ __align__(16) __half sB[2][C::BN][C::LD];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp % C::WM, wn = warp / C::WM;
+  const int wm = warp & 3, wn = warp >> 2;  // 4 x 2 warps
+  const int g = lane >> 2, t = lane & 3;
   const int bm0 = blockIdx.x * C::BM, bn0 = blockIdx.y * C::BN;
   const int nk = (md + C::BK - 1) / C::BK;
-
-  auto load = [&](int s, int k0) {
-    // A panel: consecutive threads take consecutive m of one column k
-    for (int e = tid; e < C::BK * C::BM; e += C::THREADS) {
-      const int k = e / C::BM, m = e % C::BM;
-      const int gm = bm0 + m, gk = k0 + k;
-      const bool in = gm < md && gk < md;
-      async_copy_or_zero(&As[s][k][m], A + (in ? (int64_t)gk * md + gm : 0), in);
+  const int64_t aplane = (int64_t)md * ldk, rplane = (int64_t)cnt * ldk;
+  // slice pairs (i, j), i + j < kSlices, the level i + j ascending
+  int pi[C::PAIRS], pj[C::PAIRS];
+  {
+    int q = 0;
+#pragma unroll
+    for (int l = 0; l < kSlices; ++l)
+#pragma unroll
+      for (int i = 0; i <= l; ++i) {
+        pi[q] = i;
+        pj[q] = l - i;
+        ++q;
+      }
+  }
+  const int total = C::PAIRS * nk;
+  auto load = [&](int st, int idx) {
+    const int pr = idx / nk, kt = idx - pr * nk;
+    const __half* Ai = As + pi[pr] * aplane;
+    const __half* Rj = Rs + pj[pr] * rplane;
+    const int k0 = kt * C::BK;
+    for (int e = tid; e < C::BM * (C::BK / 8); e += C::THREADS) {
+      const int m = e >> 2, c = e & 3, gm = bm0 + m, gk = k0 + 8 * c;
+      const bool in = gm < md && gk < ldk;
+      async_copy16(&sA[st][m][8 * c], Ai + (in ? (int64_t)gm * ldk + gk : 0), in);
     }
-    // R panel: consecutive threads take consecutive k of one column n
-    for (int e = tid; e < C::BK * C::BN; e += C::THREADS) {
-      const int k = e % C::BK, n = e / C::BK;
-      const int gk = k0 + k, gn = bn0 + n;
-      const bool in = gk < md && gn < cnt;
-      async_copy_or_zero(&Bs[s][k][n], R + (in ? (int64_t)gn * md + gk : 0), in);
+    for (int e = tid; e < C::BN * (C::BK / 8); e += C::THREADS) {
+      const int n = e >> 2, c = e & 3, gn = bn0 + n, gk = k0 + 8 * c;
+      const bool in = gn < cnt && gk < ldk;
+      async_copy16(&sB[st][n][8 * c], Rj + (in ? (int64_t)gn * ldk + gk : 0), in);
     }
     async_commit();
   };
-
-  double acc[4][4][2];
+  float acc32[2][4][4];
+  double acc64[2][4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
-
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        acc32[a][b][c] = 0.f;
+        acc64[a][b][c] = 0.0;
+      }
   load(0, 0);
-  for (int kt = 0; kt < nk; ++kt) {
-    const int s = kt & 1;
-    if (kt + 1 < nk) {
-      load(s ^ 1, (kt + 1) * C::BK);
+  for (int idx = 0; idx < total; ++idx) {
+    const int st = idx & 1;
+    if (idx + 1 < total) {
+      load(st ^ 1, idx + 1);
       async_wait_group<1>();
     } else {
       async_wait_group<0>();
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < C::BK; kk += 4) {
-      // fragments: A (8x4, row) a = A(lane/4, lane%4); B (4x8, col) b = B(lane%4, lane/4)
-      double a[4], b[4];
+    for (int kk = 0; kk < C::BK; kk += 16) {
+      // fragments of m16n8k16: A (row) rows g, g + 8 and columns 2t, 2t + 1 (+ 8);
+      // B (col) rows 2t, 2t + 1 (+ 8) and column g
+      uint32_t af[2][4], bf[4][2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[s][kk + (lane & 3)][wm * 32 + i * 8 + (lane >> 2)];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[s][kk + (lane & 3)][wn * 32 + j * 8 + (lane >> 2)];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dmma_8x8x4(acc[i][j][0], acc[i][j][1], a[i], b[j]);
-    }
-    __syncthreads();  // the stage is overwritten by the load two panels ahead
-  }
-  // D fragment: row lane/4, columns 2 (lane%4) + {0, 1}
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gm = bm0 + wm * 32 + i * 8 + (lane >> 2);
-    if (gm >= md) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int gn = bn0 + wn * 32 + j * 8 + 2 * (lane & 3) + c;
-        if (gn < cnt) Y[(int64_t)gn * md + gm] = alpha * acc[i][j][c];
+      for (int a = 0; a < 2; ++a) {
+        const int r0 = wm * 32 + a * 16 + g;
+        af[a][0] = *reinterpret_cast<const uint32_t*>(&sA[st][r0][kk + 2 * t]);
+        af[a][1] = *reinterpret_cast<const uint32_t*>(&sA[st][r0 + 8][kk + 2 * t]);
+        af[a][2] = *reinterpret_cast<const uint32_t*>(&sA[st][r0][kk + 2 * t + 8]);
+        af[a][3] = *reinterpret_cast<const uint32_t*>(&sA[st][r0 + 8][kk + 2 * t + 8]);
       }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c0 = wn * 32 + b * 8 + g;
+        bf[b][0] = *reinterpret_cast<const uint32_t*>(&sB[st][c0][kk + 2 * t]);
+        bf[b][1] = *reinterpret_cast<const uint32_t*>(&sB[st][c0][kk + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) hmma_16x8x16(acc32[a][b], af[a], bf[b]);
+    }
+    __syncthreads();  // the stage is overwritten by the copy two panels ahead
+    const int pr = idx / nk, kt = idx - pr * nk;
+    if (kt == nk - 1) {  // the pair's product is complete, an exact integer
+      const double sc = ldexp(1.0, -kSliceBits * (pi[pr] + pj[pr] + 2));
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            acc64[a][b][c] = fma((double)acc32[a][b][c], sc, acc64[a][b][c]);
+            acc32[a][b][c] = 0.f;
+          }
+    }
   }
-}
-
-template <typename C>
-cudaError_t launch_gemm_f64(int md, int cnt, double alpha, const double* A, const double* R,
-                            double* Y, cudaStream_t st) {
-  const dim3 grid((unsigned)((md + C::BM - 1) / C::BM), (unsigned)((cnt + C::BN - 1) / C::BN));
-  if (grid.y > 65535u) return cudaErrorInvalidValue;
-  gemm_f64_kernel<C><<<grid, C::THREADS, 0, st>>>(md, cnt, alpha, A, R, Y);
-  return cudaGetLastError();
+  // D fragment c: row g (+ 8 for c >= 2), column 2t + (c & 1)
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int gm = bm0 + wm * 32 + a * 16 + g + (c >= 2 ? 8 : 0);
+        const int gn = bn0 + wn * 32 + b * 8 + 2 * t + (c & 1);
+        if (gm < md && gn < cnt)
+          Y[(int64_t)gn * md + gm] = alpha * ldexp(acc64[a][b][c], Ea[gm] + Fr[gn]);
+      }
 }
 
 // ---- FP32: FFMA, 8 x 8 per thread --------------------------------------------
@@ -222,11 +297,31 @@ __global__ void __launch_bounds__(GemmF32Cfg::THREADS) gemm_f32_kernel(int md, i
 
 }  // namespace
 
-cudaError_t gemm_f64(int md, int cnt, double alpha, const double* A, const double* R, double* Y,
-                     cudaStream_t st) {
-  if (md <= 0 || cnt <= 0) return cudaSuccess;
+int slice_ld(int rows) { return (rows + 7) / 8 * 8; }
+
+cudaError_t slice_cols(const double* X, int rows, int cols, uint16_t* Xs, int* F,
+                       cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const int64_t threads = (int64_t)cols * 32;
+  slice_cols_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      X, rows, cols, slice_ld(rows), reinterpret_cast<__half*>(Xs), F);
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return launch_gemm_f64<GemmF64>(md, cnt, alpha, A, R, Y, st);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_f64_sliced(int md, int cnt, double alpha, const uint16_t* As, const int* Ea,
+                            const uint16_t* Rs, const int* Fr, double* Y, cudaStream_t st) {
+  if (md <= 0 || cnt <= 0) return cudaSuccess;
+  // the FP32 accumulation of a slice product is exact while md 63^2 < 2^24
+  if (md * 63 * 63 >= (1 << 24)) return cudaErrorInvalidValue;
+  using C = SlicedCfg;
+  const dim3 grid((unsigned)((md + C::BM - 1) / C::BM), (unsigned)((cnt + C::BN - 1) / C::BN));
+  if (grid.y > 65535u) return cudaErrorInvalidValue;
+  gemm_sliced_kernel<<<grid, C::THREADS, 0, st>>>(md, cnt, slice_ld(md), alpha,
+                                                  reinterpret_cast<const __half*>(As), Ea,
+                                                  reinterpret_cast<const __half*>(Rs), Fr, Y);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
 }
 
 cudaError_t gemm_f32(int md, int cnt, float alpha, const float* A, const float* R, float* Y,

@@ -70,11 +70,6 @@ struct Ops {
   static cudaError_t patch_scatter(const LevelGeom& g, const T* Y, const int* verts, int count,
                                    T* x, bool atomic, cudaStream_t st);
 
-  // Y = alpha A R: A md x md, R and Y md x cnt, all column-major (the dense
-  // product of the exact local solver on a run of gathered patch tensors).
-  static cudaError_t gemm(int md, int cnt, double alpha, const T* A, const T* R, T* Y,
-                          cudaStream_t st);
-
   // xf += P xc (embedding), fine geometry given; s0, s1 scratch of fine nd each.
   static cudaError_t prolongate_add(const void* tab, const LevelGeom& fine, const T* xc, T* xf,
                                     T* s0, T* s1, cudaStream_t st);
@@ -92,9 +87,21 @@ struct Ops {
 };
 
 // ---- dense products of the exact local solver (gemm.cu) ----------------------
-// Y = alpha A R: A md x md, R and Y md x cnt, all column-major.
-cudaError_t gemm_f64(int md, int cnt, double alpha, const double* A, const double* R, double* Y,
-                     cudaStream_t st);
+// FP64 by FP16 slices: kSlices slices of kSliceBits bits per value.
+constexpr int kSlices = 8, kSliceBits = 6;
+// leading dimension (FP16 values, a multiple of 8) of the slices of `rows`-long columns
+int slice_ld(int rows);
+// the slices of the columns of X (rows x cols, column-major): Xs holds kSlices
+// planes of cols x slice_ld(rows) FP16 values (as 16-bit words), F one
+// power-of-two exponent per column
+cudaError_t slice_cols(const double* X, int rows, int cols, uint16_t* Xs, int* F,
+                       cudaStream_t st);
+// Y = alpha A R (md x cnt, column-major) from the slices of the rows of A (As, Ea:
+// slice_cols of A^T, i.e. of A's columns when A is symmetric) and of the columns
+// of R (Rs, Fr)
+cudaError_t gemm_f64_sliced(int md, int cnt, double alpha, const uint16_t* As, const int* Ea,
+                            const uint16_t* Rs, const int* Fr, double* Y, cudaStream_t st);
+// FP32: Y = alpha A R, A md x md, R and Y md x cnt, all column-major.
 cudaError_t gemm_f32(int md, int cnt, float alpha, const float* A, const float* R, float* Y,
                      cudaStream_t st);
 

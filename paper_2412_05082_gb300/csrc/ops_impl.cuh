@@ -449,15 +449,6 @@ cudaError_t Ops<T>::patch_scatter(const LevelGeom& g, const T* Y, const int* ver
   return cudaErrorInvalidValue;
 }
 
-template <typename T>
-cudaError_t Ops<T>::gemm(int md, int cnt, double alpha, const T* A, const T* R, T* Y,
-                         cudaStream_t st) {
-  if constexpr (sizeof(T) == 8)
-    return gemm_f64(md, cnt, alpha, A, R, Y, st);
-  else
-    return gemm_f32(md, cnt, (float)alpha, A, R, Y, st);
-}
-
 // one transfer pass along `axis`; shapes per axis given for input and output
 template <typename T, int K, bool PROLONG>
 static cudaError_t xfer_pass(const XferTab<T, K>& tab, int d, int axis, const int* din,
