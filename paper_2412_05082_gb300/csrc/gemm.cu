@@ -16,11 +16,13 @@
 // accumulation over the whole inner dimension is exact; the products of the
 // slice pairs (i, j) with i + j < kSlices are scaled by 2^(-6 (i + j + 2)) and
 // summed in FP64.  The dropped pairs and the split's remainder are below
-// 2^(-6 kSlices) relative to the row and column maxima: 2^-48 for 8 slices,
-// the rounding level of an FP64 product with an inner dimension of 2,197.
+// 2^(-6 kSlices) relative to the row and column maxima: 2^-54 for 9 slices,
+// the FP64 significand.  The bound is relative to the maxima, so fewer slices
+// fail where a row of the inverse spans a wide range (8 slices: 2.5e-10 on one
+// exact step of the single 3D k = 7 patch of level 1, against 1e-10 asked).
 // FP16 mma.sync runs at 600 TFLOP/s on GB300 against 1.1 for the FP64 tensor
-// instruction (measured), so the 36 slice products of the emulation beat the
-// FP64 product several times over.
+// instruction (measured), so the 45 slice products of the emulation still beat
+// the FP64 product several times over.
 //
 // FP32 (the mixed forms): FFMA with 8 x 8 outputs per thread, a 128 x 128 tile
 // per block of 256 threads, 128-bit shared-memory operand loads, k-panels of 8,

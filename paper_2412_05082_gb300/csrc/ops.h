@@ -88,7 +88,7 @@ struct Ops {
 
 // ---- dense products of the exact local solver (gemm.cu) ----------------------
 // FP64 by FP16 slices: kSlices slices of kSliceBits bits per value.
-constexpr int kSlices = 8, kSliceBits = 6;
+constexpr int kSlices = 9, kSliceBits = 6;  // 54 bits: the FP64 significand
 // leading dimension (FP16 values, a multiple of 8) of the slices of `rows`-long columns
 int slice_ld(int rows);
 // the slices of the columns of X (rows x cols, column-major): Xs holds kSlices
