@@ -289,6 +289,24 @@ bh_status bh_batch_set_tile(bh_batch* batch, int degree, int patches_per_block);
  * the current right-hand sides, over reps launches after one warm-up. */
 bh_status bh_batch_vcycle_time(bh_batch* batch, int reps, double* ms);
 
+/* Persistent form of the batched V-cycle (on = 1; 0: the captured graph, the
+ * default): the whole V-cycle runs as ONE cooperative launch whose blocks walk
+ * its phases -- every color of the patch kernel, the sweeps, transfers, vector
+ * operations and coarse solves of all problems at one depth -- separated by a
+ * grid barrier.  Every barrier wait is bounded (2 s of clock cycles); a wait
+ * that runs out ends the kernel with a status word that the next call reading
+ * it turns into BH_ETIMEOUT.  Same arithmetic as the graph.  Host only. */
+bh_status bh_batch_set_persistent(bh_batch* batch, int on);
+
+/* Check of the persistent form's failure path: one persistent V-cycle whose
+ * grid barrier expects one block more than the launch has, so that the first
+ * barrier wait runs out after wait_ms (0 < wait_ms <= 10000) and every block
+ * leaves the kernel; returns BH_ETIMEOUT (BH_EINVAL if the barrier had
+ * completed).  No device fault, trap or unbounded wait is involved; the
+ * batch's internal vectors are left undefined, the caller's are not touched.
+ * Synchronous. */
+bh_status bh_batch_check_barrier_timeout(bh_batch* batch, double wait_ms);
+
 /* One batched V-cycle from zero: x_dev[i] = MG_L(0, b_dev[i]) (Algorithm 1)
  * for every problem i, by the captured graph in the batch's precision (the
  * preconditioner that bh_batch_solve applies).  b_dev, x_dev: host arrays of

@@ -78,6 +78,8 @@ SIGNATURES = {
     "bh_set_tile": (_I, [_P, _I]),
     "bh_batch_vcycle_time": (_I, [_P, _I, _c.POINTER(_D)]),
     "bh_batch_vcycle": (_I, [_P, _P, _P]),
+    "bh_batch_set_persistent": (_I, [_P, _I]),
+    "bh_batch_check_barrier_timeout": (_I, [_P, _D]),
     "bh_batch_smooth_colors": (_I, [_P, _P, _P, _I, _I]),
     "bh_batch_solve": (_I, [_P, _P, _P, _D, _I, _P, _P]),
     "bh_batch_stats": (_I, [_P, _c.POINTER(_c.c_longlong)]),
@@ -379,6 +381,16 @@ class Batch:
     def set_tile(self, degree, patches_per_block):
         """bh_batch_set_tile: patches per block of the fused MVS launch of one degree."""
         _check(load().bh_batch_set_tile(self._h, degree, patches_per_block))
+
+    def set_persistent(self, on=True):
+        """bh_batch_set_persistent: the V-cycle as one cooperative launch (True)
+        or as the captured graph (False, the default)."""
+        _check(load().bh_batch_set_persistent(self._h, 1 if on else 0))
+
+    def check_barrier_timeout(self, wait_ms=50.0):
+        """bh_batch_check_barrier_timeout: the persistent kernel's bounded
+        barrier wait made to run out; returns the status code (BH_ETIMEOUT)."""
+        return load().bh_batch_check_barrier_timeout(self._h, float(wait_ms))
 
     def vcycle_time(self, reps=5):
         """bh_batch_vcycle_time: device time (ms) of one replay of the batch's V-cycle graph."""

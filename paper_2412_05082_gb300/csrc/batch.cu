@@ -29,6 +29,8 @@
 #include "ctx.h"
 #include "ops_impl.cuh"
 
+#include <cuda_runtime_api.h>
+
 namespace bh {
 void set_last_error(const std::string& msg);  // api.cu
 bool alloc_fault();                           // api.cu: host-side fault injection
@@ -280,6 +282,187 @@ __global__ void dot_batch_final(const int64_t* cprefix, const int* pid, int n,
 }
 
 // ---------------------------------------------------------------------------
+// persistent form: the whole V-cycle in one cooperative launch
+// ---------------------------------------------------------------------------
+// The V-cycle's level operations become phases of one kernel: every block
+// walks the phase list; inside a phase the blocks share its work list (tiles
+// of the patch kernel, threads of the sweeps, transfers, vector operations and
+// the coarse solve); a grid barrier separates the phases.
+enum PhaseKind : int {
+  kPhMvs = 0,      // colored-MVS tiles (value type of the V-cycle)
+  kPhSweep0 = 1,   // FP64 x-split sweep
+  kPhSweep2 = 2,   // FP64 y-combination (residual)
+  kPhRestr = 3,    // FP64 restriction pass
+  kPhProl = 4,     // prolongation pass (value type of the V-cycle)
+  kPhZero = 5,     // zero vectors (value type of the V-cycle)
+  kPhCoarse = 6,   // coarse solve (value type of the V-cycle)
+  kPhConv = 7      // FP64 <-> FP32 conversions
+};
+
+struct MvsGroup {  // the tiles of one degree in an MVS phase
+  const void* args;  // MvsArgs<T>[]
+  const int* pid;
+  const Tile* tiles;
+  int ntiles;
+};
+
+struct Phase {
+  int kind;
+  int n;              // entries of the work list
+  int64_t total;      // items: threads, or tiles (MVS), or (problem, row) pairs (coarse)
+  const void* args;   // SweepArgs / XferArgs / Vec / Conv / Symv entries
+  const int64_t* prefix;
+  const int* pid;
+  int dir;            // conversion direction
+  int maxn;           // coarse: largest coarse size
+  int ngroups;        // MVS: degree groups
+  MvsGroup groups[kMaxK + 1];
+};
+
+// Grid barrier with a bounded wait: thread 0 of every block arrives on a
+// counter; the last one to arrive resets it and advances the generation, the
+// others spin on the generation for at most `budget` clock cycles.  A wait
+// that runs out sets *status (1) and every block leaves the kernel at its next
+// barrier, so a barrier that can never complete (fewer co-resident blocks than
+// `expected`) ends the kernel with an error status instead of a hang.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned expected,
+                                             int* status, long long budget) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = gen;
+    volatile int* vstatus = status;
+    const unsigned g = *vgen;
+    __threadfence();  // this block's writes of the phase before its arrival
+    if (atomicAdd(count, 1u) == expected - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (*vstatus != 0 || clock64() - t0 > budget) {
+          atomicExch(status, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) vcycle_persistent_kernel(
+    Meta m64, Meta mT, const Phase* __restrict__ phases, int nphases, unsigned* bar,
+    unsigned expected, int* status, long long budget) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int f = 0; f < nphases; ++f) {
+    const Phase& P = phases[f];
+    const int kind = P.kind;
+    if (kind == kPhSweep0 || kind == kPhSweep2) {
+      const SweepArgs<double>* args = static_cast<const SweepArgs<double>*>(P.args);
+      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
+        const int s = find_seg(P.prefix, P.n, tid);
+        const int p = P.pid[s];
+        if (!m64.active[p]) continue;
+        const int64_t local = tid - P.prefix[s];
+#define BH_CALL(KK)                                                                              \
+  if (kind == kPhSweep0)                                                                         \
+    sweep_thread<double, KK, 0, true>(static_cast<const Tables<double, KK>*>(m64.tabs[p])->op,    \
+                                      args[s], local);                                           \
+  else                                                                                           \
+    sweep_thread<double, KK, 2, true>(static_cast<const Tables<double, KK>*>(m64.tabs[p])->op,    \
+                                      args[s], local)
+        BH_KSWITCH(m64.k[p], BH_CALL)
+#undef BH_CALL
+      }
+    } else if (kind == kPhRestr) {
+      const XferArgs<double>* args = static_cast<const XferArgs<double>*>(P.args);
+      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
+        const int s = find_seg(P.prefix, P.n, tid);
+        const int p = P.pid[s];
+        if (!m64.active[p]) continue;
+        const int64_t local = tid - P.prefix[s];
+#define BH_CALL(KK) \
+  restrict_thread<double, KK>(static_cast<const Tables<double, KK>*>(m64.tabs[p])->xfer, args[s], local)
+        BH_KSWITCH(m64.k[p], BH_CALL)
+#undef BH_CALL
+      }
+    } else if (kind == kPhProl) {
+      const XferArgs<T>* args = static_cast<const XferArgs<T>*>(P.args);
+      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
+        const int s = find_seg(P.prefix, P.n, tid);
+        const int p = P.pid[s];
+        if (!mT.active[p]) continue;
+        const int64_t local = tid - P.prefix[s];
+#define BH_CALL(KK) \
+  prolong_thread<T, KK>(static_cast<const Tables<T, KK>*>(mT.tabs[p])->xfer, args[s], local)
+        BH_KSWITCH(mT.k[p], BH_CALL)
+#undef BH_CALL
+      }
+    } else if (kind == kPhZero) {
+      const Vec<T>* v = static_cast<const Vec<T>*>(P.args);
+      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
+        const int s = find_seg(P.prefix, P.n, tid);
+        if (!mT.active[P.pid[s]]) continue;
+        v[s].y[tid - P.prefix[s]] = T(0);
+      }
+    } else if (kind == kPhConv) {
+      const Conv* v = static_cast<const Conv*>(P.args);
+      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
+        const int s = find_seg(P.prefix, P.n, tid);
+        if (!m64.active[P.pid[s]]) continue;
+        const int64_t i = tid - P.prefix[s];
+        if (P.dir == kD2F)
+          v[s].f[i] = (float)v[s].d[i];
+        else
+          v[s].d[i] = (double)v[s].f[i];
+      }
+    } else if (kind == kPhCoarse) {
+      const Symv<T>* ops = static_cast<const Symv<T>*>(P.args);
+      for (int64_t it = gtid; it < P.total; it += gthreads) {
+        const int s = (int)(it / P.maxn), i = (int)(it - (int64_t)s * P.maxn);
+        const Symv<T> o = ops[s];
+        if (i >= o.n || !mT.active[P.pid[s]]) continue;
+        double acc = 0.0;
+        for (int j = 0; j < o.n; ++j) acc = fma(o.A[(int64_t)j * o.n + i], (double)o.b[j], acc);
+        o.x[i] = (T)(o.scale * acc);
+      }
+    } else {  // kPhMvs: one tile per block at a time, the degree groups one after another
+      for (int64_t t = blockIdx.x; t < P.total; t += gridDim.x) {
+        int g = 0;
+        int64_t tl = t;
+        while (g + 1 < P.ngroups && tl >= P.groups[g].ntiles) tl -= P.groups[g++].ntiles;
+        const MvsGroup G = P.groups[g];
+        const Tile tile = G.tiles[tl];
+        const MvsArgs<T>* args = static_cast<const MvsArgs<T>*>(G.args);
+        const int p = G.pid[tile.s];
+        __syncthreads();  // the previous tile's last stage still reads shared memory
+        if (!mT.active[p]) continue;
+#define BH_CALL(KK)                                                                           \
+  {                                                                                           \
+    const auto* tb = static_cast<const Tables<T, KK>*>(mT.tabs[p]);                           \
+    if (KK <= kBatchInteriorMaxK && mvs2_tile_is_interior(args[tile.s], tile.first, tile.count)) \
+      mvs2_tile_interior<T, KK>(tb->op, tb->fdm, args[tile.s], tile.first, tile.count, smem_raw); \
+    else                                                                                      \
+      mvs2_tile<T, KK>(tb->op, tb->fdm, args[tile.s], tile.first, tile.count, smem_raw);       \
+  }
+        BH_KSWITCH(mT.k[p], BH_CALL)
+#undef BH_CALL
+      }
+    }
+    if (f + 1 < nphases && !grid_barrier(bar, bar + 1, expected, status, budget)) return;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 template <typename A>
@@ -400,6 +583,15 @@ struct bh_batch {
   std::vector<cudaEvent_t> join;
   long long launches = 0;        // kernels run by the batch (graph replays count their nodes)
   long long graph_kernels = 0;   // kernel nodes of the captured V-cycle graph
+  // persistent form: the V-cycle's phases for one cooperative launch
+  bool persistent = false;
+  Phase* d_phases = nullptr;
+  int nphases = 0;
+  size_t psmem = 0;              // dynamic shared memory of the persistent kernel
+  int pgrid = 0;                 // its co-resident grid
+  unsigned* d_bar = nullptr;     // [count, generation, status, -]
+  int* h_status = nullptr;       // pinned copy of the status word
+  long long budget_cycles = 0;   // bounded barrier wait (clock64 cycles)
   std::vector<int> last_iters;
 };
 
@@ -852,6 +1044,8 @@ cudaError_t run_colors(bh_batch* b, const VDepth<T>& V, int c0, int c1) {
   return cudaSuccess;
 }
 
+struct TopOps;
+template <typename T> const VecOpList<T>& vdepth_top(const TopOps& top);
 template <typename T> const VDepth<T>& vdepth(const Depth& D);
 template <> const VDepth<double>& vdepth<double>(const Depth& D) { return D.v64; }
 template <> const VDepth<float>& vdepth<float>(const Depth& D) { return D.v32; }
@@ -891,15 +1085,18 @@ cudaError_t vcycle_from(bh_batch* b, int t) {
 // The captured graph: x64_L = MG(0, b64_L) for every problem.  FP64: zero
 // x64_L, V-cycle.  R64: zero x32_L, b32_L = b64_L, FP32 V-cycle (FP64 defects
 // against b64_L on the finest level), x64_L = x32_L.
-bh_status capture_vcycle(bh_batch* b) {
-  if (b->gexec) {
-    cudaGraphExecDestroy(b->gexec);
-    b->gexec = nullptr;
-  }
-  if (b->graph) {
-    cudaGraphDestroy(b->graph);
-    b->graph = nullptr;
-  }
+// the first and last operations of the V-cycle (x_L zeroed, and for the FP32
+// V-cycle the conversions of b_L and x_L), built once per prepare()
+struct TopOps {
+  VecOpList<double> zero64;
+  VecOpList<float> zero32;
+  ConvOpList cin, cout_;
+};
+
+template <> const VecOpList<double>& vdepth_top<double>(const TopOps& top) { return top.zero64; }
+template <> const VecOpList<float>& vdepth_top<float>(const TopOps& top) { return top.zero32; }
+
+bh_status build_top(bh_batch* b, TopOps& top) {
   std::vector<std::pair<int, Vec<double>>> zf64;
   std::vector<std::pair<int, Vec<float>>> zf32;
   std::vector<std::pair<int, Conv>> bin, xout;
@@ -910,16 +1107,28 @@ bh_status capture_vcycle(bh_batch* b) {
     bin.push_back({p, Conv{F.b64, F.b32, F.g.nd, 0}});
     xout.push_back({p, Conv{F.x64, F.x32, F.g.nd, 0}});
   }
-  VecOpList<double> zero64;
-  VecOpList<float> zero32;
-  ConvOpList cin, cout_;
   if (b->mixed) {
-    BCKS(make_vec(b, zf32, zero32));
-    BCKS(make_conv(b, bin, cin));
-    BCKS(make_conv(b, xout, cout_));
+    BCKS(make_vec(b, zf32, top.zero32));
+    BCKS(make_conv(b, bin, top.cin));
+    BCKS(make_conv(b, xout, top.cout_));
   } else {
-    BCKS(make_vec(b, zf64, zero64));
+    BCKS(make_vec(b, zf64, top.zero64));
   }
+  return BH_OK;
+}
+
+bh_status capture_vcycle(bh_batch* b, const TopOps& top) {
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  const VecOpList<double>& zero64 = top.zero64;
+  const VecOpList<float>& zero32 = top.zero32;
+  const ConvOpList &cin = top.cin, &cout_ = top.cout_;
   const long long before = b->launches, before_g = g_kernel_launches.load();
   BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
   cudaError_t e;
@@ -958,9 +1167,28 @@ bh_status set_active(bh_batch* b, const std::vector<int>& act) {
   return BH_OK;
 }
 
+bh_status launch_persistent(bh_batch* b, unsigned extra, long long budget);
+
+// one V-cycle x64_L = MG(0, b64_L): the captured graph, or the persistent kernel
 bh_status launch_graph(bh_batch* b) {
+  if (b->persistent) return launch_persistent(b, 0, b->budget_cycles);
   BCK(cudaGraphLaunch(b->gexec, b->st));
   count_launch(b, (int)b->graph_kernels);
+  return BH_OK;
+}
+
+// clear the persistent kernel's status word (before a call) / read it (after
+// a synchronization): BH_ETIMEOUT if a bounded barrier wait ran out
+bh_status clear_status(bh_batch* b) {
+  if (!b->persistent) return BH_OK;
+  BCK(cudaMemsetAsync(b->d_bar + 2, 0, sizeof(unsigned), b->st));
+  *b->h_status = 0;
+  return BH_OK;
+}
+
+bh_status check_status(const bh_batch* b) {
+  if (b->persistent && *b->h_status != 0)
+    return berr(BH_ETIMEOUT, "persistent V-cycle: a grid-barrier wait ran out (status word set)");
   return BH_OK;
 }
 
@@ -975,6 +1203,142 @@ bh_status raise_smem_limit(size_t smem) {
   if ((int)smem > fa.maxDynamicSharedSizeBytes)
     BCK(cudaFuncSetAttribute(mvs2_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem));
+  return BH_OK;
+}
+
+// ---- persistent form: the phase list of one V-cycle ------------------------
+template <typename T>
+struct PhaseBuilder {
+  std::vector<Phase>& ph;
+  size_t smem = 0;
+  void list(int kind, int n, int64_t total, const void* args, const int64_t* prefix,
+            const int* pid, int dir = 0) {
+    if (total <= 0) return;
+    Phase P{};
+    P.kind = kind;
+    P.n = n;
+    P.total = total;
+    P.args = args;
+    P.prefix = prefix;
+    P.pid = pid;
+    P.dir = dir;
+    ph.push_back(P);
+  }
+  void sweep(const SweepOp<double>& op, int kind) {
+    list(kind, op.pid.n, op.total, op.args.d, op.prefix.d, op.pid.d);
+  }
+  template <typename U>
+  void xfer(const XferOp<U>& op, int kind) {
+    list(kind, op.pid.n, op.total, op.args.d, op.prefix.d, op.pid.d);
+  }
+  void zero(const VecOpList<T>& op) { list(kPhZero, op.pid.n, op.total, op.v.d, op.prefix.d, op.pid.d); }
+  void conv(const ConvOpList& op, int dir) {
+    list(kPhConv, op.pid.n, op.total, op.v.d, op.prefix.d, op.pid.d, dir);
+  }
+  void mvs(const std::vector<MvsOp<T>>& ops) {
+    if (ops.empty()) return;
+    Phase P{};
+    P.kind = kPhMvs;
+    for (const MvsOp<T>& op : ops) {
+      MvsGroup& G = P.groups[P.ngroups++];
+      G.args = op.args.d;
+      G.pid = op.pid.d;
+      G.tiles = op.tiles.d;
+      G.ntiles = op.tiles.n;
+      P.total += op.tiles.n;
+      smem = std::max(smem, op.smem);
+    }
+    ph.push_back(P);
+  }
+};
+
+// the phases in the order of vcycle_from: per depth (descending) the coarse
+// solve, pre-smoothing, defect, restriction and zeroed coarse iterate; per
+// depth (ascending) the prolongation and post-smoothing
+template <typename T>
+bh_status build_phases(bh_batch* b, const TopOps& top) {
+  std::vector<Phase> ph;
+  PhaseBuilder<T> B{ph};
+  const int T_ = (int)b->depth.size();
+  if (b->mixed) {
+    B.zero(vdepth_top<T>(top));
+    B.conv(top.cin, kD2F);
+  } else {
+    B.zero(vdepth_top<T>(top));
+  }
+  for (int t = 0; t < T_; ++t) {
+    const Depth& D = b->depth[t];
+    const VDepth<T>& V = vdepth<T>(D);
+    if (D.coarse) {
+      Phase P{};
+      P.kind = kPhCoarse;
+      P.n = D.nsymv;
+      P.maxn = D.maxn_symv;
+      P.total = (int64_t)D.nsymv * D.maxn_symv;
+      P.args = V.symv.d;
+      P.pid = D.symv_pid.d;
+      ph.push_back(P);
+    }
+    if (!D.smooth) break;  // no deeper depth holds smoothing work
+    for (int s = 0; s < b->pre; ++s)
+      for (int col = 0; col < 8; ++col) B.mvs(V.mvs[col]);
+    if (b->mixed) B.conv(D.x_f2d, kF2D);
+    B.sweep(D.res_x, kPhSweep0);
+    B.sweep(D.res_y, kPhSweep2);
+    B.xfer(D.restr[0], kPhRestr);
+    B.xfer(D.restr[1], kPhRestr);
+    if (b->mixed) B.conv(D.b_d2f, kD2F);
+    B.zero(V.zero_coarse);
+  }
+  for (int t = T_ - 1; t >= 0; --t) {
+    const Depth& D = b->depth[t];
+    if (!D.smooth) continue;
+    const VDepth<T>& V = vdepth<T>(D);
+    B.xfer(V.prol[0], kPhProl);
+    B.xfer(V.prol[1], kPhProl);
+    for (int s = 0; s < b->post; ++s)
+      for (int col = 0; col < 8; ++col) B.mvs(V.mvs[col]);
+  }
+  if (b->mixed) B.conv(top.cout_, kF2D);
+  DevArray<Phase> dph;
+  BCKS(upload(b, ph, dph));
+  b->d_phases = dph.d;
+  b->nphases = (int)ph.size();
+  b->psmem = std::max<size_t>(B.smem, 64);
+  // co-resident grid of the cooperative launch
+  auto kernel = vcycle_persistent_kernel<T>;
+  BCK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->psmem));
+  int per_sm = 0, dev = 0, sms = 0, clock_khz = 0, coop = 0;
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, b->psmem));
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  BCK(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
+  BCK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (per_sm < 1 || !coop)
+    return berr(BH_EINVAL, "persistent V-cycle: no co-resident block fits (tile too large)");
+  b->pgrid = per_sm * sms;
+  b->budget_cycles = (long long)clock_khz * 2000;  // a 2 s bound on one barrier wait
+  return BH_OK;
+}
+
+// one persistent V-cycle: x64_L = MG(0, b64_L) for every problem; `extra`
+// more arrivals than the grid provides make every barrier wait run out
+// (the failure-path check), with a wait of `budget` cycles
+bh_status launch_persistent(bh_batch* b, unsigned extra, long long budget) {
+  BCK(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->st));  // count, generation
+  Meta m64 = meta<double>(b);
+  Meta mT = b->mixed ? meta<float>(b) : meta<double>(b);
+  const Phase* phases = b->d_phases;
+  int nph = b->nphases;
+  unsigned* bar = b->d_bar;
+  unsigned expected = (unsigned)b->pgrid + extra;
+  int* status = reinterpret_cast<int*>(b->d_bar + 2);
+  void* args[] = {&m64, &mT, &phases, &nph, &bar, &expected, &status, &budget};
+  const void* kernel = b->mixed ? (const void*)vcycle_persistent_kernel<float>
+                                : (const void*)vcycle_persistent_kernel<double>;
+  BCK(cudaLaunchCooperativeKernel(kernel, dim3(b->pgrid), dim3(256), args, b->psmem, b->st));
+  count_launch(b);
+  BCK(cudaMemcpyAsync(b->h_status, status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
   return BH_OK;
 }
 
@@ -1002,7 +1366,21 @@ bh_status prepare(bh_batch* b) {
     b->join.push_back(ev);
   }
   BCKS(build_depths(b));
-  return capture_vcycle(b);
+  TopOps top;
+  BCKS(build_top(b, top));
+  BCKS(capture_vcycle(b, top));
+  if (!b->d_bar) {
+    DevArray<unsigned> bar;
+    BCKS(upload(b, std::vector<unsigned>(4, 0u), bar));
+    b->d_bar = bar.d;
+    if (cudaMallocHost((void**)&b->h_status, sizeof(int)) != cudaSuccess) {
+      b->h_status = nullptr;
+      cudaGetLastError();
+      return berr(BH_ENOMEM, "cudaMallocHost failed");
+    }
+    *b->h_status = 0;
+  }
+  return b->mixed ? build_phases<float>(b, top) : build_phases<double>(b, top);
 }
 
 bh_status ensure_plan(bh_batch* b) {
@@ -1221,6 +1599,7 @@ bh_status bh_batch_destroy(bh_batch* b) {
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);
   for (cudaStream_t st : b->side) cudaStreamDestroy(st);
   if (b->st) cudaStreamDestroy(b->st);
+  if (b->h_status) cudaFreeHost(b->h_status);
   delete b->plan;
   delete b;
   return BH_OK;
@@ -1236,6 +1615,32 @@ bh_status bh_batch_set_tile(bh_batch* b, int degree, int patches_per_block) {
   return prepare(b);
 }
 
+bh_status bh_batch_set_persistent(bh_batch* b, int on) {
+  if (!b || (on != 0 && on != 1)) return berr(BH_EINVAL, "bh_batch_set_persistent: bad arguments");
+  b->persistent = on == 1;
+  return BH_OK;
+}
+
+bh_status bh_batch_check_barrier_timeout(bh_batch* b, double wait_ms) {
+  if (!b || !(wait_ms > 0.0) || wait_ms > 10000.0)
+    return berr(BH_EINVAL, "bh_batch_check_barrier_timeout: wait_ms must be in (0, 10000]");
+  int dev = 0, clock_khz = 0;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
+  std::vector<int> act(b->P, 1);
+  BCKS(set_active(b, act));
+  BCKS(wait_user(b));
+  const bool was = b->persistent;
+  b->persistent = true;
+  bh_status s = clear_status(b);
+  if (s == BH_OK) s = launch_persistent(b, 1u, (long long)(clock_khz * wait_ms));
+  b->persistent = was;
+  if (s != BH_OK) return s;
+  BCK(cudaStreamSynchronize(b->st));
+  if (*b->h_status == 0) return berr(BH_EINVAL, "barrier check: the barrier completed");
+  return berr(BH_ETIMEOUT, "barrier check: the bounded grid-barrier wait ran out as arranged");
+}
+
 bh_status bh_batch_vcycle_time(bh_batch* b, int reps, double* ms) {
   if (!b || reps < 1 || !ms) return berr(BH_EINVAL, "bad arguments");
   std::vector<int> act(b->P, 1);
@@ -1244,15 +1649,17 @@ bh_status bh_batch_vcycle_time(bh_batch* b, int reps, double* ms) {
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
-  BCK(cudaGraphLaunch(b->gexec, b->st));
+  BCKS(clear_status(b));
+  BCKS(launch_graph(b));
   BCK(cudaEventRecord(e0, b->st));
-  for (int r = 0; r < reps; ++r) BCK(cudaGraphLaunch(b->gexec, b->st));
+  for (int r = 0; r < reps; ++r) BCKS(launch_graph(b));
   BCK(cudaEventRecord(e1, b->st));
   BCK(cudaEventSynchronize(e1));
   float t = 0.f;
   BCK(cudaEventElapsedTime(&t, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  BCKS(check_status(b));
   *ms = t / reps;
   return BH_OK;
 }
@@ -1272,8 +1679,10 @@ bh_status bh_batch_vcycle(bh_batch* b, const double* const* b_dev, double* const
     xl[p] = F.x64;
   }
   BCKS(copy_lists(b, bl.data(), b_dev));
+  BCKS(clear_status(b));
   BCKS(launch_graph(b));
-  BCKS(copy_lists(b, x_dev, xl.data()));
+  BCKS(copy_lists(b, x_dev, xl.data()));  // synchronizes the batch's stream
+  BCKS(check_status(b));
   return signal_user(b);
 }
 
@@ -1368,6 +1777,7 @@ bh_status bh_batch_solve(bh_batch* b, const double* const* b_dev, double* const*
   }
   std::vector<int> act(P, 1);
   BCKS(set_active(b, act));
+  BCKS(clear_status(b));
   BCK(run_vec<double>(b, S.zero_x, kZero, nullptr, 0, 0, 0.0));
   // r0 = b (right, in r64_L) or M^-1 b (left, in x64_L); beta = ||r0||, ||b||
   BCK(run_vec<double>(b, S.copy_b, kCopy, nullptr, 0, 0, 0.0));
@@ -1381,6 +1791,7 @@ bh_status bh_batch_solve(bh_batch* b, const double* const* b_dev, double* const*
   std::vector<double>& hd = S.hd;
   BCK(cudaMemcpyAsync(hd.data(), b->d_dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st));
   BCK(cudaStreamSynchronize(b->st));
+  BCKS(check_status(b));
   std::vector<double> beta(P), bnorm(P), ref(P);
   for (int p = 0; p < P; ++p) {
     beta[p] = std::sqrt(hd[(size_t)p * cs]);
@@ -1435,6 +1846,7 @@ bh_status bh_batch_solve(bh_batch* b, const double* const* b_dev, double* const*
       BCK(cudaMemcpyAsync(hd.data(), b->d_dots, hd.size() * sizeof(double), cudaMemcpyDeviceToHost,
                           b->st));
       BCK(cudaStreamSynchronize(b->st));
+      BCKS(check_status(b));
       bool changed = false;
       for (int p = 0; p < P; ++p) {
         if (!act[p]) continue;

@@ -97,14 +97,18 @@ struct SweepArgs {
 };
 
 // window w[j] = value at node c K - 2K + j, j in [LO, HI), zero outside 1..n;
-// row c K + q (q = 0..K-1) with band offset t reads w[q + t + 2K]
-template <typename T, int K, int LO, int HI>
+// row c K + q (q = 0..K-1) with band offset t reads w[q + t + 2K].  A sweep
+// kernel reads its inputs through the read-only data path (__ldg); a kernel
+// that writes them itself in an earlier phase (the persistent V-cycle) takes
+// COHERENT = true and plain loads.
+template <typename T, int K, int LO, int HI, bool COHERENT = false>
 __device__ __forceinline__ void load_window(const T* __restrict__ p, int64_t base,
                                             int64_t stride, int c, int n, T* w) {
 #pragma unroll
   for (int j = LO; j < HI; ++j) {
     const int g = c * K - 2 * K + j;
-    w[j] = (g >= 1 && g <= n) ? __ldg(p + base + (int64_t)(g - 1) * stride) : T(0);
+    const T* src = p + base + (int64_t)(g - 1) * stride;
+    w[j] = (g >= 1 && g <= n) ? (COHERENT ? *src : __ldg(src)) : T(0);
   }
 }
 
@@ -128,7 +132,7 @@ __device__ __forceinline__ void band_acc(const T (&tab)[3 * K + 1][4 * K + 1], c
 //                (in0 = T_M, in1 = T_L, in2 = T_B)
 // KIND 2: final2d y = B in0 + 2 L in1 + M in2  (in = T_M, T_L, T_B)
 // KIND 3: final3d y = M in0 + B in1 + L in2    (in = U_M, U_B, U_L)
-template <typename T, int K, int KIND, bool CANON>
+template <typename T, int K, int KIND, bool CANON, bool COHERENT = false>
 __device__ __forceinline__ void sweep_cell(const OpTab<T, K>& tab, const SweepArgs<T>& a,
                                            int64_t base, int c, const int* cls) {
   constexpr int W = 4 * K + 1;  // B band reaches node offsets -2K..2K of every row
@@ -138,7 +142,7 @@ __device__ __forceinline__ void sweep_cell(const OpTab<T, K>& tab, const SweepAr
     T aM[K], aL[K], aB[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) aM[q] = aL[q] = aB[q] = T(0);
-    load_window<T, K, 0, W>(a.in[0], base, a.stride, c, a.n, w);
+    load_window<T, K, 0, W, COHERENT>(a.in[0], base, a.stride, c, a.n, w);
     band_acc<T, K, 0, CANON>(tab.M, cls, w, aM, T(1));
     band_acc<T, K, 1, CANON>(tab.L, cls, w, aL, T(1));
     band_acc<T, K, 2, CANON>(tab.B, cls, w, aB, T(1));
@@ -155,14 +159,14 @@ __device__ __forceinline__ void sweep_cell(const OpTab<T, K>& tab, const SweepAr
     T u0[K], u1[K], u2[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) u0[q] = u1[q] = u2[q] = T(0);
-    load_window<T, K, 0, W>(a.in[0], base, a.stride, c, a.n, w);  // T_M
+    load_window<T, K, 0, W, COHERENT>(a.in[0], base, a.stride, c, a.n, w);  // T_M
     band_acc<T, K, 2, CANON>(tab.B, cls, w, u0, T(1));
     band_acc<T, K, 0, CANON>(tab.M, cls, w, u1, T(1));
     band_acc<T, K, 1, CANON>(tab.L, cls, w, u2, T(2));
-    load_window<T, K, K, WML>(a.in[1], base, a.stride, c, a.n, w);  // T_L
+    load_window<T, K, K, WML, COHERENT>(a.in[1], base, a.stride, c, a.n, w);  // T_L
     band_acc<T, K, 1, CANON>(tab.L, cls, w, u0, T(2));
     band_acc<T, K, 0, CANON>(tab.M, cls, w, u2, T(2));
-    load_window<T, K, K, WML>(a.in[2], base, a.stride, c, a.n, w);  // T_B
+    load_window<T, K, K, WML, COHERENT>(a.in[2], base, a.stride, c, a.n, w);  // T_B
     band_acc<T, K, 0, CANON>(tab.M, cls, w, u0, T(1));
 #pragma unroll
     for (int q = 0; q < K; ++q) {
@@ -178,18 +182,18 @@ __device__ __forceinline__ void sweep_cell(const OpTab<T, K>& tab, const SweepAr
 #pragma unroll
     for (int q = 0; q < K; ++q) y[q] = T(0);
     if (KIND == 2) {
-      load_window<T, K, 0, W>(a.in[0], base, a.stride, c, a.n, w);
+      load_window<T, K, 0, W, COHERENT>(a.in[0], base, a.stride, c, a.n, w);
       band_acc<T, K, 2, CANON>(tab.B, cls, w, y, T(1));
-      load_window<T, K, K, WML>(a.in[1], base, a.stride, c, a.n, w);
+      load_window<T, K, K, WML, COHERENT>(a.in[1], base, a.stride, c, a.n, w);
       band_acc<T, K, 1, CANON>(tab.L, cls, w, y, T(2));
-      load_window<T, K, K, WML>(a.in[2], base, a.stride, c, a.n, w);
+      load_window<T, K, K, WML, COHERENT>(a.in[2], base, a.stride, c, a.n, w);
       band_acc<T, K, 0, CANON>(tab.M, cls, w, y, T(1));
     } else {
-      load_window<T, K, K, WML>(a.in[0], base, a.stride, c, a.n, w);
+      load_window<T, K, K, WML, COHERENT>(a.in[0], base, a.stride, c, a.n, w);
       band_acc<T, K, 0, CANON>(tab.M, cls, w, y, T(1));
-      load_window<T, K, 0, W>(a.in[1], base, a.stride, c, a.n, w);
+      load_window<T, K, 0, W, COHERENT>(a.in[1], base, a.stride, c, a.n, w);
       band_acc<T, K, 2, CANON>(tab.B, cls, w, y, T(1));
-      load_window<T, K, K, WML>(a.in[2], base, a.stride, c, a.n, w);
+      load_window<T, K, K, WML, COHERENT>(a.in[2], base, a.stride, c, a.n, w);
       band_acc<T, K, 1, CANON>(tab.L, cls, w, y, T(1));
     }
     const T sc = (T)a.scale;
@@ -204,7 +208,7 @@ __device__ __forceinline__ void sweep_cell(const OpTab<T, K>& tab, const SweepAr
 }
 
 // one thread of a sweep: thread index tid in [0, lines * N)
-template <typename T, int K, int KIND>
+template <typename T, int K, int KIND, bool COHERENT = false>
 __device__ __forceinline__ void sweep_thread(const OpTab<T, K>& tab, const SweepArgs<T>& a,
                                              int64_t tid) {
   int64_t line;
@@ -220,7 +224,7 @@ __device__ __forceinline__ void sweep_thread(const OpTab<T, K>& tab, const Sweep
   int64_t strides[3] = {1, (int64_t)a.n, (int64_t)a.n * a.n};
   const int64_t base = line_offset(line, a.d, a.axis, dims, strides);
   if (c >= 2 && c <= a.N - 2) {
-    sweep_cell<T, K, KIND, true>(tab, a, base, c, nullptr);
+    sweep_cell<T, K, KIND, true, COHERENT>(tab, a, base, c, nullptr);
   } else {
     int cls[K];
 #pragma unroll
@@ -228,7 +232,7 @@ __device__ __forceinline__ void sweep_thread(const OpTab<T, K>& tab, const Sweep
       const int g = c * K + q;
       cls[q] = (g >= 1) ? row_class<K>(g, a.N) : 0;
     }
-    sweep_cell<T, K, KIND, false>(tab, a, base, c, cls);
+    sweep_cell<T, K, KIND, false, COHERENT>(tab, a, base, c, cls);
   }
 }
 

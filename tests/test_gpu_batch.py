@@ -324,3 +324,55 @@ def test_two_live_batches_with_different_tile_memory(bh):
     assert its2 == its1
     for a, b in zip(xs1, again):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "r64"])
+def test_persistent_vcycle_equals_the_graph_and_the_oracle(bh, precision):
+    """The persistent form (one cooperative launch walking the V-cycle's phases
+    with a grid barrier between them) runs the same per-problem arithmetic as
+    the captured graph: one V-cycle equals the graph's to rounding and, in
+    FP64, the oracle's Algorithm 1 to 1e-10; a right-preconditioned solve takes
+    the same iterations and reaches the 1e-8 true residual."""
+    Hs = hierarchies()
+    bs = [rhs_rough_solution(H.A[H.L], 600 + i)[0] for i, H in enumerate(Hs)]
+    prec = bh.FP64 if precision == "fp64" else bh.MIXED_FP32_R64
+    with bh.Batch([bh.default_params(d, k, L, precision=prec) for d, k, L in MIX]) as batch:
+        B = [cuda(b) for b in bs]
+        Xg = [torch.empty_like(v) for v in B]
+        Xp = [torch.empty_like(v) for v in B]
+        batch.vcycle(B, Xg)
+        its_g, rr_g = batch.solve(B, [torch.empty_like(v) for v in B], 1e-8, 100)
+        batch.set_persistent(True)
+        batch.vcycle(B, Xp)
+        its_p, rr_p = batch.solve(B, [torch.empty_like(v) for v in B], 1e-8, 100)
+        for (d, k, L), H, b, xg, xp in zip(MIX, Hs, bs, Xg, Xp):
+            assert relerr(host(xp), host(xg)) <= (1e-13 if precision == "fp64" else 1e-6), (k, L)
+            if precision == "fp64":
+                ref = H.vcycle(H.L, np.zeros_like(b), b)
+                assert relerr(host(xp), ref) <= 1e-10, (k, L)
+        assert its_p == its_g
+        assert all(r <= 1.0001e-8 for r in rr_p)
+
+
+def test_persistent_barrier_wait_is_bounded(bh):
+    """The persistent kernel's grid barrier made to expect one block more than
+    the launch has: every block's wait runs out after the given bound, the
+    kernel ends with its status word set (BH_ETIMEOUT, no fault, no hang), and
+    the batch keeps working afterwards in both forms."""
+    import time
+    probs = [(2, 2, 4), (2, 5, 3)]
+    Hs = [mg.Hierarchy(d, k, L) for d, k, L in probs]
+    bs = [workload.rhs_uniform(H.A[H.L].shape[0], 700 + i) for i, H in enumerate(Hs)]
+    with bh.Batch([bh.default_params(d, k, L) for d, k, L in probs]) as batch:
+        t0 = time.perf_counter()
+        st = batch.check_barrier_timeout(50.0)
+        dt = time.perf_counter() - t0
+        assert st == bh.BH_ETIMEOUT, st
+        assert dt < 10.0, dt
+        B = [cuda(b) for b in bs]
+        for persistent in (False, True):
+            batch.set_persistent(persistent)
+            X = [torch.empty_like(v) for v in B]
+            batch.vcycle(B, X)
+            for H, b, x in zip(Hs, bs, X):
+                assert relerr(host(x), H.vcycle(H.L, np.zeros_like(b), b)) <= 1e-10
