@@ -1305,9 +1305,17 @@ bh_status build_phases(bh_batch* b, const TopOps& top) {
   b->d_phases = dph.d;
   b->nphases = (int)ph.size();
   b->psmem = std::max<size_t>(B.smem, 64);
-  // co-resident grid of the cooperative launch
+  // co-resident grid of the cooperative launch; the kernel's shared-memory
+  // limit is only ever raised (other live batches may launch it with more)
   auto kernel = vcycle_persistent_kernel<T>;
-  BCK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->psmem));
+  {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa{};
+    BCK(cudaFuncGetAttributes(&fa, kernel));
+    if ((int)b->psmem > fa.maxDynamicSharedSizeBytes)
+      BCK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->psmem));
+  }
   int per_sm = 0, dev = 0, sms = 0, clock_khz = 0, coop = 0;
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, b->psmem));
   BCK(cudaGetDevice(&dev));
