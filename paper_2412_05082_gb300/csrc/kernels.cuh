@@ -261,6 +261,13 @@ __device__ __forceinline__ void async_copy_or_zero(T* dst, const T* src, bool va
                : "memory");
 }
 
+// Asynchronous global -> shared copy of 16 bytes through L2 (cp.async.cg); both
+// addresses must be 16-byte aligned.
+__device__ __forceinline__ void async_copy_chunk16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void async_copy_wait() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }

@@ -54,13 +54,23 @@ struct Mvs2Cfg {
   // with the window, so that no stage after the window copy waits on a global
   // load (the FP32 kernel is bound by load latency, the FP64 one by its pipe)
   static constexpr bool PREFETCH = sizeof(T) == 4;
-  // values per patch: window, T_M, T_L, T_B (and the prefetched b and x); the
-  // two m x m buffers of the residual and the FDM reuse the window's space once
-  // the x-split has read it
-  static constexpr int PER = W * W + W * M + 2 * WM * M + (PREFETCH ? 2 * M * M : 0);
+  // FP32, k <= 4: window rows of tiles away from the boundary are copied as
+  // 16-byte chunks; each shared-memory row starts on a 16-byte boundary and
+  // holds its row at the row's own offset 0..3 (the global row start modulo 4
+  // values).  For k >= 5 the padded rows would cost a resident block per SM.
+  static constexpr bool VECWIN = sizeof(T) == 4 && K <= 4;
+  static constexpr int CH = (W + 3 + 3) / 4;      // 16-byte chunks per window row
+  static constexpr int WS = VECWIN ? 4 * CH : W;  // shared-memory row stride of the window
+  static constexpr int WIN = W * WS;
+  // values per patch: window, T_M, T_L, T_B (and the prefetched b and x, or
+  // in the interior form b and the residual); the m x m buffers of the
+  // residual and the FDM reuse space whose contents are no longer needed
+  static constexpr int PER = WIN + W * M + 2 * WM * M + (PREFETCH ? 2 * M * M : 0);
   static_assert(2 * M * M <= W * W, "FDM buffers must fit in the window region");
-  // M, L, B class tables, the four S, and the interior type's 1 / (l_x + l_y)
-  static constexpr int TABLES = 3 * NC * BW + 5 * M * M;
+  static_assert(M * M <= W * M, "the FDM buffer must fit in the T_M region");
+  // M, L, B class tables, the four S, and the interior type's 1 / (l_x + l_y),
+  // padded so that the window starts on a 16-byte boundary
+  static constexpr int TABLES = (3 * NC * BW + 5 * M * M + 3) / 4 * 4;
   static constexpr int BUDGET = 110 * 1024;  // bytes of shared memory per block (2 per SM)
   static constexpr int FIT = (BUDGET / (int)sizeof(T) - TABLES) / PER;
   static constexpr int PB_MAX = FIT < 1 ? 1 : (FIT > 32 ? 32 : FIT);
@@ -150,7 +160,8 @@ __device__ __forceinline__ void ycombine_half(const T* sM, const T* sL, const T*
 // patches into sBv, sXv ([patch][row][column]).  Patch nodes always lie in the
 // interior 1..n.  Values of x on a patch's own nodes are changed by no other
 // patch of its color, so the copy stays current until the patch's update.
-template <typename T, int K>
+// WITH_X false: b only.
+template <typename T, int K, bool WITH_X = true>
 __device__ __forceinline__ void prefetch_patch_nodes(const MvsArgs<T>& a, int np,
                                                      const int (*sV)[2], T* sBv, T* sXv) {
   constexpr int M = 2 * K - 1, MM = M * M;
@@ -159,7 +170,7 @@ __device__ __forceinline__ void prefetch_patch_nodes(const MvsArgs<T>& a, int np
     const int p = e / MM, i = (e / M) % M, j = e % M;
     const int64_t gi = (int64_t)(K * (sV[p][1] - 1) + i) * n + (K * (sV[p][0] - 1) + j);
     async_copy_or_zero(sBv + e, a.b + gi, true);
-    async_copy_or_zero(sXv + e, a.x + gi, true);
+    if constexpr (WITH_X) async_copy_or_zero(sXv + e, a.x + gi, true);
   }
 }
 
@@ -177,8 +188,8 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
   T* sB = sL + NC * BW;
   T* sS = sB + NC * BW;  // [4][M][M]
   const int pb = a.pb;
-  T* sX = reinterpret_cast<T*>(smem_raw) + C::TABLES;  // [pb][W][W]
-  T* sTM = sX + pb * W * W;    // [pb][W][M]
+  T* sX = reinterpret_cast<T*>(smem_raw) + C::TABLES;  // [pb][W][W] (in a [pb][W][WS] region)
+  T* sTM = sX + pb * C::WIN;   // [pb][W][M]
   T* sTL = sTM + pb * W * M;   // [pb][WM][M]
   T* sTB = sTL + pb * WM * M;  // [pb][WM][M]
   T* sR = sX;                  // [pb][M][M], over the window after the x-split
@@ -495,16 +506,25 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
                                                    int first, int np, unsigned char* smem_raw) {
   using C = Mvs2Cfg<T, K>;
   constexpr int M = C::M, W = C::W, WM = C::WM, MM = M * M;
+  constexpr int WS = C::WS;
   const int pb = a.pb;
-  T* sX = reinterpret_cast<T*>(smem_raw) + C::TABLES;  // same layout as mvs2_tile
-  T* sTM = sX + pb * W * W;
+  T* sX = reinterpret_cast<T*>(smem_raw) + C::TABLES;  // [pb][W][WS]
+  T* sTM = sX + pb * C::WIN;
   T* sTL = sTM + pb * W * M;
   T* sTB = sTL + pb * WM * M;
-  T* sR = sX;  // over the window after the x-split
-  T* sF = sR + pb * MM;
-  T* sBv = sTB + pb * WM * M;  // b and x on the patch nodes (PREFETCH)
-  T* sXv = sBv + pb * MM;
+  T* sBv = sTB + pb * WM * M;  // b on the patch nodes (PREFETCH)
+  // FP64: R and F over the window once the x-split has read it.  FP32: the
+  // window stays intact to the update, which reads x on the patch nodes from
+  // it; R takes the space after b, F that of T_M once the y-combination has
+  // read it
+  T* sR = C::PREFETCH ? sBv + pb * MM : sX;
+  T* sF = C::PREFETCH ? sTM : sR + pb * MM;
   __shared__ int sVi[32][2];
+  // index in x of window node (0, 0) (negative for patches at v_a = 2), the
+  // row offset of window row 0 in shared memory, and whether the window lies in
+  // the interior 1..n (then its rows are copied as 16-byte chunks)
+  __shared__ long long sW0[32];
+  __shared__ int sOff0[32], sDeep[32];
   const int N = a.N, n = a.n;
   // operator and eigenvector tables staged in shared memory (layout of OpTab
   // and FdmTab), read at compile-time offsets, and the interior type's
@@ -520,26 +540,68 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   const OpTab<T, K>& op_s = *reinterpret_cast<const OpTab<T, K>*>(smem_raw);
   const FdmTab<T, K>& fdm_s =
       *reinterpret_cast<const FdmTab<T, K>*>(smem_raw + sizeof(T) * 3 * C::NC * C::BW);
+  // offset in values of a.x from a 16-byte boundary
+  const int xo = C::VECWIN ? (int)((reinterpret_cast<uintptr_t>(a.x) / sizeof(T)) & 3) : 0;
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
     const int vid = a.verts[first + p];
-    sVi[p][0] = vid % (N - 1) + 1;
-    sVi[p][1] = vid / (N - 1) + 1;
+    const int v0 = vid % (N - 1) + 1, v1 = vid / (N - 1) + 1;
+    sVi[p][0] = v0;
+    sVi[p][1] = v1;
+    const long long w0 = (long long)(K * (v1 - 2) - 1) * n + (K * (v0 - 2) - 1);
+    sW0[p] = w0;
+    sOff0[p] = (int)((xo + w0) & 3);
+    sDeep[p] = (v0 >= 3 && v0 <= N - 3 && v1 >= 3 && v1 <= N - 3) ? 1 : 0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < np * W * W; e += blockDim.x) {
-    const int p = e / (W * W), wy = (e / W) % W, wx = e % W;
-    const int gx = K * (sVi[p][0] - 2) + wx, gy = K * (sVi[p][1] - 2) + wy;
-    const bool in = gx >= 1 && gx <= n && gy >= 1 && gy <= n;
-    // outside the interior the (unread) source is the first value of x
-    async_copy_or_zero(sX + e, a.x + (in ? (int64_t)(gy - 1) * n + (gx - 1) : 0), in);
+  // window column 0 of window row wy of patch p in shared memory
+  auto win_row = [&](int p, int wy) -> const T* {
+    if constexpr (C::VECWIN)
+      return sX + (p * W + wy) * WS + ((sOff0[p] + wy * n) & 3);
+    else
+      return sX + (p * W + wy) * W;
+  };
+  if constexpr (C::VECWIN) {
+    // item (patch, row, chunk); a chunk holds shared positions 4c .. 4c + 3 of
+    // the row, i.e. window columns 4c - off .. 4c + 3 - off
+    constexpr int CH = C::CH;
+    for (int e = threadIdx.x; e < np * W * CH; e += blockDim.x) {
+      const int row = e / CH, c = e - row * CH;  // row = p W + wy
+      const int p = row / W, wy = row - p * W;
+      const long long s = sW0[p] + (long long)wy * n;  // index in x of window node (wy, 0)
+      const int off = (sOff0[p] + wy * n) & 3;
+      T* dst = sX + row * WS + 4 * c;
+      if (sDeep[p]) {
+        // a.x + s - off is 16-byte aligned; the chunk lies in 0 .. n^2 - 1
+        // because the window lies at least k - 1 nodes inside the interior
+        async_copy_chunk16(dst, a.x + (s - off + 4 * c));
+      } else {
+        const int gy = K * (sVi[p][1] - 2) + wy, gx0 = K * (sVi[p][0] - 2);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int wx = 4 * c + u - off;
+          if (wx < 0 || wx >= W) continue;
+          const int gx = gx0 + wx;
+          const bool in = gx >= 1 && gx <= n && gy >= 1 && gy <= n;
+          async_copy_or_zero(dst + u, a.x + (in ? s + wx : 0), in);
+        }
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < np * W * W; e += blockDim.x) {
+      const int p = e / (W * W), wy = (e / W) % W, wx = e % W;
+      const int gx = K * (sVi[p][0] - 2) + wx, gy = K * (sVi[p][1] - 2) + wy;
+      const bool in = gx >= 1 && gx <= n && gy >= 1 && gy <= n;
+      // outside the interior the (unread) source is the first value of x
+      async_copy_or_zero(sX + e, a.x + (in ? (int64_t)(gy - 1) * n + (gx - 1) : 0), in);
+    }
   }
-  if constexpr (C::PREFETCH) prefetch_patch_nodes<T, K>(a, np, sVi, sBv, sXv);
+  if constexpr (C::PREFETCH) prefetch_patch_nodes<T, K, false>(a, np, sVi, sBv, nullptr);
   async_copy_wait();
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * np * W; e += blockDim.x) {
     const int q_ = e / (W), wy = e - q_ * (W);  // item (half, patch, wy)
     const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
-    const T* xr = sX + (p * W + wy) * W + K;
+    const T* xr = win_row(p, wy) + K;
     T* tm = sTM + (p * W + wy) * M;
     if (half == 0)
       xsplit_m_canon<T, K, 0>(op_s, xr, tm);
@@ -549,7 +611,7 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   for (int e = threadIdx.x; e < 2 * np * WM; e += blockDim.x) {
     const int q_ = e / (WM), r = e - q_ * (WM);  // item (half, patch, r)
     const int half = q_ >= np ? 1 : 0, p = q_ - half * np;
-    const T* xr = sX + (p * W + K + r) * W + K;
+    const T* xr = win_row(p, K + r) + K;
     T* tl = sTL + (p * WM + r) * M;
     T* tb = sTB + (p * WM + r) * M;
     if (half == 0)
@@ -624,7 +686,7 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
     const T* src = sF + p * MM + i * M;
     const int gy = K * (sVi[p][1] - 1) + i + 1, gx0 = K * (sVi[p][0] - 1) + 1;
     T* xrow = a.x + (int64_t)(gy - 1) * n + (gx0 - 1);
-    const T* xv = sXv + p * MM + i * M;  // x on the row's patch nodes (PREFETCH)
+    const T* xv = win_row(p, K + 1 + i) + K + 1;  // x on the row's patch nodes (PREFETCH)
     auto put = [&](int j, T v) {
       if constexpr (C::PREFETCH)
         xrow[j] = xv[j] + ps * v;
