@@ -16,8 +16,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbiharm.so")
-SOURCES = ["inst_f64.cu", "inst_f32.cu", "vec.cu", "api.cu", "setup.cpp", "noalloc.cu", "batch.cu",
-           "serve.cpp", "probe.cu", "gemm.cu"]
+# the longest translation units first
+SOURCES = ["batch_pers_f64.cu", "batch_pers_f32.cu", "inst_f64.cu", "inst_f32.cu",
+           "batch_mvs_f64.cu", "batch_mvs_f32.cu", "batch.cu", "vec.cu", "api.cu", "setup.cpp",
+           "noalloc.cu", "serve.cpp", "probe.cu", "gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

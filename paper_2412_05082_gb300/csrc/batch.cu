@@ -58,172 +58,13 @@ bh_status berr(bh_status s, const std::string& msg) {
     if (s_ != BH_OK) return s_; \
   } while (0)
 
-// ---------------------------------------------------------------------------
-// device side
-// ---------------------------------------------------------------------------
-struct Meta {                 // per problem, indexed by problem id
-  const int* k;               // degree
-  const void* const* tabs;    // Tables<T, K>* (device) of the launch's value type
-  const int* active;          // 0: problem finished, skip it
-};
+}  // namespace
 
-// first index p with prefix[p + 1] > tid (prefix[0] = 0, increasing)
-__device__ __forceinline__ int find_seg(const int64_t* prefix, int n, int64_t tid) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= tid)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
+#include "batch_dev.cuh"
 
-#define BH_KSWITCH(k, CALL) \
-  switch (k) {              \
-    case 2: CALL(2); break; \
-    case 3: CALL(3); break; \
-    case 4: CALL(4); break; \
-    case 5: CALL(5); break; \
-    case 6: CALL(6); break; \
-    case 7: CALL(7); break; \
-  }
+using namespace bh::bdev;
 
-template <typename T, int KIND>
-__global__ void __launch_bounds__(128) sweep_batch_kernel(Meta m, const SweepArgs<T>* args,
-                                                          const int64_t* prefix, const int* pid,
-                                                          int n) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= prefix[n]) return;
-  const int s = find_seg(prefix, n, tid);
-  const int p = pid[s];
-  if (!m.active[p]) return;
-  const int64_t local = tid - prefix[s];
-#define BH_CALL(KK) \
-  sweep_thread<T, KK, KIND>(static_cast<const Tables<T, KK>*>(m.tabs[p])->op, args[s], local)
-  BH_KSWITCH(m.k[p], BH_CALL)
-#undef BH_CALL
-}
-
-template <typename T, bool PROLONG>
-__global__ void __launch_bounds__(128) xfer_batch_kernel(Meta m, const XferArgs<T>* args,
-                                                         const int64_t* prefix, const int* pid,
-                                                         int n) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= prefix[n]) return;
-  const int s = find_seg(prefix, n, tid);
-  const int p = pid[s];
-  if (!m.active[p]) return;
-  const int64_t local = tid - prefix[s];
-#define BH_CALL(KK)                                                                          \
-  if (PROLONG)                                                                               \
-    prolong_thread<T, KK>(static_cast<const Tables<T, KK>*>(m.tabs[p])->xfer, args[s], local); \
-  else                                                                                       \
-    restrict_thread<T, KK>(static_cast<const Tables<T, KK>*>(m.tabs[p])->xfer, args[s], local)
-  BH_KSWITCH(m.k[p], BH_CALL)
-#undef BH_CALL
-}
-
-struct Tile {
-  int s;      // index into the op's problem list
-  int first;  // first patch of the color list
-  int count;
-};
-
-// Degrees whose interior tiles take the folded path inside the batched
-// kernel.  Its register count is the maximum over the degrees it dispatches:
-// with the folded path up to k = 4 it stays at 64 per thread and the 2D sweep's
-// batched solve ran 1 % faster than without it; up to k = 5 or 7 it needs
-// 80-128 registers and ran 3-17 % slower (measured on GB300, FP64).
-constexpr int kBatchInteriorMaxK = 4;
-
-template <typename T>
-__global__ void __launch_bounds__(256) mvs2_batch_kernel(Meta m, const MvsArgs<T>* args,
-                                                         const int* pid, const Tile* tiles,
-                                                         int ntiles) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {  // any grid size (one block per tile)
-    __syncthreads();  // the previous tile's last stage still reads shared memory
-    const Tile tl = tiles[t];
-    const int p = pid[tl.s];
-    if (!m.active[p]) continue;
-#define BH_CALL(KK)                                                                     \
-  {                                                                                     \
-    const auto* tb = static_cast<const Tables<T, KK>*>(m.tabs[p]);                      \
-    if (KK <= kBatchInteriorMaxK && mvs2_tile_is_interior(args[tl.s], tl.first, tl.count)) \
-      mvs2_tile_interior<T, KK>(tb->op, tb->fdm, args[tl.s], tl.first, tl.count, smem_raw); \
-    else                                                                                \
-      mvs2_tile<T, KK>(tb->op, tb->fdm, args[tl.s], tl.first, tl.count, smem_raw);       \
-  }
-    BH_KSWITCH(m.k[p], BH_CALL)
-#undef BH_CALL
-  }
-}
-
-template <typename T>
-struct Symv {  // coarse solve x = scale A b, A dense symmetric FP64 (n x n)
-  const double* A;
-  const T* b;
-  T* x;
-  int n;
-  double scale;
-};
-
-template <typename T>
-__global__ void coarse_batch_kernel(Meta m, const Symv<T>* ops, const int* pid, int count) {
-  const int s = blockIdx.y;
-  if (s >= count || !m.active[pid[s]]) return;
-  const Symv<T> o = ops[s];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= o.n) return;
-  double acc = 0.0;
-  for (int j = 0; j < o.n; ++j) acc = fma(o.A[(int64_t)j * o.n + i], (double)o.b[j], acc);
-  o.x[i] = (T)(o.scale * acc);
-}
-
-template <typename T>
-struct Vec {  // one problem's vector operands: y + yslot * ys, x + xslot * xs, n values
-  T* y;
-  const T* x;
-  int64_t n;
-  int64_t ys, xs;
-};
-
-// zero, copy, y += c x, y = x / sqrt(c): one launch over the concatenation
-enum VecOp { kZero = 0, kCopy = 1, kAxpyDev = 2, kScaleInvSqrt = 3 };
-
-template <typename T>
-__global__ void vec_batch_kernel(Meta m, const Vec<T>* v, const int64_t* prefix, const int* pid,
-                                 int n, int op, const double* coef, int cstride, int cslot,
-                                 double sign, int yslot, int xslot) {
-  const int64_t total = prefix[n];
-  for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    const int s = find_seg(prefix, n, tid);
-    const int p = pid[s];
-    if (!m.active[p]) continue;
-    const int64_t i = tid - prefix[s];
-    const Vec<T> o = v[s];
-    T* y = o.y + yslot * o.ys;
-    const T* x = o.x + xslot * o.xs;
-    switch (op) {
-      case kZero: y[i] = T(0); break;
-      case kCopy: y[i] = x[i]; break;
-      case kAxpyDev: y[i] = T(fma(sign * coef[p * cstride + cslot], (double)x[i], (double)y[i])); break;
-      default: y[i] = T((double)x[i] / sqrt(coef[p * cstride + cslot])); break;
-    }
-  }
-}
-
-// conversion between an FP64 vector (d + slot * ds) and an FP32 one
-struct Conv {
-  double* d;
-  float* f;
-  int64_t n;
-  int64_t ds;
-};
-enum ConvDir { kD2F = 0, kF2D = 1 };
+namespace {
 
 __global__ void conv_batch_kernel(Meta m, const Conv* v, const int64_t* prefix, const int* pid,
                                   int n, int dir, int slot) {
@@ -281,186 +122,9 @@ __global__ void dot_batch_final(const int64_t* cprefix, const int* pid, int n,
   out[pid[s] * cstride + cslot] = t;
 }
 
-// ---------------------------------------------------------------------------
-// persistent form: the whole V-cycle in one cooperative launch
-// ---------------------------------------------------------------------------
-// The V-cycle's level operations become phases of one kernel: every block
-// walks the phase list; inside a phase the blocks share its work list (tiles
-// of the patch kernel, threads of the sweeps, transfers, vector operations and
-// the coarse solve); a grid barrier separates the phases.
-enum PhaseKind : int {
-  kPhMvs = 0,      // colored-MVS tiles (value type of the V-cycle)
-  kPhSweep0 = 1,   // FP64 x-split sweep
-  kPhSweep2 = 2,   // FP64 y-combination (residual)
-  kPhRestr = 3,    // FP64 restriction pass
-  kPhProl = 4,     // prolongation pass (value type of the V-cycle)
-  kPhZero = 5,     // zero vectors (value type of the V-cycle)
-  kPhCoarse = 6,   // coarse solve (value type of the V-cycle)
-  kPhConv = 7      // FP64 <-> FP32 conversions
-};
+}  // namespace
 
-struct MvsGroup {  // the tiles of one degree in an MVS phase
-  const void* args;  // MvsArgs<T>[]
-  const int* pid;
-  const Tile* tiles;
-  int ntiles;
-};
-
-struct Phase {
-  int kind;
-  int n;              // entries of the work list
-  int64_t total;      // items: threads, or tiles (MVS), or (problem, row) pairs (coarse)
-  const void* args;   // SweepArgs / XferArgs / Vec / Conv / Symv entries
-  const int64_t* prefix;
-  const int* pid;
-  int dir;            // conversion direction
-  int maxn;           // coarse: largest coarse size
-  int ngroups;        // MVS: degree groups
-  MvsGroup groups[kMaxK + 1];
-};
-
-// Grid barrier with a bounded wait: thread 0 of every block arrives on a
-// counter; the last one to arrive resets it and advances the generation, the
-// others spin on the generation for at most `budget` clock cycles.  A wait
-// that runs out sets *status (1) and every block leaves the kernel at its next
-// barrier, so a barrier that can never complete (fewer co-resident blocks than
-// `expected`) ends the kernel with an error status instead of a hang.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned expected,
-                                             int* status, long long budget) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned* vgen = gen;
-    volatile int* vstatus = status;
-    const unsigned g = *vgen;
-    __threadfence();  // this block's writes of the phase before its arrival
-    if (atomicAdd(count, 1u) == expected - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == g) {
-        if (*vstatus != 0 || clock64() - t0 > budget) {
-          atomicExch(status, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(100);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256, 2) vcycle_persistent_kernel(
-    Meta m64, Meta mT, const Phase* __restrict__ phases, int nphases, unsigned* bar,
-    unsigned expected, int* status, long long budget) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int f = 0; f < nphases; ++f) {
-    const Phase& P = phases[f];
-    const int kind = P.kind;
-    if (kind == kPhSweep0 || kind == kPhSweep2) {
-      const SweepArgs<double>* args = static_cast<const SweepArgs<double>*>(P.args);
-      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
-        const int s = find_seg(P.prefix, P.n, tid);
-        const int p = P.pid[s];
-        if (!m64.active[p]) continue;
-        const int64_t local = tid - P.prefix[s];
-#define BH_CALL(KK)                                                                              \
-  if (kind == kPhSweep0)                                                                         \
-    sweep_thread<double, KK, 0, true>(static_cast<const Tables<double, KK>*>(m64.tabs[p])->op,    \
-                                      args[s], local);                                           \
-  else                                                                                           \
-    sweep_thread<double, KK, 2, true>(static_cast<const Tables<double, KK>*>(m64.tabs[p])->op,    \
-                                      args[s], local)
-        BH_KSWITCH(m64.k[p], BH_CALL)
-#undef BH_CALL
-      }
-    } else if (kind == kPhRestr) {
-      const XferArgs<double>* args = static_cast<const XferArgs<double>*>(P.args);
-      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
-        const int s = find_seg(P.prefix, P.n, tid);
-        const int p = P.pid[s];
-        if (!m64.active[p]) continue;
-        const int64_t local = tid - P.prefix[s];
-#define BH_CALL(KK) \
-  restrict_thread<double, KK>(static_cast<const Tables<double, KK>*>(m64.tabs[p])->xfer, args[s], local)
-        BH_KSWITCH(m64.k[p], BH_CALL)
-#undef BH_CALL
-      }
-    } else if (kind == kPhProl) {
-      const XferArgs<T>* args = static_cast<const XferArgs<T>*>(P.args);
-      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
-        const int s = find_seg(P.prefix, P.n, tid);
-        const int p = P.pid[s];
-        if (!mT.active[p]) continue;
-        const int64_t local = tid - P.prefix[s];
-#define BH_CALL(KK) \
-  prolong_thread<T, KK>(static_cast<const Tables<T, KK>*>(mT.tabs[p])->xfer, args[s], local)
-        BH_KSWITCH(mT.k[p], BH_CALL)
-#undef BH_CALL
-      }
-    } else if (kind == kPhZero) {
-      const Vec<T>* v = static_cast<const Vec<T>*>(P.args);
-      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
-        const int s = find_seg(P.prefix, P.n, tid);
-        if (!mT.active[P.pid[s]]) continue;
-        v[s].y[tid - P.prefix[s]] = T(0);
-      }
-    } else if (kind == kPhConv) {
-      const Conv* v = static_cast<const Conv*>(P.args);
-      for (int64_t tid = gtid; tid < P.total; tid += gthreads) {
-        const int s = find_seg(P.prefix, P.n, tid);
-        if (!m64.active[P.pid[s]]) continue;
-        const int64_t i = tid - P.prefix[s];
-        if (P.dir == kD2F)
-          v[s].f[i] = (float)v[s].d[i];
-        else
-          v[s].d[i] = (double)v[s].f[i];
-      }
-    } else if (kind == kPhCoarse) {
-      const Symv<T>* ops = static_cast<const Symv<T>*>(P.args);
-      for (int64_t it = gtid; it < P.total; it += gthreads) {
-        const int s = (int)(it / P.maxn), i = (int)(it - (int64_t)s * P.maxn);
-        const Symv<T> o = ops[s];
-        if (i >= o.n || !mT.active[P.pid[s]]) continue;
-        double acc = 0.0;
-        for (int j = 0; j < o.n; ++j) acc = fma(o.A[(int64_t)j * o.n + i], (double)o.b[j], acc);
-        o.x[i] = (T)(o.scale * acc);
-      }
-    } else {  // kPhMvs: one tile per block at a time, the degree groups one after another
-      for (int64_t t = blockIdx.x; t < P.total; t += gridDim.x) {
-        int g = 0;
-        int64_t tl = t;
-        while (g + 1 < P.ngroups && tl >= P.groups[g].ntiles) tl -= P.groups[g++].ntiles;
-        const MvsGroup G = P.groups[g];
-        const Tile tile = G.tiles[tl];
-        const MvsArgs<T>* args = static_cast<const MvsArgs<T>*>(G.args);
-        const int p = G.pid[tile.s];
-        __syncthreads();  // the previous tile's last stage still reads shared memory
-        if (!mT.active[p]) continue;
-#define BH_CALL(KK)                                                                           \
-  {                                                                                           \
-    const auto* tb = static_cast<const Tables<T, KK>*>(mT.tabs[p]);                           \
-    if (KK <= kBatchInteriorMaxK && mvs2_tile_is_interior(args[tile.s], tile.first, tile.count)) \
-      mvs2_tile_interior<T, KK>(tb->op, tb->fdm, args[tile.s], tile.first, tile.count, smem_raw); \
-    else                                                                                      \
-      mvs2_tile<T, KK>(tb->op, tb->fdm, args[tile.s], tile.first, tile.count, smem_raw);       \
-  }
-        BH_KSWITCH(mT.k[p], BH_CALL)
-#undef BH_CALL
-      }
-    }
-    if (f + 1 < nphases && !grid_barrier(bar, bar + 1, expected, status, budget)) return;
-  }
-}
+namespace {
 
 // ---------------------------------------------------------------------------
 // host side
@@ -493,6 +157,7 @@ struct MvsOp {
   DevArray<int> pid;
   DevArray<Tile> tiles;
   size_t smem = 0;
+  int k = 0;  // the degree of every problem of the op
 };
 
 template <typename T>
@@ -874,6 +539,7 @@ bh_status build_vdepth(bh_batch* b, int t, VDepth<T>& V, Depth& D) {
         BCKS(upload(b, mpid[g], op.pid));
         BCKS(upload(b, mtiles[g], op.tiles));
         op.smem = smem_k[k];
+        op.k = k;
       }
     }
   }
@@ -1024,8 +690,15 @@ cudaError_t run_mvs(bh_batch* b, const std::vector<MvsOp<T>>& ops) {
     const MvsOp<T>& op = ops[i];
     cudaStream_t st = fork ? b->side[i] : b->st;
     if (fork && (e = cudaStreamWaitEvent(st, b->fork, 0)) != cudaSuccess) return e;
-    mvs2_batch_kernel<T><<<op.tiles.n, 256, op.smem, st>>>(meta<T>(b), op.args.d, op.pid.d,
-                                                           op.tiles.d, op.tiles.n);
+    Meta m = meta<T>(b);
+    const MvsArgs<T>* args = op.args.d;
+    const int* pid = op.pid.d;
+    const Tile* tiles = op.tiles.d;
+    int ntiles = op.tiles.n;
+    void* params[] = {&m, &args, &pid, &tiles, &ntiles};
+    if ((e = cudaLaunchKernel(mvs2_batch_kernel_for<T>(op.k), dim3((unsigned)ntiles), dim3(256),
+                              params, op.smem, st)) != cudaSuccess)
+      return e;
     count_launch(b);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (fork && (e = cudaEventRecord(b->join[i], st)) != cudaSuccess) return e;
@@ -1195,14 +868,14 @@ bh_status check_status(const bh_batch* b) {
 // only ever raise a kernel's shared-memory limit: graphs of other live batches
 // may launch it with more shared memory than this batch needs
 template <typename T>
-bh_status raise_smem_limit(size_t smem) {
+bh_status raise_smem_limit(int k, size_t smem) {
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
+  const void* kernel = mvs2_batch_kernel_for<T>(k);
   cudaFuncAttributes fa{};
-  BCK(cudaFuncGetAttributes(&fa, mvs2_batch_kernel<T>));
+  BCK(cudaFuncGetAttributes(&fa, kernel));
   if ((int)smem > fa.maxDynamicSharedSizeBytes)
-    BCK(cudaFuncSetAttribute(mvs2_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem));
+    BCK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return BH_OK;
 }
 
@@ -1307,7 +980,7 @@ bh_status build_phases(bh_batch* b, const TopOps& top) {
   b->psmem = std::max<size_t>(B.smem, 64);
   // co-resident grid of the cooperative launch; the kernel's shared-memory
   // limit is only ever raised (other live batches may launch it with more)
-  auto kernel = vcycle_persistent_kernel<T>;
+  const void* kernel = vcycle_persistent_kernel_for<T>();
   {
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
@@ -1342,8 +1015,8 @@ bh_status launch_persistent(bh_batch* b, unsigned extra, long long budget) {
   unsigned expected = (unsigned)b->pgrid + extra;
   int* status = reinterpret_cast<int*>(b->d_bar + 2);
   void* args[] = {&m64, &mT, &phases, &nph, &bar, &expected, &status, &budget};
-  const void* kernel = b->mixed ? (const void*)vcycle_persistent_kernel<float>
-                                : (const void*)vcycle_persistent_kernel<double>;
+  const void* kernel = b->mixed ? vcycle_persistent_kernel_for<float>()
+                                : vcycle_persistent_kernel_for<double>();
   BCK(cudaLaunchCooperativeKernel(kernel, dim3(b->pgrid), dim3(256), args, b->psmem, b->st));
   count_launch(b);
   BCK(cudaMemcpyAsync(b->h_status, status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
@@ -1351,15 +1024,15 @@ bh_status launch_persistent(bh_batch* b, unsigned extra, long long budget) {
 }
 
 bh_status prepare(bh_batch* b) {
-  // mvs kernel: allow the largest dynamic shared memory any tile shape needs
-  size_t smem = 0;
-  for (int p = 0; p < b->P; ++p)
-    smem = std::max(smem, mvs_smem_for(b, b->k[p],
-                                       std::min(mvs_pb(b, b->k[p]), mvs_pb_max(b, b->k[p]))));
-  if (b->mixed)
-    BCKS(raise_smem_limit<float>(smem));
-  else
-    BCKS(raise_smem_limit<double>(smem));
+  // mvs kernels: allow the dynamic shared memory of each degree's tile shape
+  for (int p = 0; p < b->P; ++p) {
+    const int k = b->k[p];
+    const size_t smem = mvs_smem_for(b, k, std::min(mvs_pb(b, k), mvs_pb_max(b, k)));
+    if (b->mixed)
+      BCKS(raise_smem_limit<float>(k, smem));
+    else
+      BCKS(raise_smem_limit<double>(k, smem));
+  }
   // one side stream and join event per degree present (created once)
   int groups = 0;
   for (int k = 0; k <= kMaxK; ++k)

@@ -346,10 +346,19 @@ def test_persistent_vcycle_equals_the_graph_and_the_oracle(bh, precision):
         batch.vcycle(B, Xp)
         its_p, rr_p = batch.solve(B, [torch.empty_like(v) for v in B], 1e-8, 100)
         for (d, k, L), H, b, xg, xp in zip(MIX, Hs, bs, Xg, Xp):
-            assert relerr(host(xp), host(xg)) <= (1e-13 if precision == "fp64" else 1e-6), (k, L)
+            # up to k = 4 both forms run the same tile code; above it the graph
+            # form's interior tiles take the folded fast diagonalization and the
+            # persistent kernel the unfolded one, equal up to the rounding of
+            # either (FP64), or of the FP32 V-cycle (checked against the oracle)
+            ref = H.vcycle(H.L, np.zeros_like(b), b)
             if precision == "fp64":
-                ref = H.vcycle(H.L, np.zeros_like(b), b)
+                assert relerr(host(xp), host(xg)) <= (1e-13 if k <= 4 else 1e-11), (k, L)
                 assert relerr(host(xp), ref) <= 1e-10, (k, L)
+            else:
+                if k <= 4:
+                    assert relerr(host(xp), host(xg)) <= 1e-6, (k, L)
+                assert relerr(host(xp), ref) <= 1e-3, (k, L)
+                assert relerr(host(xg), ref) <= 1e-3, (k, L)
         assert its_p == its_g
         assert all(r <= 1.0001e-8 for r in rr_p)
 
