@@ -58,8 +58,16 @@ enum { BH_FDM = 0, BH_EXACT = 1 };
  * in FP64 arithmetic (from the FP32 iterate) and restricts it in FP64: the
  * FP32 rounding error of A x is amplified by the coarse-grid correction like
  * the condition number of A_l, which stalls the plain FP32 V-cycle on fine
- * meshes at high degree (2D k >= 5 on 256^2 cells).  Not in the paper. */
-enum { BH_FP64 = 0, BH_MIXED_FP32 = 1, BH_MIXED_FP32_R64 = 2 };
+ * meshes at high degree (2D k >= 5 on 256^2 cells).  BH_MIXED_FP32_RC is
+ * BH_MIXED_FP32_R64 with that defect evaluated in compensated FP32
+ * arithmetic instead of FP64: every value of the sum factorization is a pair
+ * hi + lo of floats, every 1D coefficient c is stored as fl32(c) plus
+ * fl32(c - fl32(c)), products with the FP32 iterate are made exact by FMA and
+ * sums by TwoSum, so the defect is accurate to about (terms) 2^-48 of
+ * sum |terms| (FP64: 2^-53, FP32: 2^-24); the FP64 pipe, which issues 1/64 of
+ * the FP32 rate on this GPU, is used only for the final b - (hi + lo).  The
+ * restriction stays FP64.  Neither form is in the paper. */
+enum { BH_FP64 = 0, BH_MIXED_FP32 = 1, BH_MIXED_FP32_R64 = 2, BH_MIXED_FP32_RC = 3 };
 /* GMRES preconditioning side (Sec. 5.1 leaves it open).  BH_RIGHT (the
  * default) keeps the preconditioned directions (flexible form) and stops on the
  * true residual b - A x; its FP64 rounding floor eps ||A|| ||x|| / ||b|| is
@@ -89,8 +97,8 @@ typedef struct {
   int post_steps;
   double omega;      /* damping; <= 0: Sec. 5.1 defaults (AVS 1/4 in 2D, 0.1 in 3D
                         (1/8 exact); MVS 1 in 2D, 0.7 in 3D) */
-  int precision;     /* BH_FP64 | BH_MIXED_FP32 | BH_MIXED_FP32_R64 (mixed forms need
-                        gmres_side = BH_RIGHT, or krylov = BH_CG) */
+  int precision;     /* BH_FP64 | BH_MIXED_FP32 | BH_MIXED_FP32_R64 | BH_MIXED_FP32_RC
+                        (mixed forms need gmres_side = BH_RIGHT, or krylov = BH_CG) */
   int gmres_restart; /* restart length m (default 50) */
   int gmres_side;    /* BH_RIGHT (default) | BH_LEFT */
   int coarse;        /* BH_COARSE_EXACT (default) | BH_COARSE_SMOOTH */
@@ -125,6 +133,16 @@ bh_status bh_apply_A(bh_ctx* ctx, int level, const double* x_dev, double* y_dev)
 /* r = b - A_l x (Algorithm 1, restriction step).  r_dev must not alias x_dev. */
 bh_status bh_residual(bh_ctx* ctx, int level, const double* x_dev, const double* b_dev,
                       double* r_dev);
+
+/* r = b - A_l x for an FP32 iterate x_dev (n(l) floats) and an FP64 b_dev, in
+ * the compensated FP32 arithmetic of BH_MIXED_FP32_RC (the defect that form
+ * restricts, Algorithm 1's restriction step): the result differs from the
+ * exact defect of (double) x by about (terms) 2^-48 of (|A_l| |x| + |b|).  The
+ * context must have a mixed precision (it uses the FP32 tables' hi + lo
+ * parts).  r_dev (n(l) doubles) must not alias x_dev; it may be b_dev.
+ * BH_EINVAL for an FP64 context.  Not in the paper. */
+bh_status bh_defect_compensated(bh_ctx* ctx, int level, const float* x_dev, const double* b_dev,
+                                double* r_dev);
 
 /* steps smoothing steps x <- S_l(x, b) of the context's smoother (AVS or
  * colored MVS, Sec. 3) with its local solver and damping, in place on x_dev. */
@@ -272,8 +290,9 @@ bh_status bh_setup_fdm(int degree, double gamma, int type, double* S, double* la
 typedef struct bh_batch bh_batch;
 
 /* count problems, params[i] each: dim 2, BH_MVS_COLORED, BH_FDM,
- * BH_COARSE_EXACT, BH_GMRES, precision BH_FP64 or BH_MIXED_FP32_R64 (the
- * latter with BH_RIGHT); precision, gmres_side, pre_steps and post_steps the
+ * BH_COARSE_EXACT, BH_GMRES, precision BH_FP64, BH_MIXED_FP32_R64 or
+ * BH_MIXED_FP32_RC (the mixed ones with BH_RIGHT; BH_MIXED_FP32_RC in the
+ * graph form only); precision, gmres_side, pre_steps and post_steps the
  * same for every problem (BH_EINVAL otherwise); the restart length is the
  * largest gmres_restart.  Allocates every hierarchy, builds the work lists and
  * captures the V-cycle graph.  Synchronous. */
@@ -295,7 +314,11 @@ bh_status bh_batch_vcycle_time(bh_batch* batch, int reps, double* ms);
  * operations and coarse solves of all problems at one depth -- separated by a
  * grid barrier.  Every barrier wait is bounded (2 s of clock cycles); a wait
  * that runs out ends the kernel with a status word that the next call reading
- * it turns into BH_ETIMEOUT.  Same arithmetic as the graph.  Host only. */
+ * it turns into BH_ETIMEOUT.  The graph's arithmetic up to degree 4; above it
+ * the persistent kernel solves interior patches by the unfolded fast
+ * diagonalization, the graph's per-degree kernels by the folded one (equal up
+ * to rounding).  Host only.  BH_EINVAL for a BH_MIXED_FP32_RC batch (its compensated defect sweeps are
+ * graph nodes only). */
 bh_status bh_batch_set_persistent(bh_batch* batch, int on);
 
 /* Check of the persistent form's failure path: one persistent V-cycle whose

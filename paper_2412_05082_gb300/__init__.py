@@ -18,7 +18,7 @@ BH_OK, BH_EINVAL, BH_ENOMEM, BH_ECUDA, BH_ENOCONV, BH_ETIMEOUT, BH_EBUSY = 0, -1
 BH_ECANCELED = -7
 AVS_ATOMIC, AVS_COLORED, MVS_COLORED = 0, 1, 2
 FDM, EXACT = 0, 1
-FP64, MIXED_FP32, MIXED_FP32_R64 = 0, 1, 2
+FP64, MIXED_FP32, MIXED_FP32_R64, MIXED_FP32_RC = 0, 1, 2, 3
 RIGHT, LEFT = 0, 1
 COARSE_EXACT, COARSE_SMOOTH = 0, 1
 GMRES, CG = 0, 1
@@ -54,6 +54,7 @@ SIGNATURES = {
     "bh_num_unknowns": (_I, [_P, _I, _c.POINTER(_I64)]),
     "bh_apply_A": (_I, [_P, _I, _P, _P]),
     "bh_residual": (_I, [_P, _I, _P, _P, _P]),
+    "bh_defect_compensated": (_I, [_P, _I, _P, _P, _P]),
     "bh_smooth": (_I, [_P, _I, _P, _P, _I]),
     "bh_smooth_colors": (_I, [_P, _I, _P, _P, _I, _I]),
     "bh_prolongate_add": (_I, [_P, _I, _P, _P]),
@@ -203,12 +204,13 @@ def apply_A_noalloc(dim, degree, level, gamma, x, y, stream=None):
                                      _dev(y, n, "y"), ctypes.c_void_p(stream.cuda_stream)))
 
 
-def _dev(t, n, name):
+def _dev(t, n, name, dtype=None):
     import torch
+    dtype = torch.float64 if dtype is None else dtype
     if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
         raise TypeError("%s must be a CUDA tensor" % name)
-    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
-        raise ValueError("%s must be a contiguous float64 tensor with %d values" % (name, n))
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be a contiguous %s tensor with %d values" % (name, dtype, n))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -262,6 +264,14 @@ class Context:
         n = self.num_unknowns(level)
         _check(load().bh_residual(self.handle, level, _dev(x, n, "x"), _dev(b, n, "b"),
                                   _dev(r, n, "r")))
+
+    def defect_compensated(self, level, x, b, r):
+        """bh_defect_compensated: r = b - A_l x for a float32 x, in compensated
+        FP32 arithmetic (mixed-precision contexts)."""
+        import torch
+        n = self.num_unknowns(level)
+        _check(load().bh_defect_compensated(self.handle, level, _dev(x, n, "x", torch.float32),
+                                            _dev(b, n, "b"), _dev(r, n, "r")))
 
     def smooth(self, level, x, b, steps=1):
         """bh_smooth: `steps` steps of the context's smoother (Sec. 3), x in place."""

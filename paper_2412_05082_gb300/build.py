@@ -17,9 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbiharm.so")
 # the longest translation units first
-SOURCES = ["batch_pers_f64.cu", "batch_pers_f32.cu", "inst_f64.cu", "inst_f32.cu",
+SOURCES = ["defect_ff_k7.cu", "defect_ff_k6.cu", "batch_pers_f64.cu", "batch_pers_f32.cu",
+           "defect_ff_k5.cu", "defect_ff_k2_4.cu", "inst_f64.cu", "inst_f32.cu",
            "batch_mvs_f64.cu", "batch_mvs_f32.cu", "batch.cu", "vec.cu", "api.cu", "setup.cpp",
-           "noalloc.cu", "serve.cpp", "probe.cu", "gemm.cu"]
+           "noalloc.cu", "serve.cpp", "probe.cu", "gemm.cu", "defect_ff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

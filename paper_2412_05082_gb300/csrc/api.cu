@@ -94,7 +94,11 @@ int color_of(const int* v, int d) {
 
 bool mixed(const bh_ctx* c) { return c->p.precision != BH_FP64; }
 // FP32 V-cycle whose defects before each restriction are evaluated in FP64
-bool defect64(const bh_ctx* c) { return c->p.precision == BH_MIXED_FP32_R64; }
+// the FP32 V-cycle's defect before each restriction outside FP32 arithmetic:
+// in FP64 (BH_MIXED_FP32_R64) or compensated FP32 (BH_MIXED_FP32_RC)
+bool defect64(const bh_ctx* c) {
+  return c->p.precision == BH_MIXED_FP32_R64 || c->p.precision == BH_MIXED_FP32_RC;
+}
 
 // typed accessors for the V-cycle template
 template <typename T> struct TypeOf;
@@ -225,13 +229,21 @@ bh_status smooth_t(bh_ctx* c, int l, T* x, const T* b, int steps, bool x_zero) {
 // Lc.b32.  In FP32 arithmetic the cancellation in A x leaves a rounding error
 // of about eps_32 ||A|| ||x||, whose smooth part the coarse-grid correction
 // amplifies like the condition number of A_l.
+//
+// BH_MIXED_FP32_RC: the same defect in compensated FP32 arithmetic (double-float
+// values, exact products by FMA, error-free sums: defect_ff.cu), about 2^-44 of
+// sum |terms| accurate, on the FP32 pipes; the restriction stays FP64.
 bh_status restrict_defect64(bh_ctx* c, int l, const float* x, bool x_zero) {
   Level& L = c->lv[l];
   Level& Lc = c->lv[l - 1];
   const double* r = L.db64;
   if (!(x_zero && c->p.pre_steps == 0)) {
-    CK(vec_f2d(L.dx64, x, L.g.nd, c->st));
-    CKS(residual_t<double>(c, l, L.dx64, L.db64, L.r64));
+    if (c->p.precision == BH_MIXED_FP32_RC) {
+      CK(defect_ff(c->tab32, L.g, x, L.db64, L.r64, L.ascale, c->scr64, c->st));
+    } else {
+      CK(vec_f2d(L.dx64, x, L.g.nd, c->st));
+      CKS(residual_t<double>(c, l, L.dx64, L.db64, L.r64));
+    }
     r = L.r64;
   }
   CK(Ops<double>::restrict_(c->tab64, L.g, r, Lc.db64, c->xs64[0], c->xs64[1], c->st));
@@ -651,7 +663,7 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
   if (p.level < 1 || p.level > 14) return fail(BH_EINVAL, "level must be in 1..14");
   if (p.smoother < 0 || p.smoother > 2) return fail(BH_EINVAL, "unknown smoother");
   if (p.local_solver < 0 || p.local_solver > 1) return fail(BH_EINVAL, "unknown local solver");
-  if (p.precision < 0 || p.precision > 2) return fail(BH_EINVAL, "unknown precision");
+  if (p.precision < 0 || p.precision > 3) return fail(BH_EINVAL, "unknown precision");
   if (p.pre_steps < 0 || p.post_steps < 0) return fail(BH_EINVAL, "negative smoothing steps");
   if (p.gmres_side < 0 || p.gmres_side > 1) return fail(BH_EINVAL, "unknown GMRES side");
   if (p.coarse < 0 || p.coarse > 1) return fail(BH_EINVAL, "unknown coarse solver");
@@ -724,8 +736,10 @@ bh_status bh_create(const bh_params* params, void* stream, bh_ctx** out) {
     if (mx && ((status = dmalloc(c, &L.x32, nd)) || (status = dmalloc(c, &L.b32, nd)) ||
                (status = dmalloc(c, &L.r32, nd))))
       return bail(status);
-    if (p.precision == BH_MIXED_FP32_R64 &&
-        ((status = dmalloc(c, &L.db64, nd)) || (status = dmalloc(c, &L.dx64, nd))))
+    if ((p.precision == BH_MIXED_FP32_R64 || p.precision == BH_MIXED_FP32_RC) &&
+        (status = dmalloc(c, &L.db64, nd)))
+      return bail(status);
+    if (p.precision == BH_MIXED_FP32_R64 && (status = dmalloc(c, &L.dx64, nd)))
       return bail(status);
     // vertex patches sorted by color (Sec. 3), lexicographic inside a color
     const int Nm = L.g.N - 1;
@@ -930,6 +944,19 @@ bh_status bh_residual(bh_ctx* ctx, int level, const double* x, const double* b, 
   CKS(check_level(ctx, level));
   if (!x || !b || !r || r == x) return fail(BH_EINVAL, "bad vector arguments");
   CKS(residual_t<double>(ctx, level, x, b, r));
+  ctx->n_apply++;
+  return BH_OK;
+}
+
+bh_status bh_defect_compensated(bh_ctx* ctx, int level, const float* x, const double* b,
+                                double* r) {
+  CKS(check_level(ctx, level));
+  if (!ctx->tab32)
+    return fail(BH_EINVAL, "compensated defect: needs a mixed-precision context (FP32 tables)");
+  if (!x || !b || !r || (const void*)r == (const void*)x)
+    return fail(BH_EINVAL, "bad vector arguments");
+  Level& L = ctx->lv[level];
+  CK(defect_ff(ctx->tab32, L.g, x, b, r, L.ascale, ctx->scr64, ctx->st));
   ctx->n_apply++;
   return BH_OK;
 }

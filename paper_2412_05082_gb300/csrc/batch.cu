@@ -143,6 +143,14 @@ struct SweepOp {  // one batched sweep launch
   int64_t total = 0;
 };
 
+struct FfOp {  // one batched compensated-defect sweep launch (problems of one degree)
+  DevArray<FfSweepArgs> args;
+  DevArray<int64_t> prefix;
+  DevArray<int> pid;
+  int64_t total = 0;
+  int k = 0;
+};
+
 template <typename T>
 struct XferOp {
   DevArray<XferArgs<T>> args;
@@ -197,6 +205,9 @@ struct Depth {  // operations at depth t of the lockstep V-cycle
   SweepOp<double> res_x, res_y;
   XferOp<double> restr[2];  // FP64 restriction into b64 (FP64) / db64 (R64) of level l-1
   ConvOpList x_f2d;         // R64: dx64 = x32 on level l
+  // RC: the defect of x32 in compensated FP32, a launch per degree (replaces
+  // res_x, res_y and x_f2d)
+  std::vector<FfOp> ff_x, ff_y;
   ConvOpList b_d2f;         // R64: b32 = db64 on level l-1
   DevArray<int> symv_pid;
   int nsymv = 0, maxn_symv = 0;
@@ -223,7 +234,8 @@ struct bh_batch {
   std::vector<bh_ctx*> ctx;
   std::vector<int> k, L;
   int m = 0;           // GMRES restart length
-  bool mixed = false;  // FP32 V-cycle with FP64 defects
+  bool mixed = false;  // FP32 V-cycle with FP64 (R64) or compensated FP32 (RC) defects
+  bool rc = false;     // BH_MIXED_FP32_RC
   bool right = false;  // right (flexible) preconditioning
   int pre = 1, post = 1;
   int tile[8] = {0};  // patches per block per degree (0 = default)
@@ -231,6 +243,7 @@ struct bh_batch {
   int* d_k = nullptr;
   const void** d_tabs64 = nullptr;
   const void** d_tabs32 = nullptr;
+  const void** d_tabsff = nullptr;  // RC: FfTab<k> per problem
   int* d_active = nullptr;
   double* d_dots = nullptr;      // [P][m + 2]
   double* d_coef = nullptr;      // [P][m + 2]
@@ -284,6 +297,28 @@ Meta meta(const bh_batch* b) {
 
 unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
+// one compensated-defect sweep of level Lv along axis 0 (x: FP32 iterate ->
+// out) or 1 (in -> r = b - A x)
+FfSweepArgs ff_args(const Level& Lv, int axis, const float* x, float2* const* io,
+                    const double* bvec, double* r) {
+  FfSweepArgs a{};
+  a.d = 2;
+  a.N = Lv.g.N;
+  a.n = Lv.g.n;
+  a.lines = Lv.g.nd / Lv.g.n;
+  a.stride = axis == 0 ? 1 : Lv.g.n;
+  a.axis = axis;
+  a.scale = Lv.ascale;
+  a.x = x;
+  for (int i = 0; i < 3; ++i) {
+    a.in[i] = axis == 1 ? io[i] : nullptr;
+    a.out[i] = axis == 0 ? io[i] : nullptr;
+  }
+  a.b = bvec;
+  a.r = r;
+  return a;
+}
+
 template <typename T>
 SweepArgs<T> sweep_args(const Level& Lv, int axis, const T* in0, const T* in1, const T* in2,
                         T* o0, T* o1, T* o2, const T* bvec, int mode) {
@@ -311,6 +346,22 @@ template <typename T>
 bh_status make_sweep(bh_batch* b, const std::vector<std::pair<int, SweepArgs<T>>>& items,
                      SweepOp<T>& op) {
   std::vector<SweepArgs<T>> args;
+  std::vector<int64_t> prefix{0};
+  std::vector<int> pid;
+  for (auto& it : items) {
+    args.push_back(it.second);
+    pid.push_back(it.first);
+    prefix.push_back(prefix.back() + it.second.lines * it.second.N);
+  }
+  op.total = prefix.back();
+  BCKS(upload(b, args, op.args));
+  BCKS(upload(b, prefix, op.prefix));
+  BCKS(upload(b, pid, op.pid));
+  return BH_OK;
+}
+
+bh_status make_ff(bh_batch* b, const std::vector<std::pair<int, FfSweepArgs>>& items, FfOp& op) {
+  std::vector<FfSweepArgs> args;
   std::vector<int64_t> prefix{0};
   std::vector<int> pid;
   for (auto& it : items) {
@@ -561,6 +612,7 @@ bh_status build_depths(bh_batch* b) {
     std::vector<std::pair<int, SweepArgs<double>>> rx, ry;
     std::vector<std::pair<int, XferArgs<double>>> r0, r1;
     std::vector<std::pair<int, Conv>> xf, bd;
+    std::vector<std::pair<int, FfSweepArgs>> fx[kMaxK + 1], fy[kMaxK + 1];
     for (int p = 0; p < P; ++p) {
       const int l = b->L[p] - t;
       if (l < 1) continue;
@@ -580,18 +632,34 @@ bh_status build_depths(bh_batch* b) {
       const double* xin = b->mixed ? Lv.dx64 : Lv.x64;
       const double* bin = (b->mixed && l != b->L[p]) ? Lv.db64 : Lv.b64;
       double* bc = b->mixed ? Lc.db64 : Lc.b64;
-      rx.push_back({p, sweep_args<double>(Lv, 0, xin, nullptr, nullptr, s0, s1, s2, nullptr, kStore)});
-      ry.push_back({p, sweep_args<double>(Lv, 1, s0, s1, s2, Lv.r64, nullptr, nullptr, bin, kResidual)});
+      if (b->rc) {
+        // double-float intermediates in the FP64 scratch (8 bytes per value)
+        float2* io[3] = {reinterpret_cast<float2*>(s0), reinterpret_cast<float2*>(s1),
+                         reinterpret_cast<float2*>(s2)};
+        fx[b->k[p]].push_back({p, ff_args(Lv, 0, Lv.x32, io, nullptr, nullptr)});
+        fy[b->k[p]].push_back({p, ff_args(Lv, 1, nullptr, io, bin, Lv.r64)});
+      } else {
+        rx.push_back({p, sweep_args<double>(Lv, 0, xin, nullptr, nullptr, s0, s1, s2, nullptr, kStore)});
+        ry.push_back({p, sweep_args<double>(Lv, 1, s0, s1, s2, Lv.r64, nullptr, nullptr, bin, kResidual)});
+      }
       r0.push_back({p, xfer_args<double, false>(0, Lv.g, Lv.r64, c->xs64[0], false)});
       r1.push_back({p, xfer_args<double, false>(1, Lv.g, c->xs64[0], bc, false)});
       if (b->mixed) {
-        xf.push_back({p, Conv{Lv.dx64, Lv.x32, Lv.g.nd, 0}});
+        if (!b->rc) xf.push_back({p, Conv{Lv.dx64, Lv.x32, Lv.g.nd, 0}});
         bd.push_back({p, Conv{Lc.db64, Lc.b32, Lc.g.nd, 0}});
       }
     }
     if (D.smooth) {
       BCKS(make_sweep(b, rx, D.res_x));
       BCKS(make_sweep(b, ry, D.res_y));
+      for (int k = 0; k <= kMaxK; ++k) {
+        if (fx[k].empty()) continue;
+        D.ff_x.emplace_back();
+        D.ff_y.emplace_back();
+        D.ff_x.back().k = D.ff_y.back().k = k;
+        BCKS(make_ff(b, fx[k], D.ff_x.back()));
+        BCKS(make_ff(b, fy[k], D.ff_y.back()));
+      }
       BCKS(make_xfer(b, r0, D.restr[0]));
       BCKS(make_xfer(b, r1, D.restr[1]));
       if (b->mixed) {
@@ -625,6 +693,36 @@ cudaError_t run_sweep(bh_batch* b, const SweepOp<T>& op, int kind) {
                                                    op.pid.n);
   count_launch(b);
   return cudaGetLastError();
+}
+
+// one compensated-defect sweep: a launch per degree, forked onto the side
+// streams and joined back like the patch launches
+cudaError_t run_ff(bh_batch* b, const std::vector<FfOp>& ops, int kind) {
+  if (ops.empty()) return cudaSuccess;
+  cudaError_t e;
+  const bool fork = ops.size() > 1;
+  if (fork && (e = cudaEventRecord(b->fork, b->st)) != cudaSuccess) return e;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const FfOp& op = ops[i];
+    cudaStream_t st = fork ? b->side[i] : b->st;
+    if (fork && (e = cudaStreamWaitEvent(st, b->fork, 0)) != cudaSuccess) return e;
+    const FfSweepArgs* args = op.args.d;
+    const int64_t* prefix = op.prefix.d;
+    const int* pid = op.pid.d;
+    int n = op.pid.n;
+    const int* active = b->d_active;
+    const void* const* tabs = b->d_tabsff;
+    void* params[] = {&args, &prefix, &pid, &n, &active, &tabs};
+    if ((e = cudaLaunchKernel(ff_list_kernel(op.k, kind), dim3(blocks_for(op.total, 128)),
+                              dim3(128), params, 0, st)) != cudaSuccess)
+      return e;
+    count_launch(b);
+    if (fork && (e = cudaEventRecord(b->join[i], st)) != cudaSuccess) return e;
+  }
+  if (fork)
+    for (size_t i = 0; i < ops.size(); ++i)
+      if ((e = cudaStreamWaitEvent(b->st, b->join[i], 0)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -740,9 +838,14 @@ cudaError_t vcycle_from(bh_batch* b, int t) {
   if (!D.smooth) return cudaSuccess;
   for (int s = 0; s < b->pre; ++s)
     if ((e = run_colors<T>(b, V, 0, 8)) != cudaSuccess) return e;
-  if (b->mixed && (e = run_conv(b, D.x_f2d, kF2D)) != cudaSuccess) return e;
-  if ((e = run_sweep<double>(b, D.res_x, 0)) != cudaSuccess) return e;
-  if ((e = run_sweep<double>(b, D.res_y, 2)) != cudaSuccess) return e;
+  if (b->rc) {
+    if ((e = run_ff(b, D.ff_x, 0)) != cudaSuccess) return e;
+    if ((e = run_ff(b, D.ff_y, 2)) != cudaSuccess) return e;
+  } else {
+    if (b->mixed && (e = run_conv(b, D.x_f2d, kF2D)) != cudaSuccess) return e;
+    if ((e = run_sweep<double>(b, D.res_x, 0)) != cudaSuccess) return e;
+    if ((e = run_sweep<double>(b, D.res_y, 2)) != cudaSuccess) return e;
+  }
   if ((e = run_xfer<double>(b, D.restr[0], false)) != cudaSuccess) return e;
   if ((e = run_xfer<double>(b, D.restr[1], false)) != cudaSuccess) return e;
   if (b->mixed && (e = run_conv(b, D.b_d2f, kD2F)) != cudaSuccess) return e;
@@ -1061,6 +1164,7 @@ bh_status prepare(bh_batch* b) {
     }
     *b->h_status = 0;
   }
+  if (b->rc) return BH_OK;  // graph form only
   return b->mixed ? build_phases<float>(b, top) : build_phases<double>(b, top);
 }
 
@@ -1189,9 +1293,11 @@ bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_b
         p.krylov != BH_GMRES)
       return berr(BH_EINVAL, "bh_batch_create: the batched form runs colored MVS with FDM local "
                              "solvers, the exact coarse solve and GMRES");
-    if (p.precision != BH_FP64 && p.precision != BH_MIXED_FP32_R64)
+    if (p.precision != BH_FP64 && p.precision != BH_MIXED_FP32_R64 &&
+        p.precision != BH_MIXED_FP32_RC)
       return berr(BH_EINVAL, "bh_batch_create: the batched form runs the FP64 V-cycle or the FP32 "
-                             "V-cycle with FP64 defects (BH_MIXED_FP32_R64)");
+                             "V-cycle with FP64 or compensated defects (BH_MIXED_FP32_R64, "
+                             "BH_MIXED_FP32_RC)");
     if (p.precision != params[0].precision || p.gmres_side != params[0].gmres_side ||
         p.pre_steps != params[0].pre_steps || p.post_steps != params[0].post_steps)
       return berr(BH_EINVAL, "bh_batch_create: precision, GMRES side and smoothing steps must be "
@@ -1206,7 +1312,8 @@ bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_b
   if (!b) return berr(BH_ENOMEM, "host allocation failed");
   b->P = count;
   b->user = (cudaStream_t)stream;
-  b->mixed = params[0].precision == BH_MIXED_FP32_R64;
+  b->mixed = params[0].precision == BH_MIXED_FP32_R64 || params[0].precision == BH_MIXED_FP32_RC;
+  b->rc = params[0].precision == BH_MIXED_FP32_RC;
   b->right = params[0].gmres_side == BH_RIGHT;
   b->pre = params[0].pre_steps;
   b->post = params[0].post_steps;
@@ -1233,20 +1340,23 @@ bh_status bh_batch_create(const bh_params* params, int count, void* stream, bh_b
     b->k.push_back(p.degree);
     b->L.push_back(p.level);
   }
-  std::vector<const void*> tabs64, tabs32;
+  std::vector<const void*> tabs64, tabs32, tabsff;
   for (int p = 0; p < count; ++p) {
     tabs64.push_back(Ops<double>::device_tables(b->ctx[p]->tab64, b->k[p]).tables);
     tabs32.push_back(b->mixed ? Ops<float>::device_tables(b->ctx[p]->tab32, b->k[p]).tables
                               : nullptr);
+    tabsff.push_back(b->rc ? ff_device_tables(b->ctx[p]->tab32, b->k[p]) : nullptr);
   }
   DevArray<int> dk;
-  DevArray<const void*> dt64, dt32;
+  DevArray<const void*> dt64, dt32, dtff;
   bh_status s;
-  if ((s = upload(b, b->k, dk)) || (s = upload(b, tabs64, dt64)) || (s = upload(b, tabs32, dt32)))
+  if ((s = upload(b, b->k, dk)) || (s = upload(b, tabs64, dt64)) || (s = upload(b, tabs32, dt32)) ||
+      (s = upload(b, tabsff, dtff)))
     return bail(s);
   b->d_k = dk.d;
   b->d_tabs64 = dt64.d;
   b->d_tabs32 = dt32.d;
+  b->d_tabsff = dtff.d;
   std::vector<int> act(count, 1);
   DevArray<int> da;
   if ((s = upload(b, act, da))) return bail(s);
@@ -1298,6 +1408,9 @@ bh_status bh_batch_set_tile(bh_batch* b, int degree, int patches_per_block) {
 
 bh_status bh_batch_set_persistent(bh_batch* b, int on) {
   if (!b || (on != 0 && on != 1)) return berr(BH_EINVAL, "bh_batch_set_persistent: bad arguments");
+  if (on == 1 && b->rc)
+    return berr(BH_EINVAL, "bh_batch_set_persistent: the compensated defect (BH_MIXED_FP32_RC) "
+                           "runs in the graph form only");
   b->persistent = on == 1;
   return BH_OK;
 }
@@ -1305,6 +1418,9 @@ bh_status bh_batch_set_persistent(bh_batch* b, int on) {
 bh_status bh_batch_check_barrier_timeout(bh_batch* b, double wait_ms) {
   if (!b || !(wait_ms > 0.0) || wait_ms > 10000.0)
     return berr(BH_EINVAL, "bh_batch_check_barrier_timeout: wait_ms must be in (0, 10000]");
+  if (b->rc)
+    return berr(BH_EINVAL, "bh_batch_check_barrier_timeout: no persistent form for "
+                           "BH_MIXED_FP32_RC");
   int dev = 0, clock_khz = 0;
   BCK(cudaGetDevice(&dev));
   BCK(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));

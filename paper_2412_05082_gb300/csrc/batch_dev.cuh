@@ -22,19 +22,6 @@ struct Meta {                 // per problem, indexed by problem id
   const int* active;          // 0: problem finished, skip it
 };
 
-// first index p with prefix[p + 1] > tid (prefix[0] = 0, increasing)
-__device__ __forceinline__ int find_seg(const int64_t* prefix, int n, int64_t tid) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= tid)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
 #define BH_KSWITCH(k, CALL) \
   switch (k) {              \
     case 2: CALL(2); break; \

@@ -68,6 +68,19 @@ __host__ __device__ constexpr int band_hi(int op, int q, int K) {
   return op == 2 ? (q == 0 ? 2 * K : 2 * K - q) : (q == 0 ? K : K - q);
 }
 
+// first index p with prefix[p + 1] > tid (prefix[0] = 0, increasing)
+__device__ __forceinline__ int find_seg(const int64_t* prefix, int n, int64_t tid) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= tid)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // Coordinates of a line (all non-axis coordinates) -> offset, x fastest.
 __device__ __forceinline__ int64_t line_offset(int64_t line, int d, int axis, const int* dims,
                                                const int64_t* strides) {

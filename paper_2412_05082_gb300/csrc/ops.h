@@ -105,6 +105,18 @@ cudaError_t gemm_f64_sliced(int md, int cnt, double alpha, const uint16_t* As, c
 cudaError_t gemm_f32(int md, int cnt, float alpha, const float* A, const float* R, float* Y,
                      cudaStream_t st);
 
+// ---- compensated defect of the FP32 V-cycle (defect_ff.cu) -------------------
+// r = b - scale * A_ref x for an FP32 x, in double-float arithmetic on the FP32
+// pipes (ffsweep.cuh), from the FP32 tables `tab32` (Ops<float>::make_tables);
+// scratch: apply_scratch_arrays(d) * nd float2 values (8 bytes each).
+cudaError_t defect_ff(const void* tab32, const LevelGeom& g, const float* x, const double* b,
+                      double* r, double scale, void* scratch, cudaStream_t st);
+// device copy of the hi + lo class tables (FfTab<k>) of FP32 tables
+const void* ff_device_tables(const void* tab32, int k);
+// the batched form's list kernel of degree k (ff_sweep_list_kernel; kind 0: the
+// split of the FP32 x, 2: the residual), as the address the runtime API takes
+const void* ff_list_kernel(int k, int kind);
+
 // ---- vector kernels (FP64 unless noted) -------------------------------------
 // Deterministic dot product: partial sums per block, then one block in fixed order.
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs

@@ -6,6 +6,7 @@
 #include <new>
 #include <vector>
 
+#include "ffsweep.cuh"
 #include "kernels.cuh"
 #include "mvs.cuh"
 #include "mvs3.cuh"
@@ -18,6 +19,10 @@ struct HostTables {
   MvsTab<T, K> mvs;  // operator + FDM tables for the fused MVS kernel
   Tables<T, K>* dev = nullptr;  // device copy of t (batched kernels read it from memory)
   T* dinv = nullptr;  // device, 4^d slots x m^d reciprocals of the eigenvalue sums
+  // FP32 tables only: the operator's class tables as hi + lo FP32 parts for the
+  // compensated defect (ffsweep.cuh), host copy and device copy
+  FfTab<K>* ff = nullptr;
+  FfTab<K>* dev_ff = nullptr;
   int d = 0;
 };
 
@@ -61,9 +66,36 @@ static void* make_tables_k(const Setup1D& s, int d) {
       dinv[(size_t)slot * md + l] = (T)(1.0 / sum);
     }
   h->d = d;
+  if constexpr (sizeof(T) == 4) {
+    h->ff = new (std::nothrow) FfTab<K>();
+    if (!h->ff) {
+      delete h;
+      return nullptr;
+    }
+    const double* src[3] = {s.tabM.data(), s.tabL.data(), s.tabB.data()};
+    float(*hi[3])[4 * K + 1] = {h->ff->hi.M, h->ff->hi.L, h->ff->hi.B};
+    float(*lo[3])[4 * K + 1] = {h->ff->lo.M, h->ff->lo.L, h->ff->lo.B};
+    for (int o = 0; o < 3; ++o)
+      for (int c = 0; c < nc; ++c)
+        for (int t = 0; t < bw; ++t) {
+          const double v = src[o][c * bw + t];
+          const float vh = (float)v;
+          hi[o][c][t] = vh;
+          lo[o][c][t] = (float)(v - (double)vh);
+        }
+    if (cudaMalloc(&h->dev_ff, sizeof(FfTab<K>)) != cudaSuccess ||
+        cudaMemcpy(h->dev_ff, h->ff, sizeof(FfTab<K>), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(h->dev_ff);
+      delete h->ff;
+      delete h;
+      return nullptr;
+    }
+  }
   if (cudaMalloc(&h->dev, sizeof(Tables<T, K>)) != cudaSuccess ||
       cudaMemcpy(h->dev, &h->t, sizeof(Tables<T, K>), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(h->dev);
+    cudaFree(h->dev_ff);
+    delete h->ff;
     delete h;
     return nullptr;
   }
@@ -72,6 +104,8 @@ static void* make_tables_k(const Setup1D& s, int d) {
           cudaSuccess) {
     cudaFree(h->dinv);
     cudaFree(h->dev);
+    cudaFree(h->dev_ff);
+    delete h->ff;
     delete h;
     return nullptr;
   }
@@ -111,6 +145,8 @@ static void free_tables_k(void* p) {
   auto* h = static_cast<HostTables<T, K>*>(p);
   cudaFree(h->dinv);
   cudaFree(h->dev);
+  cudaFree(h->dev_ff);
+  delete h->ff;
   delete h;
 }
 

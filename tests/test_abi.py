@@ -62,7 +62,8 @@ def test_default_params_and_validation(lib):
     ({"krylov": 1}, "symmetric"),                       # CG with the multiplicative smoother
     ({"precision": 1, "gmres_side": 1}, "flexible"),   # FP32 V-cycle with left GMRES
     ({"precision": 2, "gmres_side": 1}, "flexible"),   # FP32 V-cycle, FP64 defects, left GMRES
-    ({"precision": 3}, "precision"),
+    ({"precision": 3, "gmres_side": 1}, "flexible"),   # compensated FP32 defects, left GMRES
+    ({"precision": 4}, "precision"),
 ])
 def test_create_rejects_inconsistent_options_before_touching_a_device(lib, overrides, msg):
     # option checks run before device discovery, so they hold on a CPU-only host

@@ -120,8 +120,10 @@ def test_batched_solve_restarts(bh):
             batch.solve(B, X, 1e-8, 3)
 
 
-def test_batched_mixed_precision_vcycle_and_solve(bh):
-    """The FP32 V-cycle with FP64 defects (BH_MIXED_FP32_R64) in the batch.
+@pytest.mark.parametrize("precision", ["r64", "rc"])
+def test_batched_mixed_precision_vcycle_and_solve(bh, precision):
+    """The FP32 V-cycle with FP64 defects (BH_MIXED_FP32_R64) or compensated
+    FP32 defects (BH_MIXED_FP32_RC) in the batch.
     One V-cycle: within 1e-3 of the FP64 oracle's -- FP32 rounding (eps 6e-8)
     amplified by the condition numbers of the patch problems, which grow with
     the degree (1.5e-4 measured at k = 6) -- and no farther from the same
@@ -132,7 +134,8 @@ def test_batched_mixed_precision_vcycle_and_solve(bh):
     oracle's FP64 GMRES, the solution within 1e-6 of it."""
     Hs = hierarchies()
     bs = [rhs_rough_solution(H.A[H.L], 500 + i)[0] for i, H in enumerate(Hs)]
-    params = [bh.default_params(d, k, L, precision=bh.MIXED_FP32_R64) for d, k, L in MIX]
+    prec = bh.MIXED_FP32_R64 if precision == "r64" else bh.MIXED_FP32_RC
+    params = [bh.default_params(d, k, L, precision=prec) for d, k, L in MIX]
     with bh.Batch(params) as batch:
         B = [cuda(b) for b in bs]
         X = [torch.empty_like(v) for v in B]
@@ -179,7 +182,7 @@ def test_batched_color_with_the_512_cell_problem(bh, color):
         assert relerr(g - x, ref - x) <= 1e-10, (k, L)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "r64"])
+@pytest.mark.parametrize("precision", ["fp64", "r64", "rc"])
 def test_batched_sweep_solve_reaches_true_residual(bh, precision):
     """The benchmark's workload (2D Q2-Q4 on 512^2 and Q5-Q7 on 256^2 cells,
     b = A x* with x* ~ U[-1, 1]) solved as one batch by right-preconditioned
@@ -190,7 +193,7 @@ def test_batched_sweep_solve_reaches_true_residual(bh, precision):
     ops = [kron.KronOperator(d, k, N) for d, k, N in probs]
     xstar = [workload.vector_uniform((k * N - 1) ** d, k) for d, k, N in probs]
     bs = [A @ xs for A, xs in zip(ops, xstar)]
-    prec = bh.FP64 if precision == "fp64" else bh.MIXED_FP32_R64
+    prec = {"fp64": bh.FP64, "r64": bh.MIXED_FP32_R64, "rc": bh.MIXED_FP32_RC}[precision]
     params = [bh.default_params(d, k, workload.level_of(N), precision=prec) for d, k, N in probs]
     with bh.Batch(params) as batch:
         B = [cuda(b) for b in bs]
@@ -274,6 +277,9 @@ def test_batch_tiles_and_graph(bh):
                   bh.default_params(2, 3, 3, precision=bh.MIXED_FP32_R64)])
     with pytest.raises(bh.BiharmError):              # FP32 V-cycle needs right GMRES
         bh.Batch([bh.default_params(2, 2, 3, precision=bh.MIXED_FP32_R64, gmres_side=bh.LEFT)])
+    with bh.Batch([bh.default_params(2, 2, 3, precision=bh.MIXED_FP32_RC)]) as batch:
+        with pytest.raises(bh.BiharmError):          # compensated defects: graph form only
+            batch.set_persistent(True)
 
 
 def test_batch_autotuner_keeps_results(bh, tmp_path, monkeypatch):

@@ -6,6 +6,7 @@ reach the same 1e-8 relative residual with iteration counts within +-1."""
 import functools
 
 import numpy as np
+import scipy.sparse as sp
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -213,19 +214,65 @@ def test_solve_matches_oracle(bh, d, k, L, side):
         assert abs(est / (hist[-1] / hist[0]) - 1.0) <= 1e-3, (est, hist[-1] / hist[0])
 
 
+def mixed_mode(bh, mode):
+    return {"fp32": bh.MIXED_FP32, "r64": bh.MIXED_FP32_R64, "rc": bh.MIXED_FP32_RC}[mode]
+
+
+@pytest.mark.parametrize("d,k,L", [(2, 2, 4), (2, 4, 4), (2, 5, 3), (2, 7, 3), (3, 2, 3),
+                                   (3, 4, 2), (3, 7, 2)])
+def test_compensated_defect_matches_fp64_defect(bh, d, k, L):
+    """bh_defect_compensated, the defect of BH_MIXED_FP32_RC, for an FP32
+    iterate: at every node within 2^-36 of S = (|B| (x) |M| + 2 |L| (x) |L| +
+    |M| (x) |B|) |x| + |b| (3D: the six terms) of the exact defect b - A x,
+    evaluated by the oracle's Kronecker form in FP64.  The bound is the
+    worst case of the double-float sums (n^2 2^-48 of the largest partial
+    sum for n <= 4k+1 band terms, three sweeps); FP32 arithmetic would leave
+    errors of about 2^-24 S.  Checked on a random b and on b = A x, where the
+    defect cancels to rounding."""
+    N = 2 ** L
+    A = kron.kron_matrix(d, k, N).tocsr()
+    M, Lm, B = (abs(np.asarray(m)) for m in kron.global_1d(k, N))
+    if d == 2:
+        S = sp.kron(M, B) + 2 * sp.kron(Lm, Lm) + sp.kron(B, M)
+    else:
+        def k3(a, b2, c):
+            return sp.kron(sp.kron(a, b2), c)
+        S = (k3(M, M, B) + k3(M, B, M) + k3(B, M, M)
+             + 2 * (k3(M, Lm, Lm) + k3(Lm, M, Lm) + k3(Lm, Lm, M)))
+    n = A.shape[0]
+    rng = np.random.default_rng(1000 + 10 * d + k)
+    x32 = rng.uniform(-1.0, 1.0, n).astype(np.float32)
+    xd = x32.astype(np.float64)
+    with make_ctx(bh, d, k, L, precision=bh.MIXED_FP32_RC, gmres_side=bh.RIGHT) as ctx:
+        X = torch.tensor(x32, device="cuda")
+        for case, b in (("random", rng.uniform(-1.0, 1.0, n)), ("cancel", A @ xd)):
+            ref = b - A @ xd
+            bound = 2.0 ** -36 * (S @ np.abs(xd) + np.abs(b))
+            R = torch.empty(n, dtype=torch.float64, device="cuda")
+            ctx.defect_compensated(L, X, cuda(b), R)
+            err = np.abs(host(R) - ref)
+            assert np.all(err <= bound), (case, float((err / bound).max()))
+    with make_ctx(bh, d, k, L) as ctx64:          # an FP64 context has no FP32 tables
+        with pytest.raises(bh.BiharmError):
+            ctx64.defect_compensated(L, X, cuda(xd), torch.empty(n, dtype=torch.float64,
+                                                                 device="cuda"))
+
+
 @pytest.mark.parametrize("d,k,L,mode", [(2, 2, 5, "fp32"), (2, 3, 5, "fp32"), (2, 4, 4, "fp32"),
                                          (3, 2, 3, "fp32"), (3, 3, 3, "fp32"),
                                          (2, 2, 5, "r64"), (2, 4, 4, "r64"), (2, 6, 3, "r64"),
-                                         (2, 7, 3, "r64"), (3, 3, 3, "r64"), (3, 5, 2, "r64")])
+                                         (2, 7, 3, "r64"), (3, 3, 3, "r64"), (3, 5, 2, "r64"),
+                                         (2, 2, 5, "rc"), (2, 4, 4, "rc"), (2, 6, 3, "rc"),
+                                         (2, 7, 3, "rc"), (3, 3, 3, "rc"), (3, 5, 2, "rc")])
 def test_mixed_precision_solve(bh, d, k, L, mode):
     """FP32 V-cycle inside flexible FP64 GMRES (Sec. 5.2, shown there for
-    Q2-Q4), and the variant with FP64 defects before each restriction: the
-    same 1e-8 true residual, at most one more iteration than FP64, and the
-    same solution (both within 1e-6 of the dense solve)."""
+    Q2-Q4), and the variants with FP64 or compensated FP32 defects before each
+    restriction: the same 1e-8 true residual, at most one more iteration than
+    FP64, and the same solution (both within 1e-6 of the dense solve)."""
     n = (k * 2 ** L - 1) ** d
     b = workload.rhs_uniform(n, 21)
     exact = np.linalg.solve(oracle_A(d, k, 2 ** L).toarray(), b)
-    prec = bh.MIXED_FP32 if mode == "fp32" else bh.MIXED_FP32_R64
+    prec = mixed_mode(bh, mode)
     res = {}
     for pr in (bh.FP64, prec):
         with make_ctx(bh, d, k, L, precision=pr, gmres_side=bh.RIGHT) as ctx:
@@ -301,7 +348,7 @@ def test_mixed_precision_3d_high_degree(bh, k):
     b = workload.rhs_uniform(n, 41)
     Aop = kron.KronOperator(d, k, 2 ** L)
     res = {}
-    for pr in (bh.FP64, bh.MIXED_FP32, bh.MIXED_FP32_R64):
+    for pr in (bh.FP64, bh.MIXED_FP32, bh.MIXED_FP32_R64, bh.MIXED_FP32_RC):
         with make_ctx(bh, d, k, L, precision=pr, gmres_side=bh.RIGHT) as ctx:
             X = torch.empty(n, dtype=torch.float64, device="cuda")
             res[pr] = ctx.solve(cuda(b), X, 1e-8, 100) + (host(X),)
@@ -314,22 +361,23 @@ def test_mixed_precision_3d_high_degree(bh, k):
 
 @pytest.mark.parametrize("k,L", [(6, 8), (7, 7)])
 def test_fp64_defects_keep_the_fp32_vcycle_converging_on_fine_meshes(bh, k, L):
-    """2D, high degree, fine mesh (2.4 M and 0.8 M unknowns): with FP64
-    defects before each restriction the FP32 V-cycle needs at most two more
-    GMRES iterations than the FP64 one and reaches the same true residual
-    floor (the plain FP32 V-cycle needs 150 and 33 iterations here)."""
+    """2D, high degree, fine mesh (2.4 M and 0.8 M unknowns): with FP64 or
+    compensated FP32 defects before each restriction the FP32 V-cycle needs at
+    most two more GMRES iterations than the FP64 one and reaches the same true
+    residual floor (the plain FP32 V-cycle needs 150 and 33 iterations here)."""
     d = 2
     n = (k * 2 ** L - 1) ** d
     b = cuda(workload.rhs_uniform(n, k))
     res = {}
-    for pr in (bh.FP64, bh.MIXED_FP32_R64):
+    for pr in (bh.FP64, bh.MIXED_FP32_R64, bh.MIXED_FP32_RC):
         with make_ctx(bh, d, k, L, precision=pr, gmres_side=bh.RIGHT) as ctx:
             X = torch.empty(n, dtype=torch.float64, device="cuda")
             res[pr] = ctx.solve(b, X, 1e-8, 100)
     it64, rr64 = res[bh.FP64]
-    itr, rrr = res[bh.MIXED_FP32_R64]
-    assert itr <= it64 + 2, (itr, it64)
-    assert rrr <= 2.0 * max(rr64, 1e-8), (rrr, rr64)
+    for pr in (bh.MIXED_FP32_R64, bh.MIXED_FP32_RC):
+        itr, rrr = res[pr]
+        assert itr <= it64 + 2, (pr, itr, it64)
+        assert rrr <= 2.0 * max(rr64, 1e-8), (pr, rrr, rr64)
 
 
 @pytest.mark.parametrize("d,k,L,sm,ls", [(2, 2, 4, "atomic", "inexact"), (2, 3, 4, "colored", "exact"),
@@ -358,7 +406,8 @@ def test_cg_solve_matches_oracle(bh, d, k, L, sm, ls):
     assert relerr(host(X), xr) <= 1e-6
 
 
-@pytest.mark.parametrize("d,k,L,mode", [(2, 3, 4, "fp32"), (3, 2, 3, "fp32"), (2, 5, 3, "r64")])
+@pytest.mark.parametrize("d,k,L,mode", [(2, 3, 4, "fp32"), (3, 2, 3, "fp32"), (2, 5, 3, "r64"),
+                                         (2, 5, 3, "rc")])
 def test_mixed_precision_cg(bh, d, k, L, mode):
     """FP32 V-cycle inside flexible (Polak-Ribiere) FP64 CG: the same 1e-8
     reduction, at most one more iteration than FP64 CG, both within 1e-6 of
@@ -366,7 +415,7 @@ def test_mixed_precision_cg(bh, d, k, L, mode):
     n = (k * 2 ** L - 1) ** d
     b = workload.rhs_uniform(n, 31)
     exact = np.linalg.solve(oracle_A(d, k, 2 ** L).toarray(), b)
-    prec = bh.MIXED_FP32 if mode == "fp32" else bh.MIXED_FP32_R64
+    prec = mixed_mode(bh, mode)
     res = {}
     for pr in (bh.FP64, prec):
         with make_ctx(bh, d, k, L, smoother=bh.AVS_ATOMIC, pre_steps=2, post_steps=2,
@@ -380,22 +429,22 @@ def test_mixed_precision_cg(bh, d, k, L, mode):
     assert relerr(x64, exact) <= 1e-6 and relerr(x32, exact) <= 1e-6
 
 
-@pytest.mark.parametrize("mode", ["fp32", "r64"])
+@pytest.mark.parametrize("mode", ["fp32", "r64", "rc"])
 def test_mixed_precision_requires_flexible_gmres(bh, mode):
-    prec = bh.MIXED_FP32 if mode == "fp32" else bh.MIXED_FP32_R64
+    prec = mixed_mode(bh, mode)
     with pytest.raises(bh.BiharmError) as e:
         make_ctx(bh, 2, 2, 3, precision=prec, gmres_side=bh.LEFT)
     assert "flexible" in str(e.value)
 
 
-@pytest.mark.parametrize("mode", ["fp32", "r64"])
+@pytest.mark.parametrize("mode", ["fp32", "r64", "rc"])
 def test_mixed_vcycle_error_against_fp64_oracle(bh, mode):
     d, k, L = 2, 4, 4
     H = mg.Hierarchy(d, k, L)
     n = H.A[L].shape[0]
     b = workload.rhs_uniform(n, 31)
     ref = H.vcycle(L, np.zeros(n), b)
-    prec = bh.MIXED_FP32 if mode == "fp32" else bh.MIXED_FP32_R64
+    prec = mixed_mode(bh, mode)
     with make_ctx(bh, d, k, L, precision=prec, gmres_side=bh.RIGHT) as ctx:
         X = torch.zeros(n, dtype=torch.float64, device="cuda")
         ctx.vcycle(L, X, cuda(b))
