@@ -21,8 +21,9 @@ breakdown).
 value = sum of the paper's DoF counts (kN+1)^2 solved / device time (CUDA
 events), the solve inputs resident in HBM; L2 is flushed (256 MiB write)
 before every timed step.  e2e = the same through bh_batch_solve_host with
-pinned host buffers (copies inside the timed region).  The FP32 V-cycle with
-FP64 defects (the mixed form, Sec. 5.2) is timed on the same problems and
+pinned host buffers (copies inside the timed region).  The FP32 V-cycle
+(the mixed form, Sec. 5.2) with compensated FP32 defects (key `mixed`) and
+with FP64 defects (key `mixed_r64`) is timed on the same problems and
 reported beside it.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -361,7 +362,7 @@ def measure_serving(bh, torch, stream, nreq):
     (rate 200/s, seed 2024; 2D and 3D, k = 2..7, 1e4-2e7 DoFs; b = A x* with
     x* uniform[-1, 1], computed on the device before the replay), replayed at
     their arrival times: p50/p99 latency and throughput with 8 slots in the
-    mixed form (FP32 V-cycle with FP64 defects) and with 8 slots in FP64."""
+    mixed form (FP32 V-cycle with compensated FP32 defects) and with 8 slots in FP64."""
     import numpy as np
     reqs = workload.serving_requests(1000, 200.0, 2024)[:nreq]
     rhs = [None] * len(reqs)
@@ -397,7 +398,7 @@ def measure_serving(bh, torch, stream, nreq):
             st = srv.stats()
         lat = np.array([r["latency_s"] for r in res])
         svc = np.array([r["service_s"] for r in res])
-        out[name] = {"slots": 8, "precision": "FP32 V-cycle with FP64 defects" if mixed
+        out[name] = {"slots": 8, "precision": "FP32 V-cycle with compensated FP32 defects" if mixed
                      else "FP64", "value": dofs / wall, "unit": UNIT, "wall_s": wall,
                      "p50_latency_s": float(np.percentile(lat, 50)),
                      "p99_latency_s": float(np.percentile(lat, 99)),
@@ -413,8 +414,8 @@ def breakdown_3d(bh, torch, dev, stream, time_op):
     """The 3D sweep (Q2, Q3 on 128^3, Q4-Q7 on 64^3 cells): apply, one colored
     MVS step (inexact, and exact local solvers), and right-preconditioned
     MG-GMRES to a true residual of 1e-8 on b = A x*: FP64, the FP32 V-cycle of
-    Sec. 5.2 (k <= 4) and the FP32 V-cycle with FP64 defects (every k), with
-    the relative error of each solution against x*."""
+    Sec. 5.2 (k <= 4) and the FP32 V-cycle with FP64 or compensated FP32
+    defects (every k), with the relative error of each solution against x*."""
     out = {}
     for d, k, N in workload.SWEEP_3D:
         L = workload.level_of(N)
@@ -441,7 +442,8 @@ def breakdown_3d(bh, torch, dev, stream, time_op):
         with bh.Context(bh.default_params(d, k, L, local_solver=bh.EXACT), stream) as c2:
             row["mvs_exact_step"] = dofs / time_op(lambda: c2.smooth(L, x, b, 1), 2)
         for prec, name, kmax in ((bh.MIXED_FP32, "mixed_right", 4),
-                                 (bh.MIXED_FP32_R64, "mixed_r64_right", 7)):
+                                 (bh.MIXED_FP32_R64, "mixed_r64_right", 7),
+                                 (bh.MIXED_FP32_RC, "mixed_rc_right", 7)):
             if k > kmax:
                 continue
             with bh.Context(bh.default_params(d, k, L, precision=prec), stream) as c2:
@@ -711,28 +713,35 @@ def main():
     t_e2e = max_over_ranks(sum(te), dist, dev)
     bytes_h2d = sum(8 * c.num_unknowns() for c in ctxs)
 
-    # the mixed form on the same problems: FP32 V-cycle with FP64 defects
-    # (BH_MIXED_FP32_R64) inside the same flexible FP64 GMRES, same stop
-    mixed = {}
-    with bh.Batch([bh.default_params(d, k, L, precision=bh.MIXED_FP32_R64) for d, k, L in plist],
-                  stream) as mb:
-        mtiles = autotune.tune_batch(mb, plist)
-        xm = [torch.empty_like(x) for x in xs]
-        for _ in range(2):
-            its_m, rr_m = mb.solve(rhs, xm, 1e-8, 200)
-        tm = timed(lambda: mb.solve(rhs, xm, 1e-8, 200), min(args.steps, 5))
-        mixed = {"value": dofs_step * len(tm) * world / max_over_ranks(sum(tm), dist, dev),
-                 "unit": UNIT, "ms_per_step": statistics.mean(tm) * 1e3,
-                 "precision": "FP32 V-cycle with FP64 defects (BH_MIXED_FP32_R64) in flexible "
-                              "FP64 GMRES, same true-residual stop",
-                 "iterations": {str(k): {"iters": it, "true_relres": rr,
-                                         "err_vs_xstar": float((x - xt).abs().max() /
-                                                               xt.abs().max())}
-                                for (_, k, _), it, rr, x, xt in zip(problems, its_m, rr_m, xm,
-                                                                     xstar)},
-                 "tiles_patches_per_block": mtiles}
-        mixed["speedup_vs_fp64"] = mixed["value"] / value
-        del xm
+    # the mixed forms on the same problems, inside the same flexible FP64
+    # GMRES with the same stop: the FP32 V-cycle with compensated FP32 defects
+    # (BH_MIXED_FP32_RC, the `mixed` key) and with FP64 defects (R64)
+    def mixed_leg(prec, label, steps):
+        with bh.Batch([bh.default_params(d, k, L, precision=prec) for d, k, L in plist],
+                      stream) as mb:
+            mtiles = autotune.tune_batch(mb, plist)
+            xm = [torch.empty_like(x) for x in xs]
+            for _ in range(2):
+                its_m, rr_m = mb.solve(rhs, xm, 1e-8, 200)
+            tm = timed(lambda: mb.solve(rhs, xm, 1e-8, 200), steps)
+            leg = {"value": dofs_step * len(tm) * world / max_over_ranks(sum(tm), dist, dev),
+                   "unit": UNIT, "ms_per_step": statistics.mean(tm) * 1e3,
+                   "precision": label,
+                   "iterations": {str(k): {"iters": it, "true_relres": rr,
+                                           "err_vs_xstar": float((x - xt).abs().max() /
+                                                                 xt.abs().max())}
+                                  for (_, k, _), it, rr, x, xt in zip(problems, its_m, rr_m, xm,
+                                                                       xstar)},
+                   "tiles_patches_per_block": mtiles}
+            leg["speedup_vs_fp64"] = leg["value"] / value
+            del xm
+        return leg
+
+    mixed = mixed_leg(bh.MIXED_FP32_RC, "FP32 V-cycle with compensated FP32 (double-float) "
+                      "defects (BH_MIXED_FP32_RC) in flexible FP64 GMRES, same true-residual stop",
+                      min(args.steps, 5))
+    mixed_r64 = mixed_leg(bh.MIXED_FP32_R64, "FP32 V-cycle with FP64 defects (BH_MIXED_FP32_R64) "
+                          "in flexible FP64 GMRES, same true-residual stop", min(args.steps, 3))
     # the persistent form of the headline batch's V-cycle (one cooperative launch
     # per V-cycle instead of the graph replay), on the same solves
     batch.set_persistent(True)
@@ -763,6 +772,8 @@ def main():
         "all_true_relres_le_1e-8": all(rr <= 1.0001e-8 for _, rr in iters.values()),
         "tiles_patches_per_block": tiles,
         "mixed": mixed,
+        "mixed_r64": {key: mixed_r64[key] for key in ("value", "unit", "ms_per_step", "precision",
+                                                       "speedup_vs_fp64")},
         "persistent_vcycle": persistent,
     }
 
@@ -851,7 +862,8 @@ def main():
             # the FP32 V-cycle (Sec. 5.2, Q2-Q4) and the FP32 V-cycle with FP64
             # defects (every degree), both in flexible GMRES, on one context
             for prec, name, kmax in ((bh.MIXED_FP32, "mixed_right", 4),
-                                     (bh.MIXED_FP32_R64, "mixed_r64_right", 7)):
+                                     (bh.MIXED_FP32_R64, "mixed_r64_right", 7),
+                                     (bh.MIXED_FP32_RC, "mixed_rc_right", 7)):
                 if k > kmax:
                     continue
                 with bh.Context(bh.default_params(d, k, L, precision=prec), stream) as c2:

@@ -373,15 +373,16 @@ bh_status bh_batch_stats(const bh_batch* batch, long long* launches);
  * memory budget, after evicting idle hierarchies least recently used first;
  * otherwise it waits for running solves to release memory.  A request starts
  * as soon as a slot and its memory are free.  Precision: the FP32 V-cycle
- * with FP64 defects (BH_MIXED_FP32_R64) in flexible FP64 GMRES for degrees
- * <= mixed_max_degree, FP64 otherwise; right preconditioning (true residual).  A request's result does not depend on the
- * other requests in flight. */
+ * with compensated FP32 defects (BH_MIXED_FP32_RC) in flexible FP64 GMRES
+ * for degrees <= mixed_max_degree, FP64 otherwise; right preconditioning
+ * (true residual).  A request's result does not depend on the other requests
+ * in flight. */
 typedef struct bh_server bh_server;
 
 typedef struct {
   int slots;                /* concurrent solves (worker threads), 1..64 */
   double mem_budget_bytes;  /* device memory the resident hierarchies may use */
-  int mixed_max_degree;     /* FP32 V-cycle (FP64 defects) for k <= this, FP64 above
+  int mixed_max_degree;     /* FP32 V-cycle (compensated defects) for k <= this, FP64 above
                                (default 7: every degree) */
   double rtol;              /* GMRES relative tolerance (default 1e-8) */
   int maxit;                /* GMRES iteration limit (default 200) */

@@ -15,8 +15,9 @@
 //  - Continuous batching: a request starts as soon as a slot and its memory
 //    are free -- requests that arrive while others run join immediately, not
 //    at a batch boundary.
-//  - Precision: the FP32 V-cycle with FP64 defects (BH_MIXED_FP32_R64) inside
-//    flexible FP64 GMRES for degrees up to mixed_max_degree, FP64 otherwise;
+//  - Precision: the FP32 V-cycle with compensated FP32 defects
+//    (BH_MIXED_FP32_RC) inside flexible FP64 GMRES for degrees up to
+//    mixed_max_degree, FP64 otherwise;
 //    GMRES is right-preconditioned (true residual) for every request.
 //  - Latency of a request = completion time - submission time.
 #include <cuda_runtime.h>
@@ -78,8 +79,12 @@ double footprint(int d, int k, int L, int precision, int restart) {
   // every level: x, b, r (+ FP32 copies); finest: sweep scratch and two
   // transfer vectors (+ FP32); GMRES basis V (m+1), Z (m), w, t; patch lists
   double total = 0, nL = 0;
-  // FP64 x, b, r; + FP32 x, b, r (mixed); + FP64 defect and iterate copy (R64)
-  const double vb = precision == BH_FP64 ? 8.0 : (precision == BH_MIXED_FP32 ? 12.0 : 17.33);
+  // FP64 x, b, r; + FP32 x, b, r (mixed); + the FP64 right-hand side of the
+  // defect (RC), and the FP64 iterate copy (R64)
+  const double vb = precision == BH_FP64         ? 8.0
+                    : precision == BH_MIXED_FP32    ? 12.0
+                    : precision == BH_MIXED_FP32_RC ? 14.67
+                                                    : 17.33;
   for (int l = 1; l <= L; ++l) {
     const double n = std::pow((double)k * (1 << l) - 1.0, d);
     total += 3 * vb * n + 4.0 * n / std::pow(k, d);
@@ -196,7 +201,7 @@ void worker(bh_server* s) {
       s->cv_done.notify_all();
       continue;
     }
-    const int precision = (s->cfg.mixed_max_degree >= r->degree) ? BH_MIXED_FP32_R64 : BH_FP64;
+    const int precision = (s->cfg.mixed_max_degree >= r->degree) ? BH_MIXED_FP32_RC : BH_FP64;
     bh_status st = BH_OK;
     Pooled* p = acquire(s, lk, *r, precision, &st);
     if (!p) {

@@ -26,7 +26,7 @@ REQS = [(2, 2, 6), (3, 2, 3), (2, 5, 4), (2, 3, 5), (3, 3, 2), (2, 7, 3), (2, 4,
 
 
 def alone(bh, d, k, L, b):
-    p = bh.default_params(d, k, L, precision=bh.MIXED_FP32_R64, gmres_side=bh.RIGHT,
+    p = bh.default_params(d, k, L, precision=bh.MIXED_FP32_RC, gmres_side=bh.RIGHT,
                           gmres_restart=30)
     with bh.Context(p) as ctx:
         B = torch.tensor(b, dtype=torch.float64, device="cuda")
