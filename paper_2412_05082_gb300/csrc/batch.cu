@@ -21,8 +21,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "biharm.h"
@@ -165,7 +167,8 @@ struct MvsOp {
   DevArray<int> pid;
   DevArray<Tile> tiles;
   size_t smem = 0;
-  int k = 0;  // the degree of every problem of the op
+  int k = 0;                  // the degree of every problem of the op
+  const void* htab = nullptr;  // their common MvsTab<T, k> (host copy; a kernel parameter)
 };
 
 template <typename T>
@@ -533,10 +536,17 @@ bh_status build_vdepth(bh_batch* b, int t, VDepth<T>& V, Depth& D) {
   std::vector<std::pair<int, Vec<T>>> zc;
   std::vector<Symv<T>> sv;
   std::vector<int> svp;
-  // per color and degree (index k): patch-list arguments, problems, tiles
-  std::vector<std::vector<MvsArgs<T>>> margs(8 * (kMaxK + 1));
-  std::vector<std::vector<int>> mpid(8 * (kMaxK + 1));
-  std::vector<std::vector<Tile>> mtiles(8 * (kMaxK + 1));
+  // per color, degree and table class (problems of one degree whose tables
+  // agree byte for byte, i.e. of one penalty): patch-list arguments, problems,
+  // tiles
+  struct Group {
+    std::vector<MvsArgs<T>> args;
+    std::vector<int> pid;
+    std::vector<Tile> tiles;
+    const void* htab = nullptr;
+  };
+  std::map<std::tuple<int, int, int>, Group> groups;  // (color, degree, table class)
+  std::vector<const void*> reps[kMaxK + 1];           // one host table per class
   size_t smem_k[kMaxK + 1] = {0};
   for (int p = 0; p < b->P; ++p) {
     const int l = b->L[p] - t;
@@ -557,6 +567,11 @@ bh_status build_vdepth(bh_batch* b, int t, VDepth<T>& V, Depth& D) {
     const int pb = std::min(mvs_pb(b, k), mvs_pb_max_t<T>(k));
     smem_k[k] = mvs_smem<T>(k, pb);
     const DevTables dt = Ops<T>::device_tables(LvBuf<T>::tab(c), k);
+    size_t tbytes = 0;
+    const void* htab = Ops<T>::host_mvs_tables(LvBuf<T>::tab(c), k, &tbytes);
+    int cls = 0;
+    while (cls < (int)reps[k].size() && std::memcmp(reps[k][cls], htab, tbytes) != 0) ++cls;
+    if (cls == (int)reps[k].size()) reps[k].push_back(htab);
     for (int col = 0; col < 8; ++col) {
       MvsArgs<T> a{};
       a.x = LvBuf<T>::x(Lv);
@@ -569,29 +584,29 @@ bh_status build_vdepth(bh_batch* b, int t, VDepth<T>& V, Depth& D) {
       a.ascale = Lv.ascale;
       a.pscale = c->p.omega * Lv.pscale;
       a.dinv = static_cast<const T*>(dt.dinv);
-      const int g = col * (kMaxK + 1) + k;
-      const int s = (int)margs[g].size();
-      margs[g].push_back(a);
-      mpid[g].push_back(p);
-      for (int f = 0; f < a.count; f += pb) mtiles[g].push_back(Tile{s, f, std::min(pb, a.count - f)});
+      Group& G = groups[std::make_tuple(col, k, cls)];
+      G.htab = reps[k][cls];
+      const int s = (int)G.args.size();
+      G.args.push_back(a);
+      G.pid.push_back(p);
+      for (int f = 0; f < a.count; f += pb) G.tiles.push_back(Tile{s, f, std::min(pb, a.count - f)});
     }
   }
   if (!p0.empty()) {
     BCKS(make_xfer(b, p0, V.prol[0]));
     BCKS(make_xfer(b, p1, V.prol[1]));
     BCKS(make_vec(b, zc, V.zero_coarse));
-    for (int col = 0; col < 8; ++col) {
-      for (int k = 0; k <= kMaxK; ++k) {
-        const int g = col * (kMaxK + 1) + k;
-        if (mtiles[g].empty()) continue;
-        V.mvs[col].emplace_back();
-        MvsOp<T>& op = V.mvs[col].back();
-        BCKS(upload(b, margs[g], op.args));
-        BCKS(upload(b, mpid[g], op.pid));
-        BCKS(upload(b, mtiles[g], op.tiles));
-        op.smem = smem_k[k];
-        op.k = k;
-      }
+    for (auto& [key, G] : groups) {  // in (color, degree, class) order
+      if (G.tiles.empty()) continue;
+      const int col = std::get<0>(key), k = std::get<1>(key);
+      V.mvs[col].emplace_back();
+      MvsOp<T>& op = V.mvs[col].back();
+      BCKS(upload(b, G.args, op.args));
+      BCKS(upload(b, G.pid, op.pid));
+      BCKS(upload(b, G.tiles, op.tiles));
+      op.smem = smem_k[k];
+      op.k = k;
+      op.htab = G.htab;
     }
   }
   if (!sv.empty()) {
@@ -793,7 +808,7 @@ cudaError_t run_mvs(bh_batch* b, const std::vector<MvsOp<T>>& ops) {
     const int* pid = op.pid.d;
     const Tile* tiles = op.tiles.d;
     int ntiles = op.tiles.n;
-    void* params[] = {&m, &args, &pid, &tiles, &ntiles};
+    void* params[] = {&m, &args, &pid, &tiles, &ntiles, const_cast<void*>(op.htab)};
     if ((e = cudaLaunchKernel(mvs2_batch_kernel_for<T>(op.k), dim3((unsigned)ntiles), dim3(256),
                               params, op.smem, st)) != cudaSuccess)
       return e;
@@ -1016,6 +1031,11 @@ struct PhaseBuilder {
     Phase P{};
     P.kind = kPhMvs;
     for (const MvsOp<T>& op : ops) {
+      if (P.ngroups == kMaxK + 1) {  // more table classes than a phase holds: one
+        ph.push_back(P);             // more phase (its problems are independent)
+        P = Phase{};
+        P.kind = kPhMvs;
+      }
       MvsGroup& G = P.groups[P.ngroups++];
       G.args = op.args.d;
       G.pid = op.pid.d;
@@ -1136,12 +1156,17 @@ bh_status prepare(bh_batch* b) {
     else
       BCKS(raise_smem_limit<double>(k, smem));
   }
-  // one side stream and join event per degree present (created once)
-  int groups = 0;
-  for (int k = 0; k <= kMaxK; ++k)
-    groups += std::find(b->k.begin(), b->k.end(), k) != b->k.end() ? 1 : 0;
+  BCKS(build_depths(b));
+  // one side stream and join event per parallel launch of a color or a
+  // compensated sweep (a degree and table class each; created once)
+  size_t groups = 0;
+  for (const Depth& D : b->depth) {
+    for (int col = 0; col < 8; ++col)
+      groups = std::max(groups, b->mixed ? D.v32.mvs[col].size() : D.v64.mvs[col].size());
+    groups = std::max(groups, D.ff_x.size());
+  }
   if (!b->fork) BCK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
-  while ((int)b->side.size() < groups) {
+  while (b->side.size() < groups) {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     BCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -1149,7 +1174,6 @@ bh_status prepare(bh_batch* b) {
     BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     b->join.push_back(ev);
   }
-  BCKS(build_depths(b));
   TopOps top;
   BCKS(build_top(b, top));
   BCKS(capture_vcycle(b, top));

@@ -499,8 +499,14 @@ __device__ __forceinline__ void fdm_bwd_canon(const FdmTab<T, K>& fdm, const T* 
   }
 }
 
-// all patches of the tile interior: same stages as mvs2_tile
-template <typename T, int K>
+// all patches of the tile interior: same stages as mvs2_tile.  COEF_DIRECT:
+// the coefficients are read from `op` and `fdm` themselves at compile-time
+// offsets -- for tables that are kernel parameters, constant-bank operands of
+// the FMAs, with no load instruction (FP32: 32 instead of 46 registers at
+// k = 4); otherwise they are staged in shared memory first (FP64 kernels,
+// whose constant operands the compiler hoists into 104-152 registers, and
+// tables in device memory).
+template <typename T, int K, bool COEF_DIRECT = false>
 __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
                                                    const FdmTab<T, K>& fdm, const MvsArgs<T>& a,
                                                    int first, int np, unsigned char* smem_raw) {
@@ -527,19 +533,23 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
   __shared__ int sOff0[32], sDeep[32];
   const int N = a.N, n = a.n;
   // operator and eigenvector tables staged in shared memory (layout of OpTab
-  // and FdmTab), read at compile-time offsets, and the interior type's
-  // reciprocal eigenvalue sums
+  // and FdmTab), read at compile-time offsets (unless COEF_DIRECT), and the
+  // interior type's reciprocal eigenvalue sums
   constexpr int NOP = 3 * C::NC * C::BW;
   T* sDinv = reinterpret_cast<T*>(smem_raw) + NOP + 4 * MM;
   {
     T* sT = reinterpret_cast<T*>(smem_raw);
-    for (int e = threadIdx.x; e < NOP; e += blockDim.x) sT[e] = (&op.M[0][0])[e];
-    for (int e = threadIdx.x; e < 4 * MM; e += blockDim.x) sT[NOP + e] = (&fdm.S[0][0][0])[e];
+    if constexpr (!COEF_DIRECT) {
+      for (int e = threadIdx.x; e < NOP; e += blockDim.x) sT[e] = (&op.M[0][0])[e];
+      for (int e = threadIdx.x; e < 4 * MM; e += blockDim.x) sT[NOP + e] = (&fdm.S[0][0][0])[e];
+    }
     for (int e = threadIdx.x; e < MM; e += blockDim.x) sDinv[e] = a.dinv[e];  // combination 0
   }
-  const OpTab<T, K>& op_s = *reinterpret_cast<const OpTab<T, K>*>(smem_raw);
+  const OpTab<T, K>& op_s =
+      COEF_DIRECT ? op : *reinterpret_cast<const OpTab<T, K>*>(smem_raw);
   const FdmTab<T, K>& fdm_s =
-      *reinterpret_cast<const FdmTab<T, K>*>(smem_raw + sizeof(T) * 3 * C::NC * C::BW);
+      COEF_DIRECT ? fdm
+                  : *reinterpret_cast<const FdmTab<T, K>*>(smem_raw + sizeof(T) * 3 * C::NC * C::BW);
   // offset in values of a.x from a 16-byte boundary
   const int xo = C::VECWIN ? (int)((reinterpret_cast<uintptr_t>(a.x) / sizeof(T)) & 3) : 0;
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
@@ -720,7 +730,7 @@ __global__ void __launch_bounds__(256) mvs2_color_kernel(const __grid_constant__
   const int np = min(a.pb, a.count - first);
   if (np <= 0) return;
   if (mvs2_tile_is_interior(a, first, np))
-    mvs2_tile_interior<T, K>(tab.op, tab.fdm, a, first, np, smem_raw);
+    mvs2_tile_interior<T, K, sizeof(T) == 4>(tab.op, tab.fdm, a, first, np, smem_raw);
   else
     mvs2_tile<T, K>(tab.op, tab.fdm, a, first, np, smem_raw);
 }

@@ -169,6 +169,26 @@ DevTables Ops<T>::device_tables(const void* p, int k) {
   return DevTables{nullptr, nullptr};
 }
 
+template <typename T, int K>
+static const void* host_mvs_tables_k(const void* p, size_t* bytes) {
+  *bytes = sizeof(MvsTab<T, K>);
+  return &static_cast<const HostTables<T, K>*>(p)->mvs;
+}
+
+template <typename T>
+const void* Ops<T>::host_mvs_tables(const void* p, int k, size_t* bytes) {
+  switch (k) {
+    case 2: return host_mvs_tables_k<T, 2>(p, bytes);
+    case 3: return host_mvs_tables_k<T, 3>(p, bytes);
+    case 4: return host_mvs_tables_k<T, 4>(p, bytes);
+    case 5: return host_mvs_tables_k<T, 5>(p, bytes);
+    case 6: return host_mvs_tables_k<T, 6>(p, bytes);
+    case 7: return host_mvs_tables_k<T, 7>(p, bytes);
+  }
+  *bytes = 0;
+  return nullptr;
+}
+
 template <typename T>
 void Ops<T>::free_tables(void* p, int k) {
   if (!p) return;

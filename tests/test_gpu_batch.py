@@ -73,6 +73,33 @@ def test_batched_vcycle_matches_oracle_per_problem(bh):
             assert relerr(host(x), ref) <= 1e-10, (k, L, relerr(host(x), ref))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "rc"])
+def test_batched_vcycle_with_two_penalties_of_one_degree(bh, precision):
+    """Problems of one degree with different penalties gamma have different
+    tables, which the per-degree patch launches take as a kernel parameter:
+    the batch splits them into one launch per table class, and each problem's
+    V-cycle equals the oracle's Algorithm 1 with its own gamma (1e-10 in FP64;
+    the FP32 V-cycle's 1e-3 bound otherwise)."""
+    probs = [(2, 3, 3, None), (2, 3, 3, 20.0), (2, 3, 4, 6.0), (2, 5, 2, None)]
+    Hs = [mg.Hierarchy(d, k, L, gamma=g) for d, k, L, g in probs]
+    bs = [workload.rhs_uniform(H.A[H.L].shape[0], 800 + i) for i, H in enumerate(Hs)]
+    prec = bh.FP64 if precision == "fp64" else bh.MIXED_FP32_RC
+    params = []
+    for d, k, L, g in probs:
+        kw = {"precision": prec}
+        if g is not None:
+            kw["gamma"] = g
+        params.append(bh.default_params(d, k, L, **kw))
+    with bh.Batch(params) as batch:
+        B = [cuda(b) for b in bs]
+        X = [torch.empty_like(v) for v in B]
+        batch.vcycle(B, X)
+        for (d, k, L, g), H, b, x in zip(probs, Hs, bs, X):
+            ref = H.vcycle(H.L, np.zeros_like(b), b)
+            tol = 1e-10 if precision == "fp64" else 1e-3
+            assert relerr(host(x), ref) <= tol, (k, L, g, relerr(host(x), ref))
+
+
 @pytest.mark.parametrize("side", ["right", "left"])
 def test_batched_solve_matches_oracle_gmres(bh, side):
     Hs = hierarchies()
