@@ -99,12 +99,19 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
   if (np <= 0) return;
   const int N = a.N, n = a.n;
   const int64_t n2 = (int64_t)n * n;
-  for (int e = threadIdx.x; e < NC * BW; e += blockDim.x) {
-    sM[e] = (&op.M[0][0])[e];
-    sL[e] = (&op.L[0][0])[e];
-    sB[e] = (&op.B[0][0])[e];
+  constexpr bool DIRECT = INTERIOR && sizeof(T) == 4;
+  if constexpr (!DIRECT) {
+    for (int e = threadIdx.x; e < NC * BW; e += blockDim.x) {
+      sM[e] = (&op.M[0][0])[e];
+      sL[e] = (&op.L[0][0])[e];
+      sB[e] = (&op.B[0][0])[e];
+    }
+    for (int e = threadIdx.x; e < 4 * MM; e += blockDim.x) sS[e] = (&fdm.S[0][0][0])[e];
   }
-  for (int e = threadIdx.x; e < 4 * MM; e += blockDim.x) sS[e] = (&fdm.S[0][0][0])[e];
+  const T* tM = DIRECT ? &op.M[0][0] : sM;
+  const T* tL = DIRECT ? &op.L[0][0] : sL;
+  const T* tB = DIRECT ? &op.B[0][0] : sB;
+  const T* tS = DIRECT ? &fdm.S[0][0][0] : sS;
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
     int vid = a.verts[first + p];
     int combo = 0, mul = 1;
@@ -148,9 +155,9 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
     T* tm = regA + p * C::RA + row * M;
     const bool canon = INTERIOR || sTy[p][0] == 0;
     if (half == 0)
-      line_half<T, K, 0, 0, 0, false>(sM, canon, gx0, N, w, 1, tm, 1, one);
+      line_half<T, K, 0, 0, 0, false>(tM, canon, gx0, N, w, 1, tm, 1, one);
     else
-      line_half<T, K, 1, 0, 0, false>(sM, canon, gx0, N, w, 1, tm, 1, one);
+      line_half<T, K, 1, 0, 0, false>(tM, canon, gx0, N, w, 1, tm, 1, one);
   }
   for (int e = threadIdx.x; e < 2 * np * WM * WM; e += blockDim.x) {
     const int q_ = e / (WM * WM), r = e - q_ * (WM * WM);  // item (half, patch, r)
@@ -170,11 +177,11 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
     T* tb = tl + C::TLB;
     const bool canon = INTERIOR || sTy[p][0] == 0;
     if (half == 0) {
-      line_half<T, K, 0, 1, K, false>(sL, canon, gx0, N, w, 1, tl, 1, one);
-      line_half<T, K, 0, 2, K, false>(sB, canon, gx0, N, w, 1, tb, 1, one);
+      line_half<T, K, 0, 1, K, false>(tL, canon, gx0, N, w, 1, tl, 1, one);
+      line_half<T, K, 0, 2, K, false>(tB, canon, gx0, N, w, 1, tb, 1, one);
     } else {
-      line_half<T, K, 1, 1, K, false>(sL, canon, gx0, N, w, 1, tl, 1, one);
-      line_half<T, K, 1, 2, K, false>(sB, canon, gx0, N, w, 1, tb, 1, one);
+      line_half<T, K, 1, 1, K, false>(tL, canon, gx0, N, w, 1, tl, 1, one);
+      line_half<T, K, 1, 2, K, false>(tB, canon, gx0, N, w, 1, tb, 1, one);
     }
   }
   __syncthreads();
@@ -194,9 +201,9 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
     const bool canon = INTERIOR || sTy[p][1] == 0;
     const int gy0 = K * (sV[p][1] - 1);
     if (half == 0)
-      line_half<T, K, 0, 0, 0, false>(sM, canon, gy0, N, col, 1, ub, M, one);
+      line_half<T, K, 0, 0, 0, false>(tM, canon, gy0, N, col, 1, ub, M, one);
     else
-      line_half<T, K, 1, 0, 0, false>(sM, canon, gy0, N, col, 1, ub, M, one);
+      line_half<T, K, 1, 0, 0, false>(tM, canon, gy0, N, col, 1, ub, M, one);
   }
   // U_M and U_L on the middle z
   for (int e = threadIdx.x; e < 2 * np * WM * M; e += blockDim.x) {
@@ -218,17 +225,17 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
     const int gy0 = K * (sV[p][1] - 1);
     const T two = T(2);
     if (half == 0) {
-      line_half<T, K, 0, 0, 0, false>(sM, canon, gy0, N, cb, 1, um, M, one);
-      line_half<T, K, 0, 2, K, true>(sB, canon, gy0, N, cm, 1, um, M, one);
-      line_half<T, K, 0, 1, 0, true>(sL, canon, gy0, N, cl, 1, um, M, two);
-      line_half<T, K, 0, 1, K, false>(sL, canon, gy0, N, cm, 1, ul, M, two);
-      line_half<T, K, 0, 0, 0, true>(sM, canon, gy0, N, cl, 1, ul, M, two);
+      line_half<T, K, 0, 0, 0, false>(tM, canon, gy0, N, cb, 1, um, M, one);
+      line_half<T, K, 0, 2, K, true>(tB, canon, gy0, N, cm, 1, um, M, one);
+      line_half<T, K, 0, 1, 0, true>(tL, canon, gy0, N, cl, 1, um, M, two);
+      line_half<T, K, 0, 1, K, false>(tL, canon, gy0, N, cm, 1, ul, M, two);
+      line_half<T, K, 0, 0, 0, true>(tM, canon, gy0, N, cl, 1, ul, M, two);
     } else {
-      line_half<T, K, 1, 0, 0, false>(sM, canon, gy0, N, cb, 1, um, M, one);
-      line_half<T, K, 1, 2, K, true>(sB, canon, gy0, N, cm, 1, um, M, one);
-      line_half<T, K, 1, 1, 0, true>(sL, canon, gy0, N, cl, 1, um, M, two);
-      line_half<T, K, 1, 1, K, false>(sL, canon, gy0, N, cm, 1, ul, M, two);
-      line_half<T, K, 1, 0, 0, true>(sM, canon, gy0, N, cl, 1, ul, M, two);
+      line_half<T, K, 1, 0, 0, false>(tM, canon, gy0, N, cb, 1, um, M, one);
+      line_half<T, K, 1, 2, K, true>(tB, canon, gy0, N, cm, 1, um, M, one);
+      line_half<T, K, 1, 1, 0, true>(tL, canon, gy0, N, cl, 1, um, M, two);
+      line_half<T, K, 1, 1, K, false>(tL, canon, gy0, N, cm, 1, ul, M, two);
+      line_half<T, K, 1, 0, 0, true>(tM, canon, gy0, N, cl, 1, ul, M, two);
     }
   }
   __syncthreads();
@@ -250,13 +257,13 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
     const bool canon = INTERIOR || sTy[p][2] == 0;
     const int gz0 = K * (sV[p][2] - 1);
     if (half == 0) {
-      line_half<T, K, 0, 0, 0, false>(sM, canon, gz0, N, cum, 1, R, MM, one);
-      line_half<T, K, 0, 2, K, true>(sB, canon, gz0, N, cub, 1, R, MM, one);
-      line_half<T, K, 0, 1, 0, true>(sL, canon, gz0, N, cul, 1, R, MM, one);
+      line_half<T, K, 0, 0, 0, false>(tM, canon, gz0, N, cum, 1, R, MM, one);
+      line_half<T, K, 0, 2, K, true>(tB, canon, gz0, N, cub, 1, R, MM, one);
+      line_half<T, K, 0, 1, 0, true>(tL, canon, gz0, N, cul, 1, R, MM, one);
     } else {
-      line_half<T, K, 1, 0, 0, false>(sM, canon, gz0, N, cum, 1, R, MM, one);
-      line_half<T, K, 1, 2, K, true>(sB, canon, gz0, N, cub, 1, R, MM, one);
-      line_half<T, K, 1, 1, 0, true>(sL, canon, gz0, N, cul, 1, R, MM, one);
+      line_half<T, K, 1, 0, 0, false>(tM, canon, gz0, N, cum, 1, R, MM, one);
+      line_half<T, K, 1, 2, K, true>(tB, canon, gz0, N, cub, 1, R, MM, one);
+      line_half<T, K, 1, 1, 0, true>(tL, canon, gz0, N, cul, 1, R, MM, one);
     }
     // r = b - ascale * (A x) on this column's patch nodes of the half
     const int i = r / M, j = r % M;
@@ -286,7 +293,7 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
       for (int e = threadIdx.x; e < np * M3; e += blockDim.x) {
         const int p = e / M3, l = e % M3;
         const int c_ax = (l / st) % M, l0 = l - c_ax * st;
-        const T* S = sS + sTy[p][ax] * MM;
+        const T* S = tS + sTy[p][ax] * MM;
         const T* src = in + p * istride + l0;
         T s = T(0);
 #pragma unroll
@@ -319,7 +326,7 @@ __device__ __forceinline__ void mvs3_tile(const OpTab<T, K>& op, const FdmTab<T,
         // first element of line q (the two other coordinates) in [z][y][x] order
         const int l0 = ax == 0 ? q * M : (ax == 1 ? (q / M) * MM + q % M : q);
         const int t = INTERIOR ? 0 : sTy[p][ax];
-        const T* S = sS + t * MM;
+        const T* S = tS + t * MM;
         const T* src = in + p * istride + l0;
         T* dst = outp + p * ostride + l0;
         if (stage == 2) {
