@@ -40,9 +40,13 @@ struct Mvs3Cfg {
   static constexpr int BUDGET = 220 * 1024;
   static constexpr int FIT = (BUDGET / (int)sizeof(T) - TABLES) / PER;
   static constexpr int PB_MAX = FIT < 1 ? 1 : (FIT > 16 ? 16 : FIT);
-  // threads per block: FP32 at high degree holds one to three patches of large
-  // intermediates per SM, so the block brings more threads to each stage
-  static constexpr int THREADS = (sizeof(T) == 4 && K >= 6) ? 512 : 256;
+  // threads per block: one block per SM holds the large intermediates of a
+  // few patches (FP32 at k >= 6, FP64 at k = 3..5), so the block brings more
+  // threads to each stage: FP64 MVS steps 4-9 % faster at k = 3..5 (measured
+  // on the 3D sweep); at k = 6 and 7 the 128 registers that 512 threads leave
+  // are too few (spills, 2 % slower at k = 6)
+  static constexpr int THREADS =
+      ((sizeof(T) == 4 && K >= 6) || (sizeof(T) == 8 && K >= 3 && K <= 5)) ? 512 : 256;
   static size_t smem_bytes(int pb) { return sizeof(T) * (size_t)(TABLES + pb * PER) + 64; }
 };
 
