@@ -168,7 +168,8 @@ struct MvsOp {
   DevArray<Tile> tiles;
   size_t smem = 0;
   int k = 0;                  // the degree of every problem of the op
-  const void* htab = nullptr;  // their common MvsTab<T, k> (host copy; a kernel parameter)
+  const void* htab = nullptr;  // FP32: their common CanonTab<float, k> (host copy; the kernel
+                               // parameter); FP64: a placeholder for the unused parameter
 };
 
 template <typename T>
@@ -567,10 +568,15 @@ bh_status build_vdepth(bh_batch* b, int t, VDepth<T>& V, Depth& D) {
     const int pb = std::min(mvs_pb(b, k), mvs_pb_max_t<T>(k));
     smem_k[k] = mvs_smem<T>(k, pb);
     const DevTables dt = Ops<T>::device_tables(LvBuf<T>::tab(c), k);
+    // FP32: one launch per class of problems whose interior tables agree byte
+    // for byte (one penalty), the tables being the launch's parameter
+    static const int kNoTable = 0;
     size_t tbytes = 0;
-    const void* htab = Ops<T>::host_mvs_tables(LvBuf<T>::tab(c), k, &tbytes);
+    const void* htab = &kNoTable;
+    if (sizeof(T) == 4) htab = Ops<T>::host_mvs_tables(LvBuf<T>::tab(c), k, &tbytes);
     int cls = 0;
-    while (cls < (int)reps[k].size() && std::memcmp(reps[k][cls], htab, tbytes) != 0) ++cls;
+    while (cls < (int)reps[k].size() && tbytes && std::memcmp(reps[k][cls], htab, tbytes) != 0)
+      ++cls;
     if (cls == (int)reps[k].size()) reps[k].push_back(htab);
     for (int col = 0; col < 8; ++col) {
       MvsArgs<T> a{};

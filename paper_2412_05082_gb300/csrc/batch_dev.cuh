@@ -79,27 +79,42 @@ struct Tile {
 // The per-degree kernels of the graph form take it for every degree.
 constexpr int kBatchInteriorMaxK = 4;
 
+// The FP32 launches' kernel parameter: the interior tiles' tables, read as
+// constant-bank operands (FP64 reads every table from device memory through
+// shared memory, and takes no parameter table).
+template <typename T, int K>
+struct BatchCoef {
+  CanonTab<T, K> c;
+};
+template <int K>
+struct BatchCoef<double, K> {
+  int unused;
+};
+
 // One color of the colored MVS for the tiles of one degree K: one block per
 // tile (any grid size).  One instantiation per degree, so that each has the
-// register count of its own tile code.  Every problem of a launch has the same
-// tables (one degree and penalty), passed as a kernel parameter, so that the
-// FP32 interior path reads its coefficients as constant-bank operands.
+// register count of its own tile code.  In FP32 every problem of a launch has
+// the same interior tables (one degree and penalty), passed as the parameter.
 template <typename T, int K>
 __global__ void __launch_bounds__(256) mvs2_batch_kernel(Meta m, const MvsArgs<T>* args,
                                                          const int* pid, const Tile* tiles,
                                                          int ntiles,
-                                                         const __grid_constant__ MvsTab<T, K> tab) {
+                                                         const __grid_constant__ BatchCoef<T, K> bc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     __syncthreads();  // the previous tile's last stage still reads shared memory
     const Tile tl = tiles[t];
     const int p = pid[tl.s];
     if (!m.active[p]) continue;
-    if (mvs2_tile_is_interior(args[tl.s], tl.first, tl.count))
-      mvs2_tile_interior<T, K, sizeof(T) == 4>(tab.op, tab.fdm, args[tl.s], tl.first, tl.count,
-                                               smem_raw);
-    else
-      mvs2_tile<T, K>(tab.op, tab.fdm, args[tl.s], tl.first, tl.count, smem_raw);
+    const auto* tb = static_cast<const Tables<T, K>*>(m.tabs[p]);
+    if (mvs2_tile_is_interior(args[tl.s], tl.first, tl.count)) {
+      if constexpr (sizeof(T) == 4)
+        mvs2_tile_interior<T, K, true>(bc.c, bc.c, args[tl.s], tl.first, tl.count, smem_raw);
+      else
+        mvs2_tile_interior<T, K>(tb->op, tb->fdm, args[tl.s], tl.first, tl.count, smem_raw);
+    } else {
+      mvs2_tile<T, K>(tb->op, tb->fdm, args[tl.s], tl.first, tl.count, smem_raw);
+    }
   }
 }
 

@@ -31,6 +31,26 @@ struct MvsTab {
   FdmTab<T, K> fdm;
 };
 
+// The interior (canonical) row classes 0..K-1 of M, L, B and the interior
+// patch type's eigenvectors: all that the interior tiles of the fused kernel
+// read (a small kernel parameter for the batched form's FP32 launches).
+template <typename T, int K>
+struct CanonTab {
+  T M[K][4 * K + 1];
+  T L[K][4 * K + 1];
+  T B[K][4 * K + 1];
+  T S[1][2 * K - 1][2 * K - 1];
+};
+
+// the first table when DIRECT, else the second (of another type)
+template <bool DIRECT, typename A, typename B>
+__device__ __forceinline__ const auto& pick_tab(const A& a, const B& b) {
+  if constexpr (DIRECT)
+    return a;
+  else
+    return b;
+}
+
 template <typename T>
 struct MvsArgs {
   T* x;
@@ -340,8 +360,8 @@ __device__ __forceinline__ void mvs2_tile(const OpTab<T, K>& op, const FdmTab<T,
 // T_M along a window row: o[j - 1] = (M x)(j) for the half's positions j.  The
 // window values live in registers, so each output is stored as soon as it is
 // formed.
-template <typename T, int K, int HALF>
-__device__ __forceinline__ void xsplit_m_canon(const OpTab<T, K>& op, const T* xr, T* o) {
+template <typename T, int K, int HALF, typename OpT>
+__device__ __forceinline__ void xsplit_m_canon(const OpT& op, const T* xr, T* o) {
   constexpr int J0 = Half<K, HALF>::J0, J1 = Half<K, HALF>::J1;
   constexpr int A = HALF == 0 ? 0 : K, Z = 2 * K;  // nodes read: xr[A .. Z]
   T w[Z - A + 1];
@@ -359,8 +379,8 @@ __device__ __forceinline__ void xsplit_m_canon(const OpTab<T, K>& op, const T* x
 }
 
 // T_L and T_B along a middle window row
-template <typename T, int K, int HALF>
-__device__ __forceinline__ void xsplit_lb_canon(const OpTab<T, K>& op, const T* xr, T* ol,
+template <typename T, int K, int HALF, typename OpT>
+__device__ __forceinline__ void xsplit_lb_canon(const OpT& op, const T* xr, T* ol,
                                                 T* ob) {
   constexpr int J0 = Half<K, HALF>::J0, J1 = Half<K, HALF>::J1;
   constexpr int A = HALF == 0 ? -K : 0, Z = 3 * K;  // nodes read: xr[A .. Z]
@@ -384,8 +404,8 @@ __device__ __forceinline__ void xsplit_lb_canon(const OpTab<T, K>& op, const T* 
 
 // residual on a half-column: r_i = b_i - ascale (B T_M + 2 L T_L + M T_B)_i
 // (pointers as in ycombine_half), accumulated operator by operator
-template <typename T, int K, int HALF>
-__device__ __forceinline__ void ycombine_canon(const OpTab<T, K>& op, const T* cm, const T* cl,
+template <typename T, int K, int HALF, typename OpT>
+__device__ __forceinline__ void ycombine_canon(const OpT& op, const T* cm, const T* cl,
                                                const T* cb, const T* bcol, int64_t n, T asc,
                                                T* rcol) {
   constexpr int M = 2 * K - 1;
@@ -442,8 +462,8 @@ __device__ __forceinline__ void ycombine_canon(const OpTab<T, K>& op, const T* c
 // Folded FDM line of the interior type: forward (S^T v)_c for the half's
 // eigenvectors c (half 0: the K even ones, half 1: the K-1 odd ones);
 // put(c, value) receives each output.
-template <typename T, int K, int HALF, typename Put>
-__device__ __forceinline__ void fdm_fwd_canon(const FdmTab<T, K>& fdm, const T* src, int is,
+template <typename T, int K, int HALF, typename Put, typename FdmT>
+__device__ __forceinline__ void fdm_fwd_canon(const FdmT& fdm, const T* src, int is,
                                               Put put) {
   constexpr int M = 2 * K - 1;
   if (HALF == 0) {
@@ -474,8 +494,8 @@ __device__ __forceinline__ void fdm_fwd_canon(const FdmTab<T, K>& fdm, const T* 
 
 // backward (S g)_i for the half's position pairs (i, M-1-i): half 0 takes
 // i < K/2, half 1 the rest (with the middle position K-1)
-template <typename T, int K, int HALF, typename Put>
-__device__ __forceinline__ void fdm_bwd_canon(const FdmTab<T, K>& fdm, const T* src, int is,
+template <typename T, int K, int HALF, typename Put, typename FdmT>
+__device__ __forceinline__ void fdm_bwd_canon(const FdmT& fdm, const T* src, int is,
                                               Put put) {
   constexpr int M = 2 * K - 1;
   constexpr int I0 = HALF == 0 ? 0 : K / 2, I1 = HALF == 0 ? K / 2 : K;
@@ -506,10 +526,11 @@ __device__ __forceinline__ void fdm_bwd_canon(const FdmTab<T, K>& fdm, const T* 
 // k = 4); otherwise they are staged in shared memory first (FP64 kernels,
 // whose constant operands the compiler hoists into 104-152 registers, and
 // tables in device memory).
-template <typename T, int K, bool COEF_DIRECT = false>
-__device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
-                                                   const FdmTab<T, K>& fdm, const MvsArgs<T>& a,
-                                                   int first, int np, unsigned char* smem_raw) {
+template <typename T, int K, bool COEF_DIRECT = false, typename OpT = OpTab<T, K>,
+          typename FdmT = FdmTab<T, K>>
+__device__ __forceinline__ void mvs2_tile_interior(const OpT& op, const FdmT& fdm,
+                                                   const MvsArgs<T>& a, int first, int np,
+                                                   unsigned char* smem_raw) {
   using C = Mvs2Cfg<T, K>;
   constexpr int M = C::M, W = C::W, WM = C::WM, MM = M * M;
   constexpr int WS = C::WS;
@@ -545,11 +566,9 @@ __device__ __forceinline__ void mvs2_tile_interior(const OpTab<T, K>& op,
     }
     for (int e = threadIdx.x; e < MM; e += blockDim.x) sDinv[e] = a.dinv[e];  // combination 0
   }
-  const OpTab<T, K>& op_s =
-      COEF_DIRECT ? op : *reinterpret_cast<const OpTab<T, K>*>(smem_raw);
-  const FdmTab<T, K>& fdm_s =
-      COEF_DIRECT ? fdm
-                  : *reinterpret_cast<const FdmTab<T, K>*>(smem_raw + sizeof(T) * 3 * C::NC * C::BW);
+  const auto& op_s = pick_tab<COEF_DIRECT>(op, *reinterpret_cast<const OpTab<T, K>*>(smem_raw));
+  const auto& fdm_s = pick_tab<COEF_DIRECT>(
+      fdm, *reinterpret_cast<const FdmTab<T, K>*>(smem_raw + sizeof(T) * 3 * C::NC * C::BW));
   // offset in values of a.x from a 16-byte boundary
   const int xo = C::VECWIN ? (int)((reinterpret_cast<uintptr_t>(a.x) / sizeof(T)) & 3) : 0;
   for (int p = threadIdx.x; p < np; p += blockDim.x) {

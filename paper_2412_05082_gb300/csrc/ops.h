@@ -39,7 +39,8 @@ struct Ops {
   static void* make_tables(const Setup1D& s, int d);
   static void free_tables(void* tab, int k);
   static DevTables device_tables(const void* tab, int k);
-  // host copy of the fused MVS kernel's parameter tables (MvsTab<T, k>) and its size
+  // host copy of the interior tiles' tables of the fused MVS kernel
+  // (CanonTab<T, k>) and its size
   static const void* host_mvs_tables(const void* tab, int k, size_t* bytes);
 
   // mode kStore: y = scale * A_ref x; mode kResidual: y = b - scale * A_ref x.

@@ -17,6 +17,7 @@ template <typename T, int K>
 struct HostTables {
   Tables<T, K> t;
   MvsTab<T, K> mvs;  // operator + FDM tables for the fused MVS kernel
+  CanonTab<T, K> canon;  // the interior tiles' part of mvs (batched FP32 kernel parameter)
   Tables<T, K>* dev = nullptr;  // device copy of t (batched kernels read it from memory)
   T* dinv = nullptr;  // device, 4^d slots x m^d reciprocals of the eigenvalue sums
   // FP32 tables only: the operator's class tables as hi + lo FP32 parts for the
@@ -47,6 +48,14 @@ static void* make_tables_k(const Setup1D& s, int d) {
     for (int q = 0; q <= K; ++q) h->t.xfer.P[r][q] = (T)s.prolong[r * (K + 1) + q];
   h->mvs.op = h->t.op;
   h->mvs.fdm = h->t.fdm;
+  for (int q = 0; q < K; ++q)
+    for (int t = 0; t < bw; ++t) {
+      h->canon.M[q][t] = h->t.op.M[q][t];
+      h->canon.L[q][t] = h->t.op.L[q][t];
+      h->canon.B[q][t] = h->t.op.B[q][t];
+    }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) h->canon.S[0][i][j] = h->t.fdm.S[0][i][j];
   // reciprocal eigenvalue sums per type combination (FP64, then converted)
   int md = 1, slots = 1;
   for (int a = 0; a < d; ++a) {
@@ -171,8 +180,8 @@ DevTables Ops<T>::device_tables(const void* p, int k) {
 
 template <typename T, int K>
 static const void* host_mvs_tables_k(const void* p, size_t* bytes) {
-  *bytes = sizeof(MvsTab<T, K>);
-  return &static_cast<const HostTables<T, K>*>(p)->mvs;
+  *bytes = sizeof(CanonTab<T, K>);
+  return &static_cast<const HostTables<T, K>*>(p)->canon;
 }
 
 template <typename T>
