@@ -40,13 +40,16 @@ struct Mvs3Cfg {
   static constexpr int BUDGET = 220 * 1024;
   static constexpr int FIT = (BUDGET / (int)sizeof(T) - TABLES) / PER;
   static constexpr int PB_MAX = FIT < 1 ? 1 : (FIT > 16 ? 16 : FIT);
-  // threads per block: one block per SM holds the large intermediates of a
-  // few patches (FP32 at k >= 6, FP64 at k = 3..5), so the block brings more
-  // threads to each stage: FP64 MVS steps 4-9 % faster at k = 3..5 (measured
-  // on the 3D sweep); at k = 6 and 7 the 128 registers that 512 threads leave
-  // are too few (spills, 2 % slower at k = 6)
+  // threads per block: where one or two blocks per SM hold the large
+  // intermediates of a few patches, the block brings more threads to each
+  // stage.  Measured on the 3D sweep: FP64 MVS steps 4-9 % faster at
+  // k = 3..5 (at k = 6 and 7 the 128 registers that 512 threads leave are too
+  // few: spills, 2 % slower at k = 6); FP32 V-cycles 6 % and 17 % faster at
+  // k = 3 and 4, 10 % slower at k = 5 (spills)
   static constexpr int THREADS =
-      ((sizeof(T) == 4 && K >= 6) || (sizeof(T) == 8 && K >= 3 && K <= 5)) ? 512 : 256;
+      ((sizeof(T) == 4 && (K == 3 || K == 4 || K >= 6)) || (sizeof(T) == 8 && K >= 3 && K <= 5))
+          ? 512
+          : 256;
   static size_t smem_bytes(int pb) { return sizeof(T) * (size_t)(TABLES + pb * PER) + 64; }
 };
 
