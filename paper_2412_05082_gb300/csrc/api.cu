@@ -246,8 +246,8 @@ bh_status restrict_defect64(bh_ctx* c, int l, const float* x, bool x_zero) {
     }
     r = L.r64;
   }
-  CK(Ops<double>::restrict_(c->tab64, L.g, r, Lc.db64, c->xs64[0], c->xs64[1], c->st));
-  CK(vec_d2f(Lc.b32, Lc.db64, Lc.g.nd, c->st));
+  // the FP32 right-hand side of level l-1 written by the restriction's last pass
+  CK(Ops<double>::restrict_(c->tab64, L.g, r, Lc.db64, c->xs64[0], c->xs64[1], c->st, Lc.b32));
   return BH_OK;
 }
 

@@ -212,7 +212,6 @@ struct Depth {  // operations at depth t of the lockstep V-cycle
   // RC: the defect of x32 in compensated FP32, a launch per degree (replaces
   // res_x, res_y and x_f2d)
   std::vector<FfOp> ff_x, ff_y;
-  ConvOpList b_d2f;         // R64: b32 = db64 on level l-1
   DevArray<int> symv_pid;
   int nsymv = 0, maxn_symv = 0;
 };
@@ -632,7 +631,7 @@ bh_status build_depths(bh_batch* b) {
     Depth& D = b->depth[t];
     std::vector<std::pair<int, SweepArgs<double>>> rx, ry;
     std::vector<std::pair<int, XferArgs<double>>> r0, r1;
-    std::vector<std::pair<int, Conv>> xf, bd;
+    std::vector<std::pair<int, Conv>> xf;
     std::vector<std::pair<int, FfSweepArgs>> fx[kMaxK + 1], fy[kMaxK + 1];
     for (int p = 0; p < P; ++p) {
       const int l = b->L[p] - t;
@@ -664,11 +663,14 @@ bh_status build_depths(bh_batch* b) {
         ry.push_back({p, sweep_args<double>(Lv, 1, s0, s1, s2, Lv.r64, nullptr, nullptr, bin, kResidual)});
       }
       r0.push_back({p, xfer_args<double, false>(0, Lv.g, Lv.r64, c->xs64[0], false)});
-      r1.push_back({p, xfer_args<double, false>(1, Lv.g, c->xs64[0], bc, false)});
+      XferArgs<double> a1 = xfer_args<double, false>(1, Lv.g, c->xs64[0], bc, false);
       if (b->mixed) {
+        // the FP32 right-hand side of level l-1, written by the restriction's
+        // last pass
+        a1.out32 = Lc.b32;
         if (!b->rc) xf.push_back({p, Conv{Lv.dx64, Lv.x32, Lv.g.nd, 0}});
-        bd.push_back({p, Conv{Lc.db64, Lc.b32, Lc.g.nd, 0}});
       }
+      r1.push_back({p, a1});
     }
     if (D.smooth) {
       BCKS(make_sweep(b, rx, D.res_x));
@@ -685,7 +687,6 @@ bh_status build_depths(bh_batch* b) {
       BCKS(make_xfer(b, r1, D.restr[1]));
       if (b->mixed) {
         BCKS(make_conv(b, xf, D.x_f2d));
-        BCKS(make_conv(b, bd, D.b_d2f));
       }
     }
     if (b->mixed)
@@ -869,7 +870,6 @@ cudaError_t vcycle_from(bh_batch* b, int t) {
   }
   if ((e = run_xfer<double>(b, D.restr[0], false)) != cudaSuccess) return e;
   if ((e = run_xfer<double>(b, D.restr[1], false)) != cudaSuccess) return e;
-  if (b->mixed && (e = run_conv(b, D.b_d2f, kD2F)) != cudaSuccess) return e;
   if ((e = run_vec<T>(b, V.zero_coarse, kZero, nullptr, 0, 0, 0.0)) != cudaSuccess) return e;
   if ((e = vcycle_from<T>(b, t + 1)) != cudaSuccess) return e;
   if ((e = run_xfer<T>(b, V.prol[0], true)) != cudaSuccess) return e;
@@ -1089,7 +1089,6 @@ bh_status build_phases(bh_batch* b, const TopOps& top) {
     B.sweep(D.res_y, kPhSweep2);
     B.xfer(D.restr[0], kPhRestr);
     B.xfer(D.restr[1], kPhRestr);
-    if (b->mixed) B.conv(D.b_d2f, kD2F);
     B.zero(V.zero_coarse);
   }
   for (int t = T_ - 1; t >= 0; --t) {

@@ -517,6 +517,7 @@ struct XferArgs {
   int Nc;       // coarse cells per direction
   int nc, nf;   // interior nodes per direction: coarse, fine
   bool add;     // out += (prolongation into x) instead of out =
+  float* out32;  // restriction: the result also rounded to FP32 here (nullptr: not)
 };
 
 // prolongation along an axis: thread <-> (line, coarse cell C); fine nodes
@@ -596,6 +597,7 @@ __device__ __forceinline__ void restrict_thread(const XferTab<T, K>& tab, const 
 #pragma unroll
     for (int r = 0; r < 2 * K; ++r) s = fma(tab.P[r][q], w[2 * K + r], s);
     a.out[bo + (int64_t)(g - 1) * so] = s;
+    if (a.out32) a.out32[bo + (int64_t)(g - 1) * so] = (float)s;
   }
 }
 

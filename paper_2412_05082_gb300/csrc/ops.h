@@ -77,9 +77,9 @@ struct Ops {
   static cudaError_t prolongate_add(const void* tab, const LevelGeom& fine, const T* xc, T* xf,
                                     T* s0, T* s1, cudaStream_t st);
 
-  // bc = P^T rf.
+  // bc = P^T rf (and, when bc32 is given, bc rounded to FP32 into bc32).
   static cudaError_t restrict_(const void* tab, const LevelGeom& fine, const T* rf, T* bc, T* s0,
-                               T* s1, cudaStream_t st);
+                               T* s1, cudaStream_t st, float* bc32 = nullptr);
 
   // y += x
   static cudaError_t add(T* y, const T* x, int64_t n, cudaStream_t st);

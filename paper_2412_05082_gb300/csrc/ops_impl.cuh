@@ -518,10 +518,11 @@ cudaError_t Ops<T>::patch_scatter(const LevelGeom& g, const T* Y, const int* ver
 template <typename T, int K, bool PROLONG>
 static cudaError_t xfer_pass(const XferTab<T, K>& tab, int d, int axis, const int* din,
                              const int* dout, int Nc, int nc, int nf, const T* in, T* out,
-                             bool add, cudaStream_t st) {
+                             bool add, cudaStream_t st, float* out32 = nullptr) {
   XferArgs<T> a{};
   a.in = in;
   a.out = out;
+  a.out32 = out32;
   a.d = d;
   a.axis = axis;
   a.Nc = Nc;
@@ -550,7 +551,7 @@ static cudaError_t xfer_pass(const XferTab<T, K>& tab, int d, int axis, const in
 
 template <typename T, int K, bool PROLONG>
 static cudaError_t transfer_k(const void* tabp, const LevelGeom& fine, const T* in, T* out,
-                              T* s0, T* s1, cudaStream_t st) {
+                              T* s0, T* s1, cudaStream_t st, float* out32 = nullptr) {
   const auto& tab = static_cast<const HostTables<T, K>*>(tabp)->t.xfer;
   const int d = fine.d, Nc = fine.N / 2, nc = K * Nc - 1, nf = fine.n;
   int dims[3];
@@ -563,7 +564,8 @@ static cudaError_t transfer_k(const void* tabp, const LevelGeom& fine, const T* 
     const bool last = axis == d - 1;
     T* dst = last ? out : bufs[axis % 2];
     cudaError_t e =
-        xfer_pass<T, K, PROLONG>(tab, d, axis, dims, dn, Nc, nc, nf, src, dst, PROLONG && last, st);
+        xfer_pass<T, K, PROLONG>(tab, d, axis, dims, dn, Nc, nc, nf, src, dst, PROLONG && last, st,
+                                 last ? out32 : nullptr);
     if (e != cudaSuccess) return e;
     for (int i = 0; i < 3; ++i) dims[i] = dn[i];
     src = dst;
@@ -582,8 +584,8 @@ cudaError_t Ops<T>::prolongate_add(const void* tab, const LevelGeom& fine, const
 
 template <typename T>
 cudaError_t Ops<T>::restrict_(const void* tab, const LevelGeom& fine, const T* rf, T* bc, T* s0,
-                              T* s1, cudaStream_t st) {
-#define BH_CALL(KK) return transfer_k<T, KK, false>(tab, fine, rf, bc, s0, s1, st)
+                              T* s1, cudaStream_t st, float* bc32) {
+#define BH_CALL(KK) return transfer_k<T, KK, false>(tab, fine, rf, bc, s0, s1, st, bc32)
   BH_K_DISPATCH(fine.k, BH_CALL)
 #undef BH_CALL
   return cudaErrorInvalidValue;
