@@ -370,7 +370,9 @@ bh_status make_ff(bh_batch* b, const std::vector<std::pair<int, FfSweepArgs>>& i
   for (auto& it : items) {
     args.push_back(it.second);
     pid.push_back(it.first);
-    prefix.push_back(prefix.back() + it.second.lines * it.second.N);
+    // each problem's range padded to whole blocks (ff_sweep_list_kernel)
+    const int64_t items = it.second.lines * it.second.N;
+    prefix.push_back(prefix.back() + (items + kFfBlock - 1) / kFfBlock * kFfBlock);
   }
   op.total = prefix.back();
   BCKS(upload(b, args, op.args));
@@ -735,8 +737,8 @@ cudaError_t run_ff(bh_batch* b, const std::vector<FfOp>& ops, int kind) {
     const int* active = b->d_active;
     const void* const* tabs = b->d_tabsff;
     void* params[] = {&args, &prefix, &pid, &n, &active, &tabs};
-    if ((e = cudaLaunchKernel(ff_list_kernel(op.k, kind), dim3(blocks_for(op.total, 128)),
-                              dim3(128), params, 0, st)) != cudaSuccess)
+    if ((e = cudaLaunchKernel(ff_list_kernel(op.k, kind), dim3(blocks_for(op.total, kFfBlock)),
+                              dim3(kFfBlock), params, 0, st)) != cudaSuccess)
       return e;
     count_launch(b);
     if (fork && (e = cudaEventRecord(b->join[i], st)) != cudaSuccess) return e;

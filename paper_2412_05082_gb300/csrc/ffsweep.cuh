@@ -146,9 +146,22 @@ __device__ __forceinline__ void ff_band(const float (&th)[3 * K + 1][4 * K + 1],
 // KIND 1: mix3d  out0 = M in2 + B in0 + 2 L in1, out1 = M in0, out2 = 2 (L in0 + M in1)
 // KIND 2: r = b - scale (B in0 + 2 L in1 + M in2)      (2D final sweep)
 // KIND 3: r = b - scale (M in0 + B in1 + L in2)        (3D final sweep)
+// KIND 0 reads the FP32 x from the block's staged copy: the value at array
+// index i is sx[i - sx_lo] (ff_stage_x)
+template <int K, int LO, int HI>
+__device__ __forceinline__ void ff_load_window_staged(const float* sx, int64_t base, int c, int n,
+                                                      float* w) {
+#pragma unroll
+  for (int j = LO; j < HI; ++j) {
+    const int g = c * K - 2 * K + j;
+    w[j] = (g >= 1 && g <= n) ? sx[base + (g - 1)] : 0.f;
+  }
+}
+
 template <int K, int KIND, bool CANON>
 __device__ __forceinline__ void ff_sweep_cell(const FfTab<K>& tab, const FfSweepArgs& a,
-                                              int64_t base, int c, const int* cls) {
+                                              int64_t base, int c, const int* cls,
+                                              const float* sx = nullptr, int64_t sx_lo = 0) {
   constexpr int W = 4 * K + 1, WML = 3 * K + 1;
   const OpTab<float, K>& hi = tab.hi;
   const OpTab<float, K>& lo = tab.lo;
@@ -158,7 +171,7 @@ __device__ __forceinline__ void ff_sweep_cell(const FfTab<K>& tab, const FfSweep
     for (int q = 0; q < K; ++q) u0[q] = u1[q] = u2[q] = FfAcc{0.f, 0.f};
     if (KIND == 0) {
       float w[W];
-      ff_load_window<K, 0, W>(a.x, base, a.stride, c, a.n, w);
+      ff_load_window_staged<K, 0, W>(sx, base - sx_lo, c, a.n, w);  // axis 0: stride 1
       ff_band<K, 0, 1, CANON, false>(hi.M, lo.M, cls, w, nullptr, u0);
       ff_band<K, 1, 1, CANON, false>(hi.L, lo.L, cls, w, nullptr, u1);
       ff_band<K, 2, 1, CANON, false>(hi.B, lo.B, cls, w, nullptr, u2);
@@ -219,7 +232,8 @@ __device__ __forceinline__ void ff_sweep_cell(const FfTab<K>& tab, const FfSweep
 // sweep_thread
 template <int K, int KIND>
 __device__ __forceinline__ void ff_sweep_thread(const FfTab<K>& tab, const FfSweepArgs& a,
-                                                int64_t tid) {
+                                                int64_t tid, const float* sx = nullptr,
+                                                int64_t sx_lo = 0) {
   int64_t line;
   int c;
   if (a.axis == 0) {
@@ -233,7 +247,7 @@ __device__ __forceinline__ void ff_sweep_thread(const FfTab<K>& tab, const FfSwe
   int64_t strides[3] = {1, (int64_t)a.n, (int64_t)a.n * a.n};
   const int64_t base = line_offset(line, a.d, a.axis, dims, strides);
   if (c >= 2 && c <= a.N - 2) {
-    ff_sweep_cell<K, KIND, true>(tab, a, base, c, nullptr);
+    ff_sweep_cell<K, KIND, true>(tab, a, base, c, nullptr, sx, sx_lo);
   } else {
     int cls[K];
 #pragma unroll
@@ -241,33 +255,71 @@ __device__ __forceinline__ void ff_sweep_thread(const FfTab<K>& tab, const FfSwe
       const int g = c * K + q;
       cls[q] = (g >= 1) ? row_class<K>(g, a.N) : 0;
     }
-    ff_sweep_cell<K, KIND, false>(tab, a, base, c, cls);
+    ff_sweep_cell<K, KIND, false>(tab, a, base, c, cls, sx, sx_lo);
   }
 }
 
+// KIND 0 runs along the contiguous axis with one thread per cell, so that
+// neighbouring threads read x k values apart; the block instead copies the
+// x range of its items (first .. first + blockDim - 1, those below count)
+// into shared memory with coalesced loads.  The range runs from the window
+// start of the first item to the window end of the last, across line ends
+// (lines are contiguous along this axis): at most (blockDim + 3) k + 1
+// values.  Returns the array index of sx[0].
+constexpr int kFfBlock = 128;
+template <int K>
+__device__ __forceinline__ int64_t ff_stage_x(const FfSweepArgs& a, int64_t first, int64_t count,
+                                              float* sx) {
+  const int64_t last = min(first + (int64_t)blockDim.x, count) - 1;
+  const int64_t l0 = first / a.N, l1 = last / a.N;
+  const int c0 = (int)(first - l0 * a.N), c1 = (int)(last - l1 * a.N);
+  const int64_t lo = l0 * a.n + max(c0 * K - 2 * K, 1) - 1;
+  const int64_t hi = l1 * a.n + min(c1 * K + 2 * K, a.n) - 1;
+  for (int64_t i = lo + threadIdx.x; i <= hi; i += blockDim.x) sx[i - lo] = __ldg(a.x + i);
+  __syncthreads();
+  return lo;
+}
+
 template <int K, int KIND>
-__global__ void __launch_bounds__(128) ff_sweep_kernel(const __grid_constant__ FfTab<K> tab,
-                                                       const FfSweepArgs a) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= a.lines * a.N) return;
-  ff_sweep_thread<K, KIND>(tab, a, tid);
+__global__ void __launch_bounds__(kFfBlock) ff_sweep_kernel(const __grid_constant__ FfTab<K> tab,
+                                                            const FfSweepArgs a) {
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x, count = a.lines * a.N;
+  const int64_t tid = first + threadIdx.x;
+  if constexpr (KIND == 0) {
+    __shared__ float sx[(kFfBlock + 3) * K + 1];
+    const int64_t lo = ff_stage_x<K>(a, first, count, sx);
+    if (tid < count) ff_sweep_thread<K, 0>(tab, a, tid, sx, lo);
+  } else {
+    if (tid < count) ff_sweep_thread<K, KIND>(tab, a, tid);
+  }
 }
 
 // the sweep over a (problem, range) list of problems of one degree K (the
 // batched form): tabs[p] is problem p's FfTab<K> device copy, active[p] = 0
-// skips problem p
+// skips problem p.  Every problem's range is padded to a multiple of the
+// block size, so that a block works on one problem.
 template <int K, int KIND>
-__global__ void __launch_bounds__(128) ff_sweep_list_kernel(const FfSweepArgs* args,
-                                                            const int64_t* prefix,
-                                                            const int* pid, int n,
-                                                            const int* active,
-                                                            const void* const* tabs) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= prefix[n]) return;
-  const int s = find_seg(prefix, n, tid);
+__global__ void __launch_bounds__(kFfBlock) ff_sweep_list_kernel(const FfSweepArgs* args,
+                                                                 const int64_t* prefix,
+                                                                 const int* pid, int n,
+                                                                 const int* active,
+                                                                 const void* const* tabs) {
+  const int64_t bstart = (int64_t)blockIdx.x * blockDim.x;
+  if (bstart >= prefix[n]) return;
+  const int s = find_seg(prefix, n, bstart);  // the same for the whole block
   const int p = pid[s];
   if (!active[p]) return;
-  ff_sweep_thread<K, KIND>(*static_cast<const FfTab<K>*>(tabs[p]), args[s], tid - prefix[s]);
+  const FfSweepArgs& a = args[s];
+  const FfTab<K>& tab = *static_cast<const FfTab<K>*>(tabs[p]);
+  const int64_t first = bstart - prefix[s], count = a.lines * a.N;
+  const int64_t tid = first + threadIdx.x;
+  if constexpr (KIND == 0) {
+    __shared__ float sx[(kFfBlock + 3) * K + 1];
+    const int64_t lo = ff_stage_x<K>(a, first, count, sx);
+    if (tid < count) ff_sweep_thread<K, 0>(tab, a, tid, sx, lo);
+  } else {
+    if (tid < count) ff_sweep_thread<K, KIND>(tab, a, tid);
+  }
 }
 
 }  // namespace bh
