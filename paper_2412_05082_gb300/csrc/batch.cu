@@ -370,9 +370,10 @@ bh_status make_ff(bh_batch* b, const std::vector<std::pair<int, FfSweepArgs>>& i
   for (auto& it : items) {
     args.push_back(it.second);
     pid.push_back(it.first);
-    // each problem's range padded to whole blocks (ff_sweep_list_kernel)
-    const int64_t items = it.second.lines * it.second.N;
-    prefix.push_back(prefix.back() + (items + kFfBlock - 1) / kFfBlock * kFfBlock);
+    // each problem's range in whole blocks (ff_sweep_list_kernel): KIND 0 (axis
+    // 0) in tiles of lines and cells, the others one thread per cell
+    prefix.push_back(prefix.back() +
+                     ff_sweep_threads(it.second.axis == 0 ? 0 : 2, it.second.lines, it.second.N));
   }
   op.total = prefix.back();
   BCKS(upload(b, args, op.args));

@@ -10,7 +10,8 @@ namespace bh {
 template <int K, int KIND>
 inline cudaError_t launch_ff(const FfTab<K>& tab, const FfSweepArgs& a, cudaStream_t st) {
   const int block = kFfBlock;
-  ff_sweep_kernel<K, KIND><<<grid_for(a.lines * a.N, block), block, 0, st>>>(tab, a);
+  ff_sweep_kernel<K, KIND><<<grid_for(ff_sweep_threads(KIND, a.lines, a.N), block), block, 0, st>>>(
+      tab, a);
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }

@@ -146,22 +146,12 @@ __device__ __forceinline__ void ff_band(const float (&th)[3 * K + 1][4 * K + 1],
 // KIND 1: mix3d  out0 = M in2 + B in0 + 2 L in1, out1 = M in0, out2 = 2 (L in0 + M in1)
 // KIND 2: r = b - scale (B in0 + 2 L in1 + M in2)      (2D final sweep)
 // KIND 3: r = b - scale (M in0 + B in1 + L in2)        (3D final sweep)
-// KIND 0 reads the FP32 x from the block's staged copy: the value at array
-// index i is sx[i - sx_lo] (ff_stage_x)
-template <int K, int LO, int HI>
-__device__ __forceinline__ void ff_load_window_staged(const float* sx, int64_t base, int c, int n,
-                                                      float* w) {
-#pragma unroll
-  for (int j = LO; j < HI; ++j) {
-    const int g = c * K - 2 * K + j;
-    w[j] = (g >= 1 && g <= n) ? sx[base + (g - 1)] : 0.f;
-  }
-}
-
+// KIND 0 reads the FP32 x window from the block's staged copy: xw[j] is the
+// value at node c K - 2K + j of the line, zero outside 1..n (ff_split_tile)
 template <int K, int KIND, bool CANON>
 __device__ __forceinline__ void ff_sweep_cell(const FfTab<K>& tab, const FfSweepArgs& a,
                                               int64_t base, int c, const int* cls,
-                                              const float* sx = nullptr, int64_t sx_lo = 0) {
+                                              const float* xw = nullptr) {
   constexpr int W = 4 * K + 1, WML = 3 * K + 1;
   const OpTab<float, K>& hi = tab.hi;
   const OpTab<float, K>& lo = tab.lo;
@@ -171,7 +161,8 @@ __device__ __forceinline__ void ff_sweep_cell(const FfTab<K>& tab, const FfSweep
     for (int q = 0; q < K; ++q) u0[q] = u1[q] = u2[q] = FfAcc{0.f, 0.f};
     if (KIND == 0) {
       float w[W];
-      ff_load_window_staged<K, 0, W>(sx, base - sx_lo, c, a.n, w);  // axis 0: stride 1
+#pragma unroll
+      for (int j = 0; j < W; ++j) w[j] = xw[j];
       ff_band<K, 0, 1, CANON, false>(hi.M, lo.M, cls, w, nullptr, u0);
       ff_band<K, 1, 1, CANON, false>(hi.L, lo.L, cls, w, nullptr, u1);
       ff_band<K, 2, 1, CANON, false>(hi.B, lo.B, cls, w, nullptr, u2);
@@ -232,8 +223,7 @@ __device__ __forceinline__ void ff_sweep_cell(const FfTab<K>& tab, const FfSweep
 // sweep_thread
 template <int K, int KIND>
 __device__ __forceinline__ void ff_sweep_thread(const FfTab<K>& tab, const FfSweepArgs& a,
-                                                int64_t tid, const float* sx = nullptr,
-                                                int64_t sx_lo = 0) {
+                                                int64_t tid) {
   int64_t line;
   int c;
   if (a.axis == 0) {
@@ -247,7 +237,7 @@ __device__ __forceinline__ void ff_sweep_thread(const FfTab<K>& tab, const FfSwe
   int64_t strides[3] = {1, (int64_t)a.n, (int64_t)a.n * a.n};
   const int64_t base = line_offset(line, a.d, a.axis, dims, strides);
   if (c >= 2 && c <= a.N - 2) {
-    ff_sweep_cell<K, KIND, true>(tab, a, base, c, nullptr, sx, sx_lo);
+    ff_sweep_cell<K, KIND, true>(tab, a, base, c, nullptr);
   } else {
     int cls[K];
 #pragma unroll
@@ -255,49 +245,85 @@ __device__ __forceinline__ void ff_sweep_thread(const FfTab<K>& tab, const FfSwe
       const int g = c * K + q;
       cls[q] = (g >= 1) ? row_class<K>(g, a.N) : 0;
     }
-    ff_sweep_cell<K, KIND, false>(tab, a, base, c, cls, sx, sx_lo);
+    ff_sweep_cell<K, KIND, false>(tab, a, base, c, cls);
   }
 }
 
-// KIND 0 runs along the contiguous axis with one thread per cell, so that
-// neighbouring threads read x k values apart; the block instead copies the
-// x range of its items (first .. first + blockDim - 1, those below count)
-// into shared memory with coalesced loads.  The range runs from the window
-// start of the first item to the window end of the last, across line ends
-// (lines are contiguous along this axis): at most (blockDim + 3) k + 1
-// values.  Returns the array index of sx[0].
-constexpr int kFfBlock = 128;
+// KIND 0 runs along the contiguous axis.  One thread per cell along a line
+// would put different cells (and boundary and interior row classes) in one
+// warp and read x k values apart; instead a block takes a tile of 32 lines x
+// 4 consecutive cells, warp w the cell c0 + w of all 32 lines (lane = line),
+// so that the row classes and the branch are uniform in a warp.  The tile's
+// x values (per line the nodes of the four cells' windows, c0 K - 2K ..
+// (c0 + 3) K + 2K) are first copied into shared memory, zero outside 1..n.
+constexpr int kFfBlock = 128, kFfTileLines = 32, kFfTileCells = kFfBlock / kFfTileLines;
+__host__ __device__ inline int64_t ff_split_blocks(int64_t lines, int N) {
+  return (lines + kFfTileLines - 1) / kFfTileLines * ((N + kFfTileCells - 1) / kFfTileCells);
+}
+// threads of one sweep launch (KIND 0 in tiles, the others one per cell, whole blocks)
+__host__ __device__ inline int64_t ff_sweep_threads(int kind, int64_t lines, int N) {
+  return kind == 0 ? ff_split_blocks(lines, N) * kFfBlock
+                   : (lines * N + kFfBlock - 1) / kFfBlock * kFfBlock;
+}
+
 template <int K>
-__device__ __forceinline__ int64_t ff_stage_x(const FfSweepArgs& a, int64_t first, int64_t count,
-                                              float* sx) {
-  const int64_t last = min(first + (int64_t)blockDim.x, count) - 1;
-  const int64_t l0 = first / a.N, l1 = last / a.N;
-  const int c0 = (int)(first - l0 * a.N), c1 = (int)(last - l1 * a.N);
-  const int64_t lo = l0 * a.n + max(c0 * K - 2 * K, 1) - 1;
-  const int64_t hi = l1 * a.n + min(c1 * K + 2 * K, a.n) - 1;
-  for (int64_t i = lo + threadIdx.x; i <= hi; i += blockDim.x) sx[i - lo] = __ldg(a.x + i);
+struct FfSplitTile {
+  static constexpr int R = 7 * K + 1;  // staged nodes per line
+  static constexpr int RS = R | 1;     // row stride: odd, so the lanes' rows fall in distinct banks
+};
+
+template <int K>
+__device__ __forceinline__ void ff_split_tile(const FfTab<K>& tab, const FfSweepArgs& a,
+                                              int64_t blk, float* sx) {
+  using S = FfSplitTile<K>;
+  const int tc = (a.N + kFfTileCells - 1) / kFfTileCells;
+  const int64_t lt = blk / tc;
+  const int c0 = (int)(blk - lt * tc) * kFfTileCells;
+  const int64_t l0 = lt * kFfTileLines;
+  const int g0 = c0 * K - 2 * K;  // node of staged column 0
+  for (int e = threadIdx.x; e < kFfTileLines * S::R; e += blockDim.x) {
+    const int r = e / S::R, col = e - r * S::R;
+    const int64_t l = l0 + r;
+    const int g = g0 + col;
+    sx[r * S::RS + col] =
+        (l < a.lines && g >= 1 && g <= a.n) ? __ldg(a.x + l * a.n + (g - 1)) : 0.f;
+  }
   __syncthreads();
-  return lo;
+  const int lane = threadIdx.x % kFfTileLines, w = threadIdx.x / kFfTileLines;
+  const int c = c0 + w;
+  const int64_t l = l0 + lane;
+  if (c >= a.N || l >= a.lines) return;
+  const float* xw = sx + lane * S::RS + w * K;  // node c K - 2K + j at xw[j]
+  const int64_t base = l * a.n;                 // axis 0: line l starts at l n
+  if (c >= 2 && c <= a.N - 2) {
+    ff_sweep_cell<K, 0, true>(tab, a, base, c, nullptr, xw);
+  } else {
+    int cls[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int g = c * K + q;
+      cls[q] = (g >= 1) ? row_class<K>(g, a.N) : 0;
+    }
+    ff_sweep_cell<K, 0, false>(tab, a, base, c, cls, xw);
+  }
 }
 
 template <int K, int KIND>
 __global__ void __launch_bounds__(kFfBlock) ff_sweep_kernel(const __grid_constant__ FfTab<K> tab,
                                                             const FfSweepArgs a) {
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x, count = a.lines * a.N;
-  const int64_t tid = first + threadIdx.x;
   if constexpr (KIND == 0) {
-    __shared__ float sx[(kFfBlock + 3) * K + 1];
-    const int64_t lo = ff_stage_x<K>(a, first, count, sx);
-    if (tid < count) ff_sweep_thread<K, 0>(tab, a, tid, sx, lo);
+    __shared__ float sx[kFfTileLines * FfSplitTile<K>::RS];
+    ff_split_tile<K>(tab, a, blockIdx.x, sx);
   } else {
-    if (tid < count) ff_sweep_thread<K, KIND>(tab, a, tid);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid < a.lines * a.N) ff_sweep_thread<K, KIND>(tab, a, tid);
   }
 }
 
 // the sweep over a (problem, range) list of problems of one degree K (the
 // batched form): tabs[p] is problem p's FfTab<K> device copy, active[p] = 0
-// skips problem p.  Every problem's range is padded to a multiple of the
-// block size, so that a block works on one problem.
+// skips problem p.  Every problem's range holds ff_sweep_threads(KIND, ...)
+// threads, whole blocks, so that a block works on one problem.
 template <int K, int KIND>
 __global__ void __launch_bounds__(kFfBlock) ff_sweep_list_kernel(const FfSweepArgs* args,
                                                                  const int64_t* prefix,
@@ -311,14 +337,13 @@ __global__ void __launch_bounds__(kFfBlock) ff_sweep_list_kernel(const FfSweepAr
   if (!active[p]) return;
   const FfSweepArgs& a = args[s];
   const FfTab<K>& tab = *static_cast<const FfTab<K>*>(tabs[p]);
-  const int64_t first = bstart - prefix[s], count = a.lines * a.N;
-  const int64_t tid = first + threadIdx.x;
+  const int64_t first = bstart - prefix[s];
   if constexpr (KIND == 0) {
-    __shared__ float sx[(kFfBlock + 3) * K + 1];
-    const int64_t lo = ff_stage_x<K>(a, first, count, sx);
-    if (tid < count) ff_sweep_thread<K, 0>(tab, a, tid, sx, lo);
+    __shared__ float sx[kFfTileLines * FfSplitTile<K>::RS];
+    ff_split_tile<K>(tab, a, first / kFfBlock, sx);
   } else {
-    if (tid < count) ff_sweep_thread<K, KIND>(tab, a, tid);
+    const int64_t tid = first + threadIdx.x;
+    if (tid < a.lines * a.N) ff_sweep_thread<K, KIND>(tab, a, tid);
   }
 }
 
