@@ -354,7 +354,9 @@ bh_status make_sweep(bh_batch* b, const std::vector<std::pair<int, SweepArgs<T>>
   for (auto& it : items) {
     args.push_back(it.second);
     pid.push_back(it.first);
-    prefix.push_back(prefix.back() + it.second.lines * it.second.N);
+    // whole blocks per problem (sweep_batch_kernel): the split along axis 0 in tiles
+    prefix.push_back(prefix.back() + sweep_launch_threads(it.second.axis == 0 ? 0 : 2,
+                                                          it.second.lines, it.second.N));
   }
   op.total = prefix.back();
   BCKS(upload(b, args, op.args));

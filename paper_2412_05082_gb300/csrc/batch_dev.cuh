@@ -32,20 +32,37 @@ struct Meta {                 // per problem, indexed by problem id
     case 7: CALL(7); break; \
   }
 
+// Every problem's range holds sweep_launch_threads(KIND, ...) threads, whole
+// blocks, so that a block of the split (KIND 0, in tiles) works on one problem.
 template <typename T, int KIND>
 __global__ void __launch_bounds__(128) sweep_batch_kernel(Meta m, const SweepArgs<T>* args,
                                                           const int64_t* prefix, const int* pid,
                                                           int n) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= prefix[n]) return;
-  const int s = find_seg(prefix, n, tid);
-  const int p = pid[s];
-  if (!m.active[p]) return;
-  const int64_t local = tid - prefix[s];
+  if constexpr (KIND == 0) {
+    __shared__ T sx[kSplitTileLines * SplitTile<kMaxK>::RS];
+    const int64_t bstart = (int64_t)blockIdx.x * blockDim.x;
+    if (bstart >= prefix[n]) return;
+    const int s = find_seg(prefix, n, bstart);  // the same for the whole block
+    const int p = pid[s];
+    if (!m.active[p]) return;
+    const int64_t blk = (bstart - prefix[s]) / kSplitBlock;
+#define BH_CALL(KK) \
+  sweep_split_tile<T, KK>(static_cast<const Tables<T, KK>*>(m.tabs[p])->op, args[s], blk, sx)
+    BH_KSWITCH(m.k[p], BH_CALL)
+#undef BH_CALL
+  } else {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= prefix[n]) return;
+    const int s = find_seg(prefix, n, tid);
+    const int p = pid[s];
+    if (!m.active[p]) return;
+    const int64_t local = tid - prefix[s];
+    if (local >= args[s].lines * args[s].N) return;  // padding of the range
 #define BH_CALL(KK) \
   sweep_thread<T, KK, KIND>(static_cast<const Tables<T, KK>*>(m.tabs[p])->op, args[s], local)
-  BH_KSWITCH(m.k[p], BH_CALL)
+    BH_KSWITCH(m.k[p], BH_CALL)
 #undef BH_CALL
+  }
 }
 
 template <typename T, bool PROLONG>
@@ -303,6 +320,7 @@ __global__ void __launch_bounds__(256, 2) vcycle_persistent_kernel(
         const int p = P.pid[s];
         if (!m64.active[p]) continue;
         const int64_t local = tid - P.prefix[s];
+        if (local >= args[s].lines * args[s].N) continue;  // padding of the range
 #define BH_CALL(KK)                                                                              \
   if (kind == kPhSweep0)                                                                         \
     sweep_thread<double, KK, 0, true>(static_cast<const Tables<double, KK>*>(m64.tabs[p])->op,    \

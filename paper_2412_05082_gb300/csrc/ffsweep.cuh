@@ -249,52 +249,22 @@ __device__ __forceinline__ void ff_sweep_thread(const FfTab<K>& tab, const FfSwe
   }
 }
 
-// KIND 0 runs along the contiguous axis.  One thread per cell along a line
-// would put different cells (and boundary and interior row classes) in one
-// warp and read x k values apart; instead a block takes a tile of 32 lines x
-// 4 consecutive cells, warp w the cell c0 + w of all 32 lines (lane = line),
-// so that the row classes and the branch are uniform in a warp.  The tile's
-// x values (per line the nodes of the four cells' windows, c0 K - 2K ..
-// (c0 + 3) K + 2K) are first copied into shared memory, zero outside 1..n.
-constexpr int kFfBlock = 128, kFfTileLines = 32, kFfTileCells = kFfBlock / kFfTileLines;
-__host__ __device__ inline int64_t ff_split_blocks(int64_t lines, int N) {
-  return (lines + kFfTileLines - 1) / kFfTileLines * ((N + kFfTileCells - 1) / kFfTileCells);
-}
-// threads of one sweep launch (KIND 0 in tiles, the others one per cell, whole blocks)
+// KIND 0 runs along the contiguous axis, in the tiles of the FP64 split
+// (kernels.cuh: 32 lines x 4 cells per block, a warp per cell, from a
+// shared-memory copy of the tile's x)
+constexpr int kFfBlock = kSplitBlock;
 __host__ __device__ inline int64_t ff_sweep_threads(int kind, int64_t lines, int N) {
-  return kind == 0 ? ff_split_blocks(lines, N) * kFfBlock
-                   : (lines * N + kFfBlock - 1) / kFfBlock * kFfBlock;
+  return sweep_launch_threads(kind, lines, N);
 }
-
-template <int K>
-struct FfSplitTile {
-  static constexpr int R = 7 * K + 1;  // staged nodes per line
-  static constexpr int RS = R | 1;     // row stride: odd, so the lanes' rows fall in distinct banks
-};
 
 template <int K>
 __device__ __forceinline__ void ff_split_tile(const FfTab<K>& tab, const FfSweepArgs& a,
                                               int64_t blk, float* sx) {
-  using S = FfSplitTile<K>;
-  const int tc = (a.N + kFfTileCells - 1) / kFfTileCells;
-  const int64_t lt = blk / tc;
-  const int c0 = (int)(blk - lt * tc) * kFfTileCells;
-  const int64_t l0 = lt * kFfTileLines;
-  const int g0 = c0 * K - 2 * K;  // node of staged column 0
-  for (int e = threadIdx.x; e < kFfTileLines * S::R; e += blockDim.x) {
-    const int r = e / S::R, col = e - r * S::R;
-    const int64_t l = l0 + r;
-    const int g = g0 + col;
-    sx[r * S::RS + col] =
-        (l < a.lines && g >= 1 && g <= a.n) ? __ldg(a.x + l * a.n + (g - 1)) : 0.f;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x % kFfTileLines, w = threadIdx.x / kFfTileLines;
-  const int c = c0 + w;
-  const int64_t l = l0 + lane;
-  if (c >= a.N || l >= a.lines) return;
-  const float* xw = sx + lane * S::RS + w * K;  // node c K - 2K + j at xw[j]
-  const int64_t base = l * a.n;                 // axis 0: line l starts at l n
+  int64_t l;
+  int c;
+  const float* xw = split_stage<float, K>(a.x, a.lines, a.N, a.n, blk, sx, l, c);
+  if (c < 0) return;
+  const int64_t base = l * a.n;  // axis 0: line l starts at l n
   if (c >= 2 && c <= a.N - 2) {
     ff_sweep_cell<K, 0, true>(tab, a, base, c, nullptr, xw);
   } else {
@@ -312,7 +282,7 @@ template <int K, int KIND>
 __global__ void __launch_bounds__(kFfBlock) ff_sweep_kernel(const __grid_constant__ FfTab<K> tab,
                                                             const FfSweepArgs a) {
   if constexpr (KIND == 0) {
-    __shared__ float sx[kFfTileLines * FfSplitTile<K>::RS];
+    __shared__ float sx[kSplitTileLines * SplitTile<K>::RS];
     ff_split_tile<K>(tab, a, blockIdx.x, sx);
   } else {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -339,7 +309,7 @@ __global__ void __launch_bounds__(kFfBlock) ff_sweep_list_kernel(const FfSweepAr
   const FfTab<K>& tab = *static_cast<const FfTab<K>*>(tabs[p]);
   const int64_t first = bstart - prefix[s];
   if constexpr (KIND == 0) {
-    __shared__ float sx[kFfTileLines * FfSplitTile<K>::RS];
+    __shared__ float sx[kSplitTileLines * SplitTile<K>::RS];
     ff_split_tile<K>(tab, a, first / kFfBlock, sx);
   } else {
     const int64_t tid = first + threadIdx.x;

@@ -145,9 +145,12 @@ __device__ __forceinline__ void band_acc(const T (&tab)[3 * K + 1][4 * K + 1], c
 //                (in0 = T_M, in1 = T_L, in2 = T_B)
 // KIND 2: final2d y = B in0 + 2 L in1 + M in2  (in = T_M, T_L, T_B)
 // KIND 3: final3d y = M in0 + B in1 + L in2    (in = U_M, U_B, U_L)
+// KIND 0 may take its window from a staged copy: xw[j] = value at node
+// c K - 2K + j of the line, zero outside 1..n (sweep_split_tile)
 template <typename T, int K, int KIND, bool CANON, bool COHERENT = false>
 __device__ __forceinline__ void sweep_cell(const OpTab<T, K>& tab, const SweepArgs<T>& a,
-                                           int64_t base, int c, const int* cls) {
+                                           int64_t base, int c, const int* cls,
+                                           const T* xw = nullptr) {
   constexpr int W = 4 * K + 1;  // B band reaches node offsets -2K..2K of every row
   constexpr int WML = 3 * K + 1;  // M and L reach -K..K
   T w[W];
@@ -155,7 +158,12 @@ __device__ __forceinline__ void sweep_cell(const OpTab<T, K>& tab, const SweepAr
     T aM[K], aL[K], aB[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) aM[q] = aL[q] = aB[q] = T(0);
-    load_window<T, K, 0, W, COHERENT>(a.in[0], base, a.stride, c, a.n, w);
+    if (xw) {
+#pragma unroll
+      for (int j = 0; j < W; ++j) w[j] = xw[j];
+    } else {
+      load_window<T, K, 0, W, COHERENT>(a.in[0], base, a.stride, c, a.n, w);
+    }
     band_acc<T, K, 0, CANON>(tab.M, cls, w, aM, T(1));
     band_acc<T, K, 1, CANON>(tab.L, cls, w, aL, T(1));
     band_acc<T, K, 2, CANON>(tab.B, cls, w, aB, T(1));
@@ -249,12 +257,90 @@ __device__ __forceinline__ void sweep_thread(const OpTab<T, K>& tab, const Sweep
   }
 }
 
+// The split along the contiguous axis (KIND 0, axis 0) in tiles: one thread
+// per cell along a line would put different cells (boundary and interior row
+// classes, two code paths) in one warp and read x k values apart.  A block of
+// 128 threads takes 32 lines x 4 consecutive cells instead, warp w the cell
+// c0 + w of all 32 lines (lane = line), so that its row classes and branch
+// are uniform; it first copies the tile's x values (per line the nodes of the
+// four cells' windows, c0 K - 2K .. (c0 + 3) K + 2K, zero outside 1..n) into
+// shared memory with loads along the lines.
+constexpr int kSplitBlock = 128, kSplitTileLines = 32;
+constexpr int kSplitTileCells = kSplitBlock / kSplitTileLines;
+__host__ __device__ inline int64_t split_blocks(int64_t lines, int N) {
+  return (lines + kSplitTileLines - 1) / kSplitTileLines *
+         ((N + kSplitTileCells - 1) / kSplitTileCells);
+}
+// threads of one sweep launch: the split (KIND 0) in tiles, the other sweeps
+// one thread per cell, in whole blocks of 128
+__host__ __device__ inline int64_t sweep_launch_threads(int kind, int64_t lines, int N) {
+  return kind == 0 ? split_blocks(lines, N) * kSplitBlock
+                   : (lines * N + kSplitBlock - 1) / kSplitBlock * kSplitBlock;
+}
+template <int K>
+struct SplitTile {
+  static constexpr int R = 7 * K + 1;  // staged nodes per line
+  static constexpr int RS = R | 1;     // row stride: odd, so the lanes' rows fall in distinct banks
+};
+
+// the tile's staged x (V: the value type) for block blk of a split; returns
+// for the calling thread its line l, cell c and the window pointer, c = -1
+// for a thread without a cell
+template <typename V, int K>
+__device__ __forceinline__ const V* split_stage(const V* x, int64_t lines, int N, int n,
+                                                int64_t blk, V* sx, int64_t& l, int& c) {
+  using S = SplitTile<K>;
+  const int tc = (N + kSplitTileCells - 1) / kSplitTileCells;
+  const int64_t lt = blk / tc;
+  const int c0 = (int)(blk - lt * tc) * kSplitTileCells;
+  const int64_t l0 = lt * kSplitTileLines;
+  const int g0 = c0 * K - 2 * K;  // node of staged column 0
+  for (int e = threadIdx.x; e < kSplitTileLines * S::R; e += blockDim.x) {
+    const int r = e / S::R, col = e - r * S::R;
+    const int64_t lr = l0 + r;
+    const int g = g0 + col;
+    sx[r * S::RS + col] = (lr < lines && g >= 1 && g <= n) ? __ldg(x + lr * n + (g - 1)) : V(0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x % kSplitTileLines, w = threadIdx.x / kSplitTileLines;
+  c = c0 + w;
+  l = l0 + lane;
+  if (c >= N || l >= lines) c = -1;
+  return sx + lane * S::RS + w * K;
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void sweep_split_tile(const OpTab<T, K>& tab, const SweepArgs<T>& a,
+                                                 int64_t blk, T* sx) {
+  int64_t l;
+  int c;
+  const T* xw = split_stage<T, K>(a.in[0], a.lines, a.N, a.n, blk, sx, l, c);
+  if (c < 0) return;
+  const int64_t base = l * a.n;  // axis 0: line l starts at l n
+  if (c >= 2 && c <= a.N - 2) {
+    sweep_cell<T, K, 0, true>(tab, a, base, c, nullptr, xw);
+  } else {
+    int cls[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int g = c * K + q;
+      cls[q] = (g >= 1) ? row_class<K>(g, a.N) : 0;
+    }
+    sweep_cell<T, K, 0, false>(tab, a, base, c, cls, xw);
+  }
+}
+
 template <typename T, int K, int KIND>
 __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ OpTab<T, K> tab,
                                                     const SweepArgs<T> a) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= a.lines * a.N) return;
-  sweep_thread<T, K, KIND>(tab, a, tid);
+  if constexpr (KIND == 0) {
+    __shared__ T sx[kSplitTileLines * SplitTile<K>::RS];
+    sweep_split_tile<T, K>(tab, a, blockIdx.x, sx);
+  } else {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= a.lines * a.N) return;
+    sweep_thread<T, K, KIND>(tab, a, tid);
+  }
 }
 
 // ---------------------------------------------------------------------------

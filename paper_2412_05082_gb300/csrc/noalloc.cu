@@ -98,7 +98,7 @@ const OpTab<double, K>& optab(double gamma) {
 template <int K, int KIND>
 cudaError_t sweep(const OpTab<double, K>& tab, const SweepArgs<double>& a, cudaStream_t st) {
   const int block = 128;
-  const unsigned grid = (unsigned)((a.lines * a.N + block - 1) / block);
+  const unsigned grid = (unsigned)((sweep_launch_threads(KIND, a.lines, a.N) + block - 1) / block);
   sweep_kernel<double, K, KIND><<<grid, block, 0, st>>>(tab, a);
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();

@@ -214,7 +214,8 @@ void Ops<T>::free_tables(void* p, int k) {
 template <typename T, int K, int KIND>
 static cudaError_t launch_sweep(const OpTab<T, K>& tab, const SweepArgs<T>& a, cudaStream_t st) {
   const int block = 128;
-  sweep_kernel<T, K, KIND><<<grid_for(a.lines * a.N, block), block, 0, st>>>(tab, a);
+  sweep_kernel<T, K, KIND><<<grid_for(sweep_launch_threads(KIND, a.lines, a.N), block), block, 0,
+                             st>>>(tab, a);
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
