@@ -85,17 +85,8 @@ __device__ __forceinline__ float2 ff_value(const FfAcc& a) {
   return make_float2(s, __fsub_rn(a.c, __fsub_rn(s, a.s)));
 }
 
-// window w[j] = value at node c K - 2K + j, j in [LO, HI), zero outside 1..n
-// (double-float values: hi parts in wh, lo parts in wl)
-template <int K, int LO, int HI>
-__device__ __forceinline__ void ff_load_window(const float* __restrict__ p, int64_t base,
-                                               int64_t stride, int c, int n, float* w) {
-#pragma unroll
-  for (int j = LO; j < HI; ++j) {
-    const int g = c * K - 2 * K + j;
-    w[j] = (g >= 1 && g <= n) ? __ldg(p + base + (int64_t)(g - 1) * stride) : 0.f;
-  }
-}
+// window of double-float values: node c K - 2K + j, j in [LO, HI), hi parts in
+// wh[j], lo parts in wl[j], zero outside 1..n
 template <int K, int LO, int HI>
 __device__ __forceinline__ void ff_load_window(const float2* __restrict__ p, int64_t base,
                                                int64_t stride, int c, int n, float* wh,
@@ -224,6 +215,7 @@ __device__ __forceinline__ void ff_sweep_cell(const FfTab<K>& tab, const FfSweep
 template <int K, int KIND>
 __device__ __forceinline__ void ff_sweep_thread(const FfTab<K>& tab, const FfSweepArgs& a,
                                                 int64_t tid) {
+  static_assert(KIND != 0, "the split runs in tiles (ff_split_tile)");
   int64_t line;
   int c;
   if (a.axis == 0) {
