@@ -62,6 +62,8 @@ struct MvsArgs {
   double ascale;      // A_l = ascale * A_ref
   double pscale;      // omega * h^(4-d)
   const T* dinv;      // 1 / (lambda_x + lambda_y) per type combination, m^2 each
+  const void* dtab;   // single-problem kernel: device copy of its Tables<T, K> (the tables
+                      // staged in shared memory are read from it with coalesced loads)
 };
 
 template <typename T, int K>
@@ -748,10 +750,18 @@ __global__ void __launch_bounds__(256) mvs2_color_kernel(const __grid_constant__
   const int first = blockIdx.x * a.pb;
   const int np = min(a.pb, a.count - first);
   if (np <= 0) return;
-  if (mvs2_tile_is_interior(a, first, np))
-    mvs2_tile_interior<T, K, sizeof(T) == 4>(tab.op, tab.fdm, a, first, np, smem_raw);
-  else
-    mvs2_tile<T, K>(tab.op, tab.fdm, a, first, np, smem_raw);
+  // FP32 interior tiles read the parameter tables as constant operands; the
+  // tables staged in shared memory come from the device copy (a parameter
+  // read with a different address per thread would be serialized)
+  const auto* dt = static_cast<const Tables<T, K>*>(a.dtab);
+  if (mvs2_tile_is_interior(a, first, np)) {
+    if constexpr (sizeof(T) == 4)
+      mvs2_tile_interior<T, K, true>(tab.op, tab.fdm, a, first, np, smem_raw);
+    else
+      mvs2_tile_interior<T, K>(dt->op, dt->fdm, a, first, np, smem_raw);
+  } else {
+    mvs2_tile<T, K>(dt->op, dt->fdm, a, first, np, smem_raw);
+  }
 }
 
 }  // namespace bh

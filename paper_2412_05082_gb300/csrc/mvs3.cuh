@@ -377,10 +377,17 @@ __global__ void __launch_bounds__(Mvs3Cfg<T, K>::THREADS)
   const int first = blockIdx.x * a.pb;
   const int np = min(a.pb, a.count - first);
   if (np <= 0) return;
-  if (mvs3_tile_is_interior(a, first, np))
-    mvs3_tile<T, K, true>(tab.op, tab.fdm, a, first, np, smem_raw);
-  else
-    mvs3_tile<T, K, false>(tab.op, tab.fdm, a, first, np, smem_raw);
+  // FP32 interior tiles read the parameter tables as constant operands; the
+  // tables staged in shared memory come from the device copy
+  const auto* dt = static_cast<const Tables<T, K>*>(a.dtab);
+  if (mvs3_tile_is_interior(a, first, np)) {
+    if constexpr (sizeof(T) == 4)
+      mvs3_tile<T, K, true>(tab.op, tab.fdm, a, first, np, smem_raw);
+    else
+      mvs3_tile<T, K, true>(dt->op, dt->fdm, a, first, np, smem_raw);
+  } else {
+    mvs3_tile<T, K, false>(dt->op, dt->fdm, a, first, np, smem_raw);
+  }
 }
 
 }  // namespace bh

@@ -357,6 +357,7 @@ static cudaError_t mvs_color_k(const void* tabp, const LevelGeom& g, T* x, const
   a.ascale = ascale;
   a.pscale = pscale;
   a.dinv = h->dinv;
+  a.dtab = h->dev;
   using C = Mvs2Cfg<T, K>;
   // patches per block: enough blocks for two waves on 152 SMs, at most PB_MAX
   int pb = pb_req > 0 ? pb_req : auto_tile<T>(count, kMvs2TileF64[K], kMvs2TileF32[K]);
@@ -389,6 +390,7 @@ static cudaError_t mvs3_color_k(const void* tabp, const LevelGeom& g, T* x, cons
   a.ascale = ascale;
   a.pscale = pscale;
   a.dinv = h->dinv;
+  a.dtab = h->dev;
   using C = Mvs3Cfg<T, K>;
   int pb = pb_req > 0 ? pb_req : auto_tile<T>(count, kMvs3TileF64[K], kMvs3TileF32[K]);
   pb = pb < 1 ? 1 : (pb > C::PB_MAX ? C::PB_MAX : pb);
