@@ -808,8 +808,8 @@ def main():
         "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS,
         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in this
-        # configuration, from one ncu capture of the unchanged kernel (62.95 MB + 0.57 MB)
-        "traffic": 63.52e6, "traffic_unit": "bytes per launch",
+        # configuration, from one ncu capture of the unchanged kernel (62.96 MB + 0.75 MB)
+        "traffic": 63.71e6, "traffic_unit": "bytes per launch",
         "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (derived from the unit counts "
                        "and clock; the measured-peaks file has no FP64 entry)",
         "measured_peak_tflops": probe,
@@ -820,7 +820,7 @@ def main():
                         "copy bandwidth = %.2f flop/B, while this kernel does about %.0f flop per "
                         "DRAM byte; an HBM fraction of 60 %% is unreachable in FP64, the FP64 pipe "
                         "saturates first" % (FP64_PEAK_TFLOPS * 1e12 / (HBM_GBS * 1e9),
-                                             flops_launch / 63.52e6),
+                                             flops_launch / 63.71e6),
         "fma_per_patch": mvs2_fma_per_patch(k), "patches_per_launch": patches / 8,
         "launch_ms": t_step / 8 * 1e3,
     }
